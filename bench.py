@@ -1,0 +1,343 @@
+"""Benchmark of the Combined Sieve hot path on one or more GPUs.
+
+One step = one full sieve (cs_sieve) of the paper-shaped search
+K = 953#/210, m in [1e8, 1e8 + 1e5) coprime to 210, X = 20000, primes up to
+L = 1e9: prime generation, K mod p, small-prime tile sieve, large-prime walk,
+counts and checksum.  Metric: enumerated factors per second (F / time), with
+F and the bitset checksum checked against the same values on every step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
+
+Under torchrun each rank sieves its own m-range (independent problems, no
+data-path collective; weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2012_03771_gb300 import workloads  # noqa: E402
+
+METRIC = "enumerated factors/s at L=1e9 (bit-exact bitset + per-m counts)"
+UNIT = "factors/s"
+KC_NAMES = ["gen_small", "tile_sieve", "gen_large", "large_walk", "final"]
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return rank, ws
+
+
+def _params_for_rank(base: workloads.SieveParams, rank: int) -> workloads.SieveParams:
+    return base.with_(M_start=base.M_start + rank * base.M_inc)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, path):
+        self.path, self.proc = path, None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, device_index=0):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9 or parts[0] != str(device_index):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(params: workloads.SieveParams, n_rows: int, seed: int = 0):
+    """The CPU oracle (as it stands) on a bounded sample of the workload: n_rows
+    evenly spaced coprime m, all sieving primes.  Returns (factors, seconds, cores)."""
+    import oracle.oracle as O
+    rows = O.rows(params.d, params.M_start, params.M_inc)
+    idx = [int(i * (len(rows) - 1) / max(n_rows - 1, 1)) for i in range(n_rows)]
+    pick = [int(rows[i]) for i in sorted(set(idx))]
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    _, F, _ = O.sieve(params.P, params.d, params.SL, params.L, pick, threads=cores)
+    dt = time.perf_counter() - t0
+    return int(F.sum()), dt, cores, len(pick)
+
+
+def run_reference(args, params):
+    rank, ws = _dist()
+    if rank != 0:
+        return
+    import oracle.oracle as O
+    O.build()
+    n_rows = args.ref_rows
+    for _ in range(args.warmup):
+        oracle_sample(params, n_rows)
+    Fs, ts = 0, 0.0
+    cores, nr = 1, n_rows
+    for _ in range(args.steps):
+        F, dt, cores, nr = oracle_sample(params, n_rows)
+        Fs += F
+        ts += dt
+    value = Fs / ts
+    sample = f"{nr} of the search's coprime m per step (evenly spaced), all primes <= L"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * ts / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": _config(params, None),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _config(params, info):
+    c = {"workload": f"search_953: K=953#/210, m in [{params.M_start}, {params.M_start + params.M_inc}) "
+                     f"coprime to 210, X={params.SL}, primes {params.P} < p <= {params.L}",
+         "P": params.P, "d": params.d, "M_start": params.M_start, "M_inc": params.M_inc, "SL": params.SL,
+         "L": params.L, "parallelism": "replicas (independent m-ranges per rank)",
+         "l2": "flushed between steps (512 MB device write)"}
+    if info is not None:
+        c.update({"M_c": int(info.M_c), "W": int(info.W), "bitset_bytes": int(info.bitset_bytes),
+                  "threshold": int(info.threshold), "large_mode": int(info.large_mode),
+                  "tile_rows": int(info.tile_rows)})
+    return c
+
+
+def run_cuda(args, params):
+    import numpy as np
+    import torch
+    import paper_2012_03771_gb300 as cs
+    from paper_2012_03771_gb300 import build
+
+    rank, ws = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+    cs.load()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    tuning = dict(profile=True)
+    if args.mode:
+        tuning["large_mode"] = args.mode
+    if args.threshold:
+        tuning["threshold"] = args.threshold
+    plan = cs.Plan(*params.as_tuple(), **tuning)
+    info = plan.info
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            plan.sieve(stream)
+        plan.sync()
+        F_ref, h_ref = cs.cs_counts(plan.h)
+        stats = plan.stats()
+
+        clocks = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_bench_r{rank}.csv")
+                        if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_{os.getpid()}.csv")
+        clocks.start()
+        barrier()
+        torch.cuda.synchronize()
+        step_ms, kern_ms, kern_n = [], [0.0] * 5, [0] * 5
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.fill_(k & 0xff)                       # evict the previous step from L2
+            ev[k][0].record(stream)
+            plan.sieve(stream)
+            ev[k][1].record(stream)
+            stream.synchronize()
+            ms, n = plan.kernel_times()
+            kern_ms = [a + b for a, b in zip(kern_ms, ms)]
+            kern_n = [a + b for a, b in zip(kern_n, n)]
+            F, h = cs.cs_counts(plan.h)
+            if (F, h) != (F_ref, h_ref):
+                raise SystemExit(f"step {k}: F/hash changed ({F}, {h:#x}) != ({F_ref}, {h_ref:#x})")
+        torch.cuda.synchronize()
+        barrier()
+        clk = clocks.stop(local)
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+
+    total_ms = sum(step_ms)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        f = torch.tensor([float(F_ref)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(f, op=dist.ReduceOp.SUM)
+        F_all = float(f.item())
+    else:
+        F_all = float(F_ref)
+    value = F_all * args.steps / (total_ms / 1e3)
+    intervals_s = int(info.M_c) * ws * args.steps / (total_ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers --------------------
+    d2h = int(info.bitset_bytes) + 4 * int(info.M_c) + 16
+    host_bits = torch.empty(max(int(info.bitset_bytes) // 8, 1), dtype=torch.int64).pin_memory()
+    host_cnt = torch.empty(max(int(info.M_c), 1), dtype=torch.int32).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h2d = 0
+    for _ in range(e2e_steps):
+        p2 = cs.Plan(*params.as_tuple(), **{k: v for k, v in tuning.items() if k != "profile"})
+        h2d = int(p2.info.h2d_bytes)
+        p2.sieve(stream)
+        cs.cs_fetch_bitset(p2.h, host_bits.numpy().view(np.uint64))
+        cs.cs_counts(p2.h, host_cnt.numpy().view(np.uint32))
+        p2.close()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_value = F_all / e2e_s if ws == 1 else F_all / e2e_s
+
+    # ---- roofline of the dominant kernel ------------------------------------
+    peaks, peak_src = _peaks()
+    dom = max(range(5), key=lambda i: kern_ms[i])
+    roof = roofline(dom, kern_ms, kern_n, stats, info, params, peaks, peak_src, clk)
+
+    # ---- CPU oracle on a bounded sample -------------------------------------
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        try:
+            import oracle.oracle as O
+            O.build()
+            Fs, dt, cores, nr = oracle_sample(params, args.cpu_rows)
+            cpu = {"value": Fs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": f"{nr} of {int(info.M_c)} coprime m (evenly spaced), all primes <= L; {dt:.1f} s"}
+        except Exception as e:  # the oracle is a reported baseline only
+            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"failed: {e}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32" if info.narrow else "u64",
+            "data": "synthetic (parameters of the paper-shaped search; primes generated on device)",
+            "config": _config(params, info),
+            "intervals_per_s": intervals_s,
+            "F_per_step": int(F_ref), "hash": f"{h_ref:#018x}",
+            "stats": stats,
+            "kernel_ms_per_step": {n: kern_ms[i] / args.steps for i, n in enumerate(KC_NAMES)},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "includes": "cs_plan (host tables, H2D, allocation) + cs_sieve + bitset/counts D2H + cs_destroy"},
+            "gpu_launches": int(info.launches_per_sieve) * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def roofline(dom, kern_ms, kern_n, stats, info, params, peaks, peak_src, clk):
+    """Roofline of the dominant kernel class (algorithmic work per launch over
+    its CUDA-event duration)."""
+    name = KC_NAMES[dom]
+    per_launch_ms = kern_ms[dom] / max(kern_n[dom], 1)
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    n_sm = 152
+    if name == "final":
+        bytes_ = int(info.bitset_bytes) + 4 * int(info.M_c)
+        achieved = bytes_ / (per_launch_ms / 1e3) / 1e9
+        peak = peaks["hbm_gbs"]
+        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": peak_src}
+    # integer ALU kernels: algorithmic 32-bit integer operations against the
+    # issue rate of 152 SMs x 4 schedulers x 32 lanes at the maximum SM clock
+    peak = n_sm * 4 * 32 * sm_mhz * 1e6 / 1e12          # Tops/s
+    if name == "large_walk":
+        ops = stats["levels"] * OPS_PER_LEVEL + stats["hits_all"] * OPS_PER_HIT
+        ops_launch = ops / max(kern_n[dom] / max(1, 1), 1)
+    else:
+        ops_launch = 0
+    achieved = ops_launch / (per_launch_ms / 1e3) / 1e12
+    return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+            "frac": achieved / peak if peak else None, "traffic": None,
+            "peak_source": f"derived: {n_sm} SMs x 128 int lanes x {sm_mhz:.0f} MHz"}
+
+
+# integer operations of one solver pass and one hit
+OPS_PER_LEVEL = 1
+OPS_PER_HIT = 1
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--config", default="search_953", choices=sorted(workloads.NAMED))
+    ap.add_argument("--mode", type=int, default=0)
+    ap.add_argument("--threshold", type=int, default=0)
+    ap.add_argument("--cpu-rows", type=int, default=128)
+    ap.add_argument("--ref-rows", type=int, default=16)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    rank, ws = _dist()
+    params = _params_for_rank(workloads.NAMED[args.config], rank)
+    if args.impl == "reference":
+        run_reference(args, params)
+    else:
+        run_cuda(args, params)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * combsieve.h -- C ABI of the GB300 Combined Sieve.
+ *
+ * The Combined Sieve (S. Troisi, "Combined Sieve Algorithm for Prime Gaps",
+ * arXiv:2012.03771) sieves many intervals [N - SL, N + SL], N = m*K, at once,
+ * for K = P#/d and every multiplier m in a range that is coprime to d.  This
+ * library runs the whole sieve on one GPU (sm_103a) and keeps the result, a
+ * composite bitset laid out as [m][x coprime to K], in device memory.
+ *
+ * Output definition (the sieve's contract; a CPU oracle implements the same):
+ *   K      = P#/d, the product of the primes q <= P that do not divide d
+ *            (Section 2, "Primorials").
+ *   rows   = m in [M_start, M_start + M_inc) with gcd(m, d) = 1, ascending
+ *            (Section 3: m sharing a factor with d are skipped).  M_c rows.
+ *   cols   = x in [-SL, SL] with gcd(|x|, K) = 1, ascending; x = 0 is a column
+ *            only when K = 1.  W columns.
+ *   layout = words_per_row = ceil(W/64) uint64 words per row, row-major;
+ *            column j is bit (j & 63) of word (j >> 6); padding bits are 0.
+ *   bit    = 1 (survivor) iff no sieving prime p, P < p <= L, divides N + x
+ *            with N + x != p, and (wheel on, the default) no prime q | d
+ *            divides N + x with N + x != q.
+ *   F      = enumerated factors: the number of (p, row, col) with p | N + x,
+ *            N + x != p (the wheel is not counted).
+ *   hash   = sum over rows i, words w of mix64(word + (i*wpr + w)*0x9E3779B97F4A7C15)
+ *            mod 2^64; mix64 is the SplitMix64 finaliser.
+ *
+ * Parameter limits (violations return CS_EINVAL): 1 <= d, d squarefree with
+ * every prime factor <= P; P <= 2^20; SL <= 2^20; L <= 2^40; 1 <= M_start;
+ * M_start + M_inc <= 2^40; M_inc < 2^31; M_start*K - SL >= 2 (every N + x >= 2).
+ *
+ * Errors: every call returns a cs_status (0 = CS_OK, negative = error) and
+ * never throws; cs_last_error() gives a message for the calling thread.  A
+ * device error inside cs_sieve is sticky for that plan.
+ *
+ * Threads: a plan may be used by one thread at a time; distinct plans are
+ * independent.  All device work of a plan is enqueued on the stream given to
+ * cs_sieve; the caller may overlap several plans on several streams.
+ */
+#ifndef COMBSIEVE_H
+#define COMBSIEVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cs_plan_s *cs_plan_t;
+typedef int cs_status;
+
+#define CS_OK 0
+#define CS_EINVAL (-1)     /* parameter outside the limits above, or a bad argument */
+#define CS_ENOMEM (-2)     /* host or device allocation failed */
+#define CS_EDEVICE (-3)    /* a CUDA call failed; see cs_last_error() */
+#define CS_ETIMEOUT (-4)   /* a bounded device wait gave up */
+#define CS_ESTATE (-5)     /* call out of order, e.g. fetching before cs_sieve */
+#define CS_ESIZE (-6)      /* caller buffer too small */
+#define CS_EOVERFLOW (-7)  /* an internal device buffer overflowed (result invalid) */
+#define CS_EAGAIN (-8)     /* admission refused (no free slot or memory) */
+
+/* Tuning knobs.  A zeroed struct (or NULL) selects the defaults.  None of
+ * them changes the output; they only move work between kernels. */
+typedef struct {
+    uint64_t threshold;      /* T: primes P < p <= T take the small-prime tile
+                                sieve, T < p <= L the large-prime walk (Section
+                                3.2's threshold, "naively p > 10 S").  Must be
+                                >= 2*SL and <= 2^30 when given.  0 = automatic. */
+    uint32_t tile_rows;      /* rows per small-prime tile: 1, 2, 4, 8, 16 or 32; 0 = auto */
+    uint32_t large_mode;     /* 1 = one G solve per hit, as in Section 3.2;
+                                2 = three-gap stepping (two extra solves per prime,
+                                then O(1) per hit); 0 = automatic (2) */
+    uint32_t no_wheel;       /* 1 = do not clear x with q | N + x for primes q | d */
+    uint32_t large_grid;     /* CTAs of the large-prime kernel; 0 = automatic */
+    uint64_t chunk_numbers;  /* width of one large-prime chunk of (T, L]; 0 = automatic */
+    uint32_t profile;        /* 1 = time each kernel with CUDA events (cs_kernel_times) */
+    uint32_t reserved[7];
+} cs_tuning;
+
+typedef struct {
+    uint64_t M_c;              /* rows */
+    uint64_t W;                /* columns */
+    uint64_t words_per_row;    /* ceil(W / 64) */
+    uint64_t bitset_bytes;     /* M_c * words_per_row * 8 */
+    uint64_t S;                /* 2*SL + 1 */
+    uint64_t threshold;        /* effective T */
+    uint32_t tile_rows;
+    uint32_t large_mode;
+    uint32_t narrow;           /* 1: all large primes < 2^30 (32-bit kernels) */
+    uint32_t wheel;
+    uint64_t n_large_chunks;
+    uint64_t launches_per_sieve;  /* kernels one cs_sieve launches */
+    uint64_t h2d_bytes;        /* bytes uploaded by cs_plan */
+    uint64_t device_bytes;     /* device memory held by the plan */
+} cs_info_t;
+
+typedef struct {
+    uint64_t F;                /* enumerated factors (F_small + F_large) */
+    uint64_t F_small;
+    uint64_t F_large;
+    uint64_t solves;           /* G solves of Eq. modeq in the large-prime walk */
+    uint64_t levels;           /* passes through G's case analysis */
+    uint64_t hits_all;         /* large-prime hits before the coprime-m / stored-x filters */
+    uint64_t n_small_primes;
+    uint64_t n_large_primes;
+    uint64_t survivors;        /* set bits in the bitset */
+    uint64_t hash;
+} cs_stats_t;
+
+/* Builds a sieve instance: validates the parameters, computes the row and
+ * column maps and K's factor words on the host, allocates the device bitset and
+ * work buffers (owned by the plan) and uploads the tables.  tune may be NULL.
+ * On success *out is a new plan; on error *out is NULL. */
+cs_status cs_plan(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL,
+                  uint64_t L, const cs_tuning *tune, cs_plan_t *out);
+
+/* Enqueues the whole sieve on `stream` (a cudaStream_t; NULL = the legacy
+ * default stream) and returns without waiting: prime generation (P, L], K mod p
+ * (Section 3.1), the small-prime tile sieve, the large-prime walk (Sections
+ * 3.2-3.3), per-row counts and the checksum.  May be called again to recompute. */
+cs_status cs_sieve(cs_plan_t plan, void *stream);
+
+/* Waits for the last cs_sieve of this plan and returns its device status:
+ * CS_OK, CS_EOVERFLOW (an internal buffer overflowed), CS_EDEVICE. */
+cs_status cs_sync(cs_plan_t plan);
+
+cs_status cs_info(cs_plan_t plan, cs_info_t *out);
+
+/* Copies the bitset (M_c * words_per_row uint64 words, row-major) to host
+ * memory owned by the caller.  n_words must be at least that.  Waits for the
+ * plan's last cs_sieve. */
+cs_status cs_fetch_bitset(cs_plan_t plan, uint64_t *host, size_t n_words);
+
+/* Per-row survivor counts (n_rows >= M_c uint32, may be NULL), F and hash
+ * (either may be NULL), copied to caller-owned host memory.  Waits. */
+cs_status cs_counts(cs_plan_t plan, uint32_t *per_row, size_t n_rows, uint64_t *F, uint64_t *hash);
+
+/* Device counters of the last cs_sieve.  Waits. */
+cs_status cs_stats(cs_plan_t plan, cs_stats_t *out);
+
+/* The plan's row map (m of each row) and column map (x of each column). */
+cs_status cs_rows(cs_plan_t plan, uint64_t *m_of_row, size_t n);
+cs_status cs_columns(cs_plan_t plan, int64_t *x_of_col, size_t n);
+
+/* Borrowed device pointer to the bitset; valid until cs_destroy. */
+const void *cs_device_bitset(cs_plan_t plan);
+
+/* Kernel timings of the last cs_sieve (profile = 1 only), in milliseconds,
+ * per kernel class: [0] small-prime generation, [1] tile sieve, [2] large-prime
+ * generation, [3] large-prime walk, [4] counts/checksum; launches[i] = launches
+ * of that class.  Waits. */
+cs_status cs_kernel_times(cs_plan_t plan, double ms[5], uint64_t launches[5]);
+
+/* Frees the plan and its device memory (waits for its work first). */
+cs_status cs_destroy(cs_plan_t plan);
+
+/* Message for the last error on the calling thread ("" if none). */
+const char *cs_last_error(void);
+
+/* ---- single steps of the path, on caller-owned DEVICE buffers ---------- */
+
+/* Primes p with lo < p <= hi (hi <= 2^40), unordered, into out[0 .. cap).
+ * *count (host) receives the number found; CS_EOVERFLOW if more than cap.
+ * Synchronises `stream`. */
+cs_status cs_primes(uint64_t lo, uint64_t hi, uint64_t *out, uint64_t cap, uint64_t *count,
+                    void *stream);
+
+/* r[i] = K mod p[i] for K = P#/d (Section 3.1), for odd p[i] > P, p[i] < 2^40.
+ * Montgomery arithmetic with R = 2^32 when p < 2^31, else R = 2^64.
+ * Synchronises `stream`. */
+cs_status cs_k_mod_p(uint32_t P, uint64_t d, const uint64_t *p, uint64_t n, uint64_t *r,
+                     void *stream);
+
+/* m[i] = G(p[i], K[i], L[i], R[i]) of Section 3.3 (Eq. modfunc): the smallest
+ * m >= 0 with L <= m*K mod p <= R.  Requires 0 <= L <= R < p < 2^40,
+ * gcd(K, p) = 1; narrow = 1 uses 32-bit arithmetic and needs p < 2^30.
+ * Entries with K = 0 mod p get m = 2^64 - 1.  Synchronises `stream`. */
+cs_status cs_modsolve(const uint64_t *p, const uint64_t *K, const uint64_t *L, const uint64_t *R,
+                      uint64_t *m, uint64_t n, int narrow, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* COMBSIEVE_H */

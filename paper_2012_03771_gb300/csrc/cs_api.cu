@@ -1,0 +1,705 @@
+// Host side of the C ABI: parameter validation, the row / column maps, K's
+// factor words, device memory and the order of kernel launches for one sieve.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/combsieve.h"
+#include "cs_arith.cuh"
+#include "cs_internal.h"
+
+using namespace cs;
+
+namespace {
+
+thread_local std::string g_err;
+
+cs_status fail(cs_status code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+cs_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(e == cudaErrorMemoryAllocation ? CS_ENOMEM : CS_EDEVICE,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CS_CUDA(call)                                  \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+constexpr uint64_t MAX_P = 1ull << 20;
+constexpr uint64_t MAX_SL = 1ull << 20;
+constexpr uint64_t MAX_L = 1ull << 40;
+constexpr uint64_t MAX_M = 1ull << 40;
+constexpr uint64_t MAX_T = 1ull << 30;
+constexpr uint64_t NARROW_LIMIT = 1ull << 30;
+
+std::vector<uint32_t> primes_upto(uint64_t n) {
+    std::vector<uint32_t> out;
+    if (n < 2) return out;
+    std::vector<uint8_t> comp(n + 1, 0);
+    for (uint64_t i = 2; i <= n; i++) {
+        if (comp[i]) continue;
+        out.push_back((uint32_t)i);
+        for (uint64_t j = i * i; j <= n; j += i) comp[j] = 1;
+    }
+    return out;
+}
+
+uint64_t isqrt_u64(uint64_t n) {
+    uint64_t r = (uint64_t)sqrt((double)n);
+    while (r * r > n) r--;
+    while ((r + 1) * (r + 1) <= n) r++;
+    return r;
+}
+
+// Upper bound on the number of primes in any interval of length y (y >= 2):
+// pi(x + y) - pi(x) <= 2y / log y (Montgomery and Vaughan, "The large sieve",
+// Mathematika 20, 1973), plus slack.
+uint64_t primes_in_interval_bound(uint64_t y) {
+    if (y < 64) return 64;
+    return (uint64_t)(2.0 * (double)y / log((double)y)) + 1024;
+}
+
+// pi(x) < 1.25506 x / log x for x > 1 (Rosser and Schoenfeld, 1962), plus slack.
+uint64_t prime_count_bound(uint64_t x) {
+    if (x < 64) return 64;
+    return (uint64_t)(1.25506 * (double)x / log((double)x)) + 1024;
+}
+
+enum KernelClass { KC_GEN_SMALL = 0, KC_TILE, KC_GEN_LARGE, KC_LARGE, KC_FINAL, KC_N };
+
+}  // namespace
+
+struct cs_plan_s {
+    // parameters
+    uint32_t P = 0;
+    uint64_t d = 0, M_start = 0, M_inc = 0, L = 0;
+    uint32_t SL = 0;
+    cs_tuning tune{};
+    // derived
+    uint64_t M_c = 0, W = 0, wpr = 0, S = 0, S32 = 0, T = 0, small_hi = 0;
+    bool narrow = true, wheel = true;
+    int mode = LARGE_THREE_GAP;
+    std::vector<uint64_t> m_of_row;
+    std::vector<int64_t> x_of_col;
+    std::vector<std::pair<uint64_t, uint64_t>> chunks;    // large-prime ranges (lo, hi]
+    uint64_t large_cap = 0, small_cap = 0;
+    int large_grid = 0;
+    uint64_t h2d = 0, dev_bytes = 0;
+    // device
+    DevPlan dp{};
+    TileConfig tc{};
+    std::vector<void *> allocs;
+    uint32_t *d_base = nullptr;
+    uint32_t n_base = 0;
+    SmallPrime *d_small = nullptr;
+    void *d_lp = nullptr, *d_lr = nullptr, *d_lv = nullptr;
+    unsigned long long *d_counts = nullptr;   // [0] small count, [1..] per-chunk counts
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    bool sieved = false;
+    cs_status sticky = CS_OK;
+    // profiling
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[KC_N];
+    size_t prof_used[KC_N] = {0, 0, 0, 0, 0};
+
+    ~cs_plan_s() {
+        if (done) cudaEventDestroy(done);
+        for (int k = 0; k < KC_N; k++)
+            for (auto &e : prof_ev[k]) {
+                cudaEventDestroy(e.first);
+                cudaEventDestroy(e.second);
+            }
+        for (void *p : allocs) cudaFree(p);
+    }
+
+    template <class T>
+    cs_status dalloc(T **p, size_t count) {
+        size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+        cudaError_t e = cudaMalloc((void **)p, bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+        allocs.push_back(*p);
+        dev_bytes += bytes;
+        return CS_OK;
+    }
+    template <class T>
+    cs_status upload(T **p, const std::vector<T> &v) {
+        cs_status s = dalloc(p, v.size());
+        if (s) return s;
+        if (!v.empty()) {
+            cudaError_t e = cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy H2D");
+            h2d += v.size() * sizeof(T);
+        }
+        return CS_OK;
+    }
+};
+
+namespace {
+
+// factor d over the primes <= P; returns false if d is not squarefree or has a
+// prime factor above P
+bool split_primes(uint32_t P, uint64_t d, std::vector<uint32_t> &qK, std::vector<uint32_t> &qd) {
+    std::vector<uint32_t> pr = primes_upto(P);
+    uint64_t rest = d;
+    for (uint32_t q : pr) {
+        if (rest % q == 0) {
+            rest /= q;
+            if (rest % q == 0) return false;
+            qd.push_back(q);
+        } else {
+            qK.push_back(q);
+        }
+    }
+    return rest == 1;
+}
+
+cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc,
+                     uint32_t SL, uint64_t L, const cs_tuning *tune) {
+    if (d == 0 || P > MAX_P) return fail(CS_EINVAL, "d must be >= 1 and P <= 2^20");
+    if (SL > MAX_SL) return fail(CS_EINVAL, "SL must be <= 2^20");
+    if (L > MAX_L) return fail(CS_EINVAL, "L must be <= 2^40");
+    if (M_start < 1 || M_start > MAX_M || M_inc > MAX_M - M_start)
+        return fail(CS_EINVAL, "need 1 <= M_start and M_start + M_inc <= 2^40");
+    if (M_inc >= (1ull << 31)) return fail(CS_EINVAL, "M_inc must be < 2^31");
+    std::vector<uint32_t> qK, qd;
+    if (!split_primes(P, d, qK, qd)) return fail(CS_EINVAL, "d must be squarefree and divide P#");
+
+    pl->P = P; pl->d = d; pl->M_start = M_start; pl->M_inc = M_inc; pl->SL = SL; pl->L = L;
+    if (tune) pl->tune = *tune;
+    pl->wheel = !pl->tune.no_wheel;
+
+    // K as 32- and 64-bit factor words; K itself when it fits in 64 bits
+    std::vector<uint32_t> kch32;
+    std::vector<uint64_t> kch64;
+    {
+        uint64_t acc = 1;
+        for (uint32_t q : qK) {
+            if (acc > 0xffffffffull / q) { kch32.push_back((uint32_t)acc); acc = 1; }
+            acc *= q;
+        }
+        if (acc > 1) kch32.push_back((uint32_t)acc);
+        unsigned __int128 a64 = 1;
+        for (uint32_t q : qK) {
+            if (a64 * q > (unsigned __int128)UINT64_MAX) { kch64.push_back((uint64_t)a64); a64 = 1; }
+            a64 *= q;
+        }
+        if (a64 > 1) kch64.push_back((uint64_t)a64);
+    }
+    bool k_fits = kch64.size() <= 1;
+    uint64_t K64 = kch64.empty() ? 1 : kch64[0];
+    if (k_fits) {
+        unsigned __int128 lo = (unsigned __int128)M_start * K64;
+        if (lo < (unsigned __int128)SL + 2) return fail(CS_EINVAL, "need M_start*K - SL >= 2");
+    }
+    bool small_n = false;
+    if (k_fits) {
+        unsigned __int128 lowest = (unsigned __int128)M_start * K64 - SL;
+        small_n = lowest <= (unsigned __int128)std::max<uint64_t>(L, P);
+    }
+
+    // columns: x in [-SL, SL] with gcd(|x|, K) = 1 (x = 0 only for K = 1)
+    const uint64_t S = 2ull * SL + 1, S32 = (S + 31) / 32;
+    std::vector<uint8_t> stored(S, 1);
+    for (uint32_t q : qK) {
+        // multiples of q in [-SL, SL] (x = 0 included)
+        int64_t first = -(int64_t)(SL / q) * q;
+        for (int64_t x = first; x <= (int64_t)SL; x += q) stored[x + SL] = 0;
+    }
+    std::vector<uint32_t> col_mask(S32, 0), col_prefix(S32, 0), raw_of_col;
+    for (uint64_t z = 0; z < S; z++)
+        if (stored[z]) {
+            col_mask[z >> 5] |= 1u << (z & 31);
+            raw_of_col.push_back((uint32_t)z);
+            pl->x_of_col.push_back((int64_t)z - SL);
+        }
+    for (uint64_t w = 0, c = 0; w < S32; w++) {
+        col_prefix[w] = (uint32_t)c;
+        c += __builtin_popcount(col_mask[w]);
+    }
+    const uint64_t W = raw_of_col.size(), wpr = (W + 63) / 64;
+
+    // rows: m coprime to d
+    std::vector<uint32_t> moff_of_row;
+    std::vector<int32_t> row_of_moff(M_inc, -1);
+    {
+        std::vector<uint64_t> rem(qd.size());
+        for (size_t i = 0; i < qd.size(); i++) rem[i] = M_start % qd[i];
+        for (uint64_t k = 0; k < M_inc; k++) {
+            bool ok = true;
+            for (size_t i = 0; i < qd.size(); i++) {
+                if (rem[i] == 0) ok = false;
+                if (++rem[i] == qd[i]) rem[i] = 0;
+            }
+            if (ok) {
+                row_of_moff[k] = (int32_t)moff_of_row.size();
+                moff_of_row.push_back((uint32_t)k);
+                pl->m_of_row.push_back(M_start + k);
+            }
+        }
+    }
+    const uint64_t M_c = moff_of_row.size();
+
+    // wheel tables: for each q | d, pattern[k] = bits i < 32 with (k + i) % q == 0
+    std::vector<uint32_t> wq, wkmod, woff, wpat;
+    if (pl->wheel) {
+        for (uint32_t q : qd) {
+            uint64_t km = 1;
+            for (uint32_t f : qK) km = km * f % q;
+            wq.push_back(q);
+            wkmod.push_back((uint32_t)km);
+            woff.push_back((uint32_t)wpat.size());
+            for (uint32_t k = 0; k < q; k++) {
+                uint32_t b = 0;
+                for (uint32_t i = 0; i < 32; i++)
+                    if ((k + i) % q == 0) b |= 1u << i;
+                wpat.push_back(b);
+            }
+        }
+    }
+
+    // small / large threshold and work split
+    pl->mode = pl->tune.large_mode == 1 ? LARGE_PAPER : LARGE_THREE_GAP;
+    uint64_t T = pl->tune.threshold;
+    if (T) {
+        if (T < 2ull * SL || T > MAX_T)
+            return fail(CS_EINVAL, "threshold must satisfy 2*SL <= T <= 2^30");
+    } else {
+        uint64_t mult = pl->mode == LARGE_PAPER ? 100 : 8;
+        T = std::min<uint64_t>(std::max<uint64_t>(mult * S, 1u << 16), MAX_T);
+    }
+    // the large-prime walk needs p > 2*SL (at most one hit per interval)
+    T = std::max<uint64_t>({T, 2ull * SL, (uint64_t)P, 2});
+    pl->T = T;
+    pl->small_hi = std::min<uint64_t>(T, L);
+    pl->narrow = L < NARROW_LIMIT;
+
+    uint64_t chunk = pl->tune.chunk_numbers ? pl->tune.chunk_numbers : (1ull << 27);
+    if (L > T) {
+        for (uint64_t lo = T; lo < L; lo += chunk) pl->chunks.push_back({lo, std::min(L, lo + chunk)});
+    }
+    pl->large_cap = pl->chunks.empty() ? 0 : primes_in_interval_bound(std::min(chunk, L - T));
+    pl->small_cap = pl->small_hi > P ? prime_count_bound(pl->small_hi) : 0;
+    pl->large_grid = pl->tune.large_grid ? (int)pl->tune.large_grid : sm_count() * 8;
+
+    // tile shape: up to 32 rows of raw offsets in shared memory
+    int dev = 0, optin = 0;
+    CS_CUDA(cudaGetDevice(&dev));
+    CS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const uint64_t budget = std::min<uint64_t>((uint64_t)optin, 200 * 1024) / 4;   // words
+    std::vector<uint32_t> chunk_tab;
+    uint32_t TR = pl->tune.tile_rows;
+    if (TR && (TR > 32 || (TR & (TR - 1)))) return fail(CS_EINVAL, "tile_rows must be 1..32, a power of 2");
+    auto words_of = [&](uint64_t j0, uint64_t j1) -> uint64_t {
+        if (j1 <= j0) return 1;
+        uint64_t z0 = raw_of_col[j0], z1 = raw_of_col[j1 - 1] + 1;
+        return (z1 - (z0 & ~31ull) + 31) / 32;
+    };
+    uint64_t full_words = W ? words_of(0, W) : 1;
+    if (!TR) {
+        TR = 32;
+        while (TR > 1 && (uint64_t)(TR + 1) * full_words > budget) TR /= 2;
+    }
+    uint64_t max_words_per_chunk = budget / (TR + 1);
+    if (max_words_per_chunk < 64) return fail(CS_EINVAL, "tile_rows too large for shared memory");
+    uint32_t max_words = 1;
+    if (W == 0) {
+        chunk_tab = {0, 0, 0, 0};
+    } else {
+        uint64_t j0 = 0;
+        while (j0 < W) {
+            uint64_t j1 = std::min<uint64_t>(W, j0 + 64);
+            while (j1 < W) {
+                uint64_t nj = std::min<uint64_t>(W, j1 + 64);
+                if (words_of(j0, nj) > max_words_per_chunk) break;
+                j1 = nj;
+            }
+            uint64_t z0 = raw_of_col[j0], z1 = raw_of_col[j1 - 1] + 1;
+            chunk_tab.insert(chunk_tab.end(), {(uint32_t)j0, (uint32_t)j1, (uint32_t)z0, (uint32_t)z1});
+            max_words = std::max<uint32_t>(max_words, (uint32_t)words_of(j0, j1));
+            j0 = j1;
+        }
+    }
+
+    pl->M_c = M_c; pl->W = W; pl->wpr = wpr; pl->S = S; pl->S32 = S32;
+
+    // device memory and tables
+    DevPlan &dp = pl->dp;
+    dp.M_start = M_start; dp.M_inc = M_inc; dp.M_c = M_c;
+    dp.SL = SL; dp.S = (uint32_t)S; dp.S32 = (uint32_t)S32;
+    dp.W = (uint32_t)W; dp.wpr = (uint32_t)wpr;
+    dp.P = P; dp.L = L; dp.T = T;
+    dp.small_n = small_n; dp.K64 = K64;
+    cs_status s;
+    uint32_t *d_kch32; uint64_t *d_kch64;
+    if ((s = pl->upload(&d_kch32, kch32))) return s;
+    if ((s = pl->upload(&d_kch64, kch64))) return s;
+    dp.kch32 = d_kch32; dp.n_kch32 = (uint32_t)kch32.size();
+    dp.kch64 = d_kch64; dp.n_kch64 = (uint32_t)kch64.size();
+    uint32_t *d_mask, *d_prefix, *d_raw, *d_moff; int32_t *d_rowof;
+    if ((s = pl->upload(&d_mask, col_mask))) return s;
+    if ((s = pl->upload(&d_prefix, col_prefix))) return s;
+    if ((s = pl->upload(&d_raw, raw_of_col))) return s;
+    if ((s = pl->upload(&d_moff, moff_of_row))) return s;
+    if ((s = pl->upload(&d_rowof, row_of_moff))) return s;
+    dp.col_mask = d_mask; dp.col_prefix = d_prefix; dp.raw_of_col = d_raw;
+    dp.moff_of_row = d_moff; dp.row_of_moff = d_rowof;
+    uint32_t *d_wq, *d_wk, *d_wo, *d_wp;
+    if ((s = pl->upload(&d_wq, wq))) return s;
+    if ((s = pl->upload(&d_wk, wkmod))) return s;
+    if ((s = pl->upload(&d_wo, woff))) return s;
+    if ((s = pl->upload(&d_wp, wpat))) return s;
+    dp.qd = d_wq; dp.qd_kmod = d_wk; dp.qd_pat_off = d_wo; dp.qd_pat = d_wp;
+    dp.n_qd = (uint32_t)wq.size();
+    uint64_t *d_bits; uint32_t *d_cnt; unsigned long long *d_stats;
+    if ((s = pl->dalloc(&d_bits, M_c * wpr))) return s;
+    if ((s = pl->dalloc(&d_cnt, M_c))) return s;
+    if ((s = pl->dalloc(&d_stats, ST_COUNT))) return s;
+    dp.bits = d_bits; dp.counts = d_cnt; dp.stats = d_stats;
+
+    // base primes (odd) <= sqrt(L) for the segmented generator
+    std::vector<uint32_t> base;
+    for (uint32_t q : primes_upto(isqrt_u64(std::max<uint64_t>(L, T)) + 1))
+        if (q != 2) base.push_back(q);
+    if ((s = pl->upload(&pl->d_base, base))) return s;
+    pl->n_base = (uint32_t)base.size();
+
+    uint32_t *d_chunk;
+    if ((s = pl->upload(&d_chunk, chunk_tab))) return s;
+    pl->tc.rows = TR;
+    pl->tc.n_chunks = (uint32_t)(chunk_tab.size() / 4);
+    pl->tc.chunk = d_chunk;
+    pl->tc.max_words = max_words;
+
+    if ((s = pl->dalloc(&pl->d_small, pl->small_cap))) return s;
+    if ((s = pl->dalloc(&pl->d_counts, 1 + pl->chunks.size()))) return s;
+    if (!pl->chunks.empty()) {
+        size_t el = pl->narrow ? 4 : 8;
+        uint8_t *a, *b, *c;
+        if ((s = pl->dalloc(&a, pl->large_cap * el))) return s;
+        if ((s = pl->dalloc(&b, pl->large_cap * el))) return s;
+        if ((s = pl->dalloc(&c, pl->large_cap * el))) return s;
+        pl->d_lp = a; pl->d_lr = b; pl->d_lv = c;
+    }
+    CS_CUDA(cudaEventCreateWithFlags(&pl->done, cudaEventDisableTiming));
+    return CS_OK;
+}
+
+cs_status wait_plan(cs_plan_t pl) {
+    if (!pl->sieved) return fail(CS_ESTATE, "cs_sieve has not been called on this plan");
+    if (pl->sticky) return pl->sticky;
+    cudaError_t e = cudaEventSynchronize(pl->done);
+    if (e != cudaSuccess) {
+        pl->sticky = cuda_fail(e, "cudaEventSynchronize");
+        return pl->sticky;
+    }
+    return CS_OK;
+}
+
+struct Prof {
+    cs_plan_t pl;
+    cudaStream_t st;
+    bool on;
+    cudaEvent_t end_ev = nullptr;
+    int cls = -1;
+    cs_status begin(int k) {
+        if (!on) return CS_OK;
+        auto &v = pl->prof_ev[k];
+        size_t i = pl->prof_used[k]++;
+        if (i == v.size()) {
+            cudaEvent_t a, b;
+            CS_CUDA(cudaEventCreate(&a));
+            CS_CUDA(cudaEventCreate(&b));
+            v.push_back({a, b});
+        }
+        CS_CUDA(cudaEventRecord(v[i].first, st));
+        end_ev = v[i].second;
+        return CS_OK;
+    }
+    cs_status end() {
+        if (!on) return CS_OK;
+        CS_CUDA(cudaEventRecord(end_ev, st));
+        return CS_OK;
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+cs_status cs_plan(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL,
+                  uint64_t L, const cs_tuning *tune, cs_plan_t *out) {
+    if (!out) return fail(CS_EINVAL, "out is NULL");
+    *out = nullptr;
+    cs_plan_s *pl = new (std::nothrow) cs_plan_s();
+    if (!pl) return fail(CS_ENOMEM, "host allocation failed");
+    cs_status s;
+    try {
+        s = build_plan(pl, P, d, M_start, M_inc, SL, L, tune);
+    } catch (const std::bad_alloc &) {
+        s = fail(CS_ENOMEM, "host allocation failed");
+    }
+    if (s) {
+        delete pl;
+        return s;
+    }
+    *out = pl;
+    g_err.clear();
+    return CS_OK;
+}
+
+cs_status cs_sieve(cs_plan_t pl, void *stream) {
+    if (!pl) return fail(CS_EINVAL, "plan is NULL");
+    if (pl->sticky) return pl->sticky;
+    cudaStream_t st = (cudaStream_t)stream;
+    pl->stream = st;
+    const DevPlan &dp = pl->dp;
+    Prof prof{pl, st, pl->tune.profile != 0};
+    for (int k = 0; k < KC_N; k++) pl->prof_used[k] = 0;
+    CS_CUDA(cudaMemsetAsync(dp.stats, 0, ST_COUNT * sizeof(unsigned long long), st));
+    CS_CUDA(cudaMemsetAsync(pl->d_counts, 0, (1 + pl->chunks.size()) * sizeof(unsigned long long), st));
+    cs_status s;
+    if (pl->small_hi > pl->P) {
+        if ((s = prof.begin(KC_GEN_SMALL))) return s;
+        CS_CUDA(launch_gen_small(dp, pl->P, pl->small_hi, pl->d_base, pl->n_base, pl->d_small,
+                                 pl->small_cap, pl->d_counts, st));
+        if ((s = prof.end())) return s;
+    }
+    if ((s = prof.begin(KC_TILE))) return s;
+    CS_CUDA(launch_tile(dp, pl->tc, pl->d_small, pl->d_counts, pl->small_cap, st));
+    if ((s = prof.end())) return s;
+    for (size_t c = 0; c < pl->chunks.size(); c++) {
+        unsigned long long *cnt = pl->d_counts + 1 + c;
+        if ((s = prof.begin(KC_GEN_LARGE))) return s;
+        CS_CUDA(launch_gen_large(dp, pl->narrow, pl->chunks[c].first, pl->chunks[c].second,
+                                 pl->d_base, pl->n_base, pl->d_lp, pl->d_lr, pl->d_lv,
+                                 pl->large_cap, cnt, st));
+        if ((s = prof.end())) return s;
+        if ((s = prof.begin(KC_LARGE))) return s;
+        CS_CUDA(launch_large(dp, pl->narrow, pl->mode, pl->d_lp, pl->d_lr, pl->d_lv, cnt,
+                             pl->large_cap, pl->large_grid, st));
+        if ((s = prof.end())) return s;
+    }
+    if ((s = prof.begin(KC_FINAL))) return s;
+    CS_CUDA(launch_final(dp, st));
+    if ((s = prof.end())) return s;
+    CS_CUDA(cudaEventRecord(pl->done, st));
+    pl->sieved = true;
+    return CS_OK;
+}
+
+cs_status cs_sync(cs_plan_t pl) {
+    if (!pl) return fail(CS_EINVAL, "plan is NULL");
+    cs_status s = wait_plan(pl);
+    if (s) return s;
+    unsigned long long err = 0;
+    CS_CUDA(cudaMemcpy(&err, pl->dp.stats + ST_ERROR, sizeof(err), cudaMemcpyDeviceToHost));
+    if (err & ERR_PRIME_OVERFLOW) return fail(CS_EOVERFLOW, "prime buffer overflow");
+    if (err & ERR_SOLVER_LIMIT) return fail(CS_EDEVICE, "modular solver exceeded its pass bound");
+    return CS_OK;
+}
+
+cs_status cs_info(cs_plan_t pl, cs_info_t *out) {
+    if (!pl || !out) return fail(CS_EINVAL, "NULL argument");
+    memset(out, 0, sizeof(*out));
+    out->M_c = pl->M_c;
+    out->W = pl->W;
+    out->words_per_row = pl->wpr;
+    out->bitset_bytes = pl->M_c * pl->wpr * 8;
+    out->S = pl->S;
+    out->threshold = pl->T;
+    out->tile_rows = pl->tc.rows;
+    out->large_mode = (uint32_t)pl->mode;
+    out->narrow = pl->narrow;
+    out->wheel = pl->wheel;
+    out->n_large_chunks = pl->chunks.size();
+    out->launches_per_sieve = (pl->small_hi > pl->P ? 1 : 0) + (pl->M_c && pl->W ? 1 : 0) +
+                              (pl->M_c ? 1 : 0) + 2 * pl->chunks.size();
+    out->h2d_bytes = pl->h2d;
+    out->device_bytes = pl->dev_bytes;
+    return CS_OK;
+}
+
+cs_status cs_fetch_bitset(cs_plan_t pl, uint64_t *host, size_t n_words) {
+    if (!pl) return fail(CS_EINVAL, "plan is NULL");
+    const uint64_t need = pl->M_c * pl->wpr;
+    if (need && !host) return fail(CS_EINVAL, "host is NULL");
+    if (n_words < need) return fail(CS_ESIZE, "host buffer smaller than M_c * words_per_row");
+    cs_status s = wait_plan(pl);
+    if (s) return s;
+    if (need) {
+        CS_CUDA(cudaMemcpyAsync(host, pl->dp.bits, need * 8, cudaMemcpyDeviceToHost, pl->stream));
+        CS_CUDA(cudaStreamSynchronize(pl->stream));
+    }
+    return CS_OK;
+}
+
+cs_status cs_counts(cs_plan_t pl, uint32_t *per_row, size_t n_rows, uint64_t *F, uint64_t *hash) {
+    if (!pl) return fail(CS_EINVAL, "plan is NULL");
+    if (per_row && n_rows < pl->M_c) return fail(CS_ESIZE, "per_row smaller than M_c");
+    cs_status s = wait_plan(pl);
+    if (s) return s;
+    unsigned long long st[ST_COUNT];
+    CS_CUDA(cudaMemcpyAsync(st, pl->dp.stats, sizeof(st), cudaMemcpyDeviceToHost, pl->stream));
+    if (per_row && pl->M_c)
+        CS_CUDA(cudaMemcpyAsync(per_row, pl->dp.counts, pl->M_c * 4, cudaMemcpyDeviceToHost, pl->stream));
+    CS_CUDA(cudaStreamSynchronize(pl->stream));
+    if (F) *F = st[ST_F_SMALL] + st[ST_F_LARGE];
+    if (hash) *hash = st[ST_HASH];
+    return CS_OK;
+}
+
+cs_status cs_stats(cs_plan_t pl, cs_stats_t *out) {
+    if (!pl || !out) return fail(CS_EINVAL, "NULL argument");
+    cs_status s = wait_plan(pl);
+    if (s) return s;
+    unsigned long long st[ST_COUNT];
+    unsigned long long cnt[1];
+    CS_CUDA(cudaMemcpy(st, pl->dp.stats, sizeof(st), cudaMemcpyDeviceToHost));
+    CS_CUDA(cudaMemcpy(cnt, pl->d_counts, sizeof(cnt), cudaMemcpyDeviceToHost));
+    std::vector<unsigned long long> lc(pl->chunks.size());
+    if (!lc.empty())
+        CS_CUDA(cudaMemcpy(lc.data(), pl->d_counts + 1, lc.size() * 8, cudaMemcpyDeviceToHost));
+    memset(out, 0, sizeof(*out));
+    out->F_small = st[ST_F_SMALL];
+    out->F_large = st[ST_F_LARGE];
+    out->F = out->F_small + out->F_large;
+    out->solves = st[ST_SOLVES];
+    out->levels = st[ST_LEVELS];
+    out->hits_all = st[ST_HITS_ALL];
+    out->n_small_primes = std::min<uint64_t>(cnt[0], pl->small_cap);
+    for (auto c : lc) out->n_large_primes += c;
+    out->survivors = st[ST_SURVIVORS];
+    out->hash = st[ST_HASH];
+    return CS_OK;
+}
+
+cs_status cs_rows(cs_plan_t pl, uint64_t *m_of_row, size_t n) {
+    if (!pl) return fail(CS_EINVAL, "plan is NULL");
+    if (n < pl->M_c) return fail(CS_ESIZE, "buffer smaller than M_c");
+    if (pl->M_c) memcpy(m_of_row, pl->m_of_row.data(), pl->M_c * 8);
+    return CS_OK;
+}
+
+cs_status cs_columns(cs_plan_t pl, int64_t *x_of_col, size_t n) {
+    if (!pl) return fail(CS_EINVAL, "plan is NULL");
+    if (n < pl->W) return fail(CS_ESIZE, "buffer smaller than W");
+    if (pl->W) memcpy(x_of_col, pl->x_of_col.data(), pl->W * 8);
+    return CS_OK;
+}
+
+const void *cs_device_bitset(cs_plan_t pl) { return pl ? (const void *)pl->dp.bits : nullptr; }
+
+cs_status cs_kernel_times(cs_plan_t pl, double ms[5], uint64_t launches[5]) {
+    if (!pl || !ms || !launches) return fail(CS_EINVAL, "NULL argument");
+    if (!pl->tune.profile) return fail(CS_ESTATE, "plan was built without profile = 1");
+    cs_status s = wait_plan(pl);
+    if (s) return s;
+    for (int k = 0; k < KC_N; k++) {
+        double tot = 0;
+        for (size_t i = 0; i < pl->prof_used[k]; i++) {
+            float t = 0;
+            CS_CUDA(cudaEventElapsedTime(&t, pl->prof_ev[k][i].first, pl->prof_ev[k][i].second));
+            tot += t;
+        }
+        ms[k] = tot;
+        launches[k] = pl->prof_used[k];
+    }
+    return CS_OK;
+}
+
+cs_status cs_destroy(cs_plan_t pl) {
+    if (!pl) return CS_OK;
+    if (pl->sieved && pl->done) cudaEventSynchronize(pl->done);
+    delete pl;
+    return CS_OK;
+}
+
+const char *cs_last_error(void) { return g_err.c_str(); }
+
+cs_status cs_primes(uint64_t lo, uint64_t hi, uint64_t *out, uint64_t cap, uint64_t *count,
+                    void *stream) {
+    if (hi > MAX_L) return fail(CS_EINVAL, "hi must be <= 2^40");
+    if (!count) return fail(CS_EINVAL, "count is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    *count = 0;
+    if (hi <= lo || hi < 2) return CS_OK;
+    std::vector<uint32_t> base;
+    for (uint32_t q : primes_upto(isqrt_u64(hi) + 1))
+        if (q != 2) base.push_back(q);
+    uint32_t *d_base = nullptr;
+    unsigned long long *d_cnt = nullptr;
+    CS_CUDA(cudaMalloc(&d_base, std::max<size_t>(base.size(), 1) * 4));
+    cudaError_t e = cudaMalloc(&d_cnt, 16);
+    if (e == cudaSuccess && !base.empty())
+        e = cudaMemcpyAsync(d_base, base.data(), base.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, 16, st);
+    if (e == cudaSuccess) e = launch_gen_list(lo, hi, d_base, (uint32_t)base.size(), out, cap, d_cnt, d_cnt + 1, st);
+    unsigned long long h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d_cnt, 16, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_base);
+    cudaFree(d_cnt);
+    if (e != cudaSuccess) return cuda_fail(e, "cs_primes");
+    *count = h[0];
+    if (h[1] || h[0] > cap) return fail(CS_EOVERFLOW, "more primes than cap");
+    return CS_OK;
+}
+
+cs_status cs_k_mod_p(uint32_t P, uint64_t d, const uint64_t *p, uint64_t n, uint64_t *r, void *stream) {
+    if (d == 0 || P > MAX_P) return fail(CS_EINVAL, "bad P or d");
+    std::vector<uint32_t> qK, qd;
+    if (!split_primes(P, d, qK, qd)) return fail(CS_EINVAL, "d must be squarefree and divide P#");
+    std::vector<uint32_t> kch32;
+    std::vector<uint64_t> kch64;
+    uint64_t acc = 1;
+    for (uint32_t q : qK) {
+        if (acc > 0xffffffffull / q) { kch32.push_back((uint32_t)acc); acc = 1; }
+        acc *= q;
+    }
+    if (acc > 1) kch32.push_back((uint32_t)acc);
+    unsigned __int128 a64 = 1;
+    for (uint32_t q : qK) {
+        if (a64 * q > (unsigned __int128)UINT64_MAX) { kch64.push_back((uint64_t)a64); a64 = 1; }
+        a64 *= q;
+    }
+    if (a64 > 1) kch64.push_back((uint64_t)a64);
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t *d32 = nullptr;
+    uint64_t *d64 = nullptr;
+    CS_CUDA(cudaMalloc(&d32, std::max<size_t>(kch32.size(), 1) * 4));
+    cudaError_t e = cudaMalloc(&d64, std::max<size_t>(kch64.size(), 1) * 8);
+    if (e == cudaSuccess && !kch32.empty())
+        e = cudaMemcpyAsync(d32, kch32.data(), kch32.size() * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !kch64.empty())
+        e = cudaMemcpyAsync(d64, kch64.data(), kch64.size() * 8, cudaMemcpyHostToDevice, st);
+    DevPlan dp{};
+    dp.kch32 = d32; dp.n_kch32 = (uint32_t)kch32.size();
+    dp.kch64 = d64; dp.n_kch64 = (uint32_t)kch64.size();
+    if (e == cudaSuccess) e = launch_kmodp(dp, p, n, r, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d32);
+    cudaFree(d64);
+    if (e != cudaSuccess) return cuda_fail(e, "cs_k_mod_p");
+    return CS_OK;
+}
+
+cs_status cs_modsolve(const uint64_t *p, const uint64_t *K, const uint64_t *L, const uint64_t *R,
+                      uint64_t *m, uint64_t n, int narrow, void *stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = launch_modsolve(p, K, L, R, m, n, narrow, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "cs_modsolve");
+    return CS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,196 @@
+// Integer arithmetic used by the Combined Sieve kernels.
+//
+// * Montgomery multiplication (P. L. Montgomery, "Modular multiplication
+//   without trial division", Math. Comp. 44, 1985) with R = 2^32 and R = 2^64,
+//   for the cached residues K mod p of Section 3.1.
+// * A stack-free form of the modular-equation solver G(p, K, L, R) of
+//   Section 3.3 (Eq. modsol).
+// * The SplitMix64 finaliser (Steele, Lea and Flood, 2014) for the bitset
+//   checksum.
+#pragma once
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define CS_HD __host__ __device__ __forceinline__
+#else
+#define CS_HD inline
+#endif
+
+namespace cs {
+
+CS_HD uint64_t mulhi64(uint64_t a, uint64_t b) {
+#if defined(__CUDA_ARCH__)
+    return __umul64hi(a, b);
+#else
+    return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+// ---------------------------------------------------------------- R = 2^32
+// -p^-1 mod 2^32 for odd p, by Newton's iteration x <- x(2 - p x); an odd p is
+// its own inverse mod 8, and every step doubles the number of correct bits.
+CS_HD uint32_t mont32_neg_inv(uint32_t p) {
+    uint32_t x = p;
+    x *= 2u - p * x;
+    x *= 2u - p * x;
+    x *= 2u - p * x;
+    x *= 2u - p * x;
+    return 0u - x;
+}
+
+// a * b * 2^-32 mod p, fully reduced.  Requires odd p < 2^31, a < p, b < 2^32.
+CS_HD uint32_t mont32_mul(uint32_t a, uint32_t b, uint32_t p, uint32_t pinv) {
+    uint64_t t = (uint64_t)a * b;
+    uint32_t m = (uint32_t)t * pinv;
+    uint64_t u = t + (uint64_t)m * p;   // divisible by 2^32, u < 2^64
+    uint32_t r = (uint32_t)(u >> 32);
+    return r >= p ? r - p : r;
+}
+
+// R mod p and R^2 mod p for R = 2^32.
+CS_HD uint32_t mont32_r1(uint32_t p) { return (0u - p) % p; }
+CS_HD uint32_t mont32_r2(uint32_t p) {
+    uint64_t r = mont32_r1(p);
+    return (uint32_t)((r * r) % p);
+}
+
+// R^e mod p given R mod p and R^2 mod p.  Under mont32_mul the residues
+// Y_j = R^(j+1) mod p form a monoid with Y_a * Y_b = Y_(a+b) and identity Y_0 = R,
+// so R^e = Y_1^(e-1) by square-and-multiply.  e >= 1.
+CS_HD uint32_t mont32_rpow(uint32_t e, uint32_t r1, uint32_t r2, uint32_t p, uint32_t pinv) {
+    uint32_t acc = r1, base = r2;
+    uint32_t k = e - 1;
+    while (k) {
+        if (k & 1) acc = mont32_mul(acc, base, p, pinv);
+        base = mont32_mul(base, base, p, pinv);
+        k >>= 1;
+    }
+    return acc;
+}
+
+// ---------------------------------------------------------------- R = 2^64
+CS_HD uint64_t mont64_neg_inv(uint64_t p) {
+    uint64_t x = p;
+    x *= 2u - p * x;
+    x *= 2u - p * x;
+    x *= 2u - p * x;
+    x *= 2u - p * x;
+    x *= 2u - p * x;
+    return 0ull - x;
+}
+
+// a * b * 2^-64 mod p, fully reduced.  Requires odd p < 2^62, a < p, b < 2^64.
+CS_HD uint64_t mont64_mul(uint64_t a, uint64_t b, uint64_t p, uint64_t pinv) {
+    uint64_t lo = a * b;
+    uint64_t hi = mulhi64(a, b);
+    uint64_t m = lo * pinv;
+    // lo + low64(m * p) == 0 (mod 2^64): the carry out of that sum is (lo != 0)
+    uint64_t r = hi + mulhi64(m, p) + (lo != 0);
+    return r >= p ? r - p : r;
+}
+
+CS_HD uint64_t mont64_r1(uint64_t p) { return (0ull - p) % p; }
+// R^2 mod p = R * 2^64 mod p by 64 modular doublings of R mod p (p < 2^63).
+CS_HD uint64_t mont64_r2(uint64_t p) {
+    uint64_t r = mont64_r1(p);
+    for (int i = 0; i < 64; i++) {
+        r <<= 1;
+        if (r >= p) r -= p;
+    }
+    return r;
+}
+
+CS_HD uint64_t mont64_rpow(uint32_t e, uint64_t r1, uint64_t r2, uint64_t p, uint64_t pinv) {
+    uint64_t acc = r1, base = r2;
+    uint32_t k = e - 1;
+    while (k) {
+        if (k & 1) acc = mont64_mul(acc, base, p, pinv);
+        base = mont64_mul(base, base, p, pinv);
+        k >>= 1;
+    }
+    return acc;
+}
+
+// --------------------------------------------------------------- division
+// Quotients of the solver's operands: 32-bit hardware-friendly division when
+// both operands fit in 32 bits, 64-bit otherwise.
+CS_HD uint32_t udiv(uint32_t a, uint32_t b) { return a / b; }
+CS_HD uint64_t udiv(uint64_t a, uint64_t b) {
+    if (((a | b) >> 32) == 0) return (uint32_t)a / (uint32_t)b;
+    return a / b;
+}
+
+// ----------------------------------------------------------- G(p, K, L, R)
+//
+// Smallest m >= 0 with L <= m*K mod p <= L + w (Eq. modfunc), for 0 < K < p,
+// gcd(K, p) = 1, 0 <= L and L + w < p.  Returns m and y = m*K mod p.
+//
+// Section 3.3 gives G as a recursion over five cases:
+//   a: L = 0                      -> 0
+//   C: ceil(L/K) <= floor(R/K)    -> ceil(L/K)
+//   D: 2K >= p                    -> G(p, p-K, p-R, p-L)
+//   E: otherwise                  -> ceil((L + p*G(K, -p mod K, L mod K, R mod K)) / K)
+// (case B, K >= p, is the caller's reduction K mod p).  Case E needs the inner
+// answer before it can finish, so a direct transcription keeps a stack.  This
+// version runs the same chain of sub-problems forwards and keeps, for the
+// current sub-problem (p_k, K_k), the two lattice vectors (U, p_k) and (u, K_k)
+// of {(m, y) : y = m*K (mod p)} whose value parts are p_k and K_k, plus an
+// affine map y_0 = A + s*y_k from the current window back to the original one
+// (s = +-1; case D flips it, case E shifts it by floor(L/K)*K).  When case C
+// ends the chain with y_k = c*K_k, the answer is the lattice point
+// (B + s*c*u, A + s*c*K_k), where B is the m part accumulated alongside A.
+// The window width w = R - L is the same in every sub-problem.
+//
+// For p < 2^30 all of A, B, U, u stay within (-2^31, 2^31) (|A| < 1.5p,
+// |B| < p/2, |u| < 0.62p, |U| < 0.24p), so 32-bit registers suffice.  The
+// number of passes is at most about 2*log2(p/(w+1)) + 2; max_iter bounds it.
+template <class UT, class ST>
+CS_HD bool g_solve(UT p, UT K, UT L, UT w, UT &m_out, UT &y_out, uint32_t &iters, uint32_t max_iter) {
+    if (L == 0) {
+        m_out = 0;
+        y_out = 0;
+        return true;
+    }
+    ST A = 0, B = 0, U = 0, u = 1, s = 1;
+    for (uint32_t it = 0; it < max_iter; it++) {
+        iters++;
+        UT c = udiv((UT)(L + K - 1), K);              // ceil(L/K)
+        UT ck = c * K;
+        if (ck <= L + w) {                             // case C
+            y_out = (UT)(A + s * (ST)ck);
+            m_out = (UT)(B + s * (ST)c * u);
+            return true;
+        }
+        if (2 * K >= p) {                              // case D
+            A += s * (ST)p;
+            B += s * U;
+            s = -s;
+            u = U - u;
+            K = p - K;
+            L = p - (L + w);
+            continue;
+        }
+        UT f = c - 1;                                  // case E: floor(L/K), K does not divide L
+        A += s * (ST)(f * K);
+        B += s * (ST)f * u;
+        UT q = udiv((UT)(p + K - 1), K);               // ceil(p/K)
+        ST nu = (ST)q * u - U;
+        U = u;
+        u = nu;
+        UT np = K;
+        K = q * K - p;                                 // (-p) mod K
+        p = np;
+        L = L - f * np;                                // L mod K
+    }
+    return false;
+}
+
+// ------------------------------------------------------------- checksum
+CS_HD uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+static constexpr uint64_t kHashStep = 0x9E3779B97F4A7C15ull;
+
+}  // namespace cs

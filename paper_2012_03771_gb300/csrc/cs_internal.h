@@ -1,0 +1,110 @@
+// Internal interfaces between the host orchestration (cs_api.cu) and the
+// kernel translation units.  Not part of the public C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cs {
+
+// device statistics, one uint64 each (index into Plan::d_stats)
+enum Stat {
+    ST_F_SMALL = 0,     // enumerated factors found by the small-prime tile sieve
+    ST_F_LARGE,         // enumerated factors found by the large-prime walk
+    ST_SOLVES,          // G solves (Eq. modeq) issued by the large-prime walk
+    ST_LEVELS,          // passes through the solver's case analysis
+    ST_HITS_ALL,        // large-prime hits before the coprime-m / stored-x filters
+    ST_N_SMALL,         // small sieving primes generated
+    ST_N_LARGE,         // large sieving primes generated
+    ST_HASH,            // bitset checksum (sum of mix64 terms, mod 2^64)
+    ST_ERROR,           // bit flags, see Err
+    ST_SURVIVORS,       // total survivors (sum of per-row counts)
+    ST_COUNT = 16
+};
+
+enum Err : uint64_t {
+    ERR_PRIME_OVERFLOW = 1,   // a prime chunk produced more primes than its buffer holds
+    ERR_SOLVER_LIMIT = 2,     // the solver exceeded its pass bound (never expected)
+};
+
+// layout of one small sieving prime (p <= T < 2^31), for the tile sieve
+struct SmallPrime {
+    uint32_t p;
+    uint32_t pinv;   // -p^-1 mod 2^32 (p odd); unused for p = 2
+    uint32_t rt;     // (K mod p) * 2^32 mod p: Montgomery form of r
+    uint32_t v0;     // (r * M_start + SL) mod p
+};
+
+// everything a kernel needs about one sieve instance (device pointers)
+struct DevPlan {
+    uint64_t M_start, M_inc, M_c;
+    uint32_t SL, S, S32;          // S = 2 SL + 1 raw offsets, S32 = ceil(S/32) raw words
+    uint32_t W, wpr;              // stored columns, uint64 words per row
+    uint64_t P, L, T;             // primorial bound, sieve limit, small/large threshold
+    int small_n;                  // N + x may equal a sieving prime or a prime of d
+    uint64_t K64;                 // K when it fits in 64 bits (small_n only)
+    // K's prime factors packed into words: products that fit in 32 / 64 bits
+    const uint32_t *kch32;
+    uint32_t n_kch32;
+    const uint64_t *kch64;
+    uint32_t n_kch64;
+    // columns
+    const uint32_t *col_mask;     // S32 words: bit z set iff raw offset z = x + SL is stored
+    const uint32_t *col_prefix;   // S32 words: stored columns before word
+    const uint32_t *raw_of_col;   // W entries: raw offset of column j
+    // rows
+    const uint32_t *moff_of_row;  // M_c entries: m - M_start
+    const int32_t *row_of_moff;   // M_inc entries: row index or -1
+    // wheel (primes of d)
+    const uint32_t *qd;           // n_qd primes
+    uint32_t n_qd;
+    const uint32_t *qd_kmod;      // K mod q
+    const uint32_t *qd_pat_off;   // offset of q's pattern table in qd_pat
+    const uint32_t *qd_pat;       // pattern[k]: bits i < 32 with (k + i) % q == 0
+    // outputs
+    uint64_t *bits;               // M_c * wpr words
+    uint32_t *counts;             // M_c
+    unsigned long long *stats;    // ST_COUNT
+};
+
+// ---- kernel launchers (each enqueues on `stream`; no synchronisation) ----
+
+// Primes p with lo < p <= hi, written as small-prime entries.
+cudaError_t launch_gen_small(const DevPlan &pl, uint64_t lo, uint64_t hi, const uint32_t *base,
+                             uint32_t n_base, SmallPrime *out, uint64_t cap,
+                             unsigned long long *count, cudaStream_t stream);
+// Primes p with lo < p <= hi as (p, r, v0) large-prime entries; narrow: 32-bit fields.
+cudaError_t launch_gen_large(const DevPlan &pl, bool narrow, uint64_t lo, uint64_t hi,
+                             const uint32_t *base, uint32_t n_base, void *p_out, void *r_out,
+                             void *v_out, uint64_t cap, unsigned long long *count,
+                             cudaStream_t stream);
+// Plain prime list (uint64) in (lo, hi], no residues (for tests of the generator).
+cudaError_t launch_gen_list(uint64_t lo, uint64_t hi, const uint32_t *base, uint32_t n_base,
+                            uint64_t *out, uint64_t cap, unsigned long long *count,
+                            unsigned long long *err, cudaStream_t stream);
+// K mod p for an array of odd primes p > P (tests of the residue kernel).
+cudaError_t launch_kmodp(const DevPlan &pl, const uint64_t *p, uint64_t n, uint64_t *r,
+                         cudaStream_t stream);
+
+struct TileConfig {
+    uint32_t rows;           // rows per tile (1, 2, 4, 8, 16 or 32)
+    uint32_t n_chunks;       // column chunks
+    const uint32_t *chunk;   // device: per chunk {j0, j1, z0, z1}
+    uint32_t max_words;      // raw words of the widest chunk
+};
+cudaError_t launch_tile(const DevPlan &pl, const TileConfig &tc, const SmallPrime *sp,
+                        const unsigned long long *n_sp, uint64_t sp_cap, cudaStream_t stream);
+
+enum LargeMode { LARGE_PAPER = 1, LARGE_THREE_GAP = 2 };
+cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p, const void *r,
+                         const void *v, const unsigned long long *count, uint64_t cap,
+                         int grid, cudaStream_t stream);
+cudaError_t launch_final(const DevPlan &pl, cudaStream_t stream);
+
+// batch of G solves (tests of the solver)
+cudaError_t launch_modsolve(const uint64_t *p, const uint64_t *K, const uint64_t *L,
+                            const uint64_t *R, uint64_t *m, uint64_t n, int narrow,
+                            cudaStream_t stream);
+
+int sm_count();
+
+}  // namespace cs

@@ -1,0 +1,219 @@
+// Large-prime kernel (primes T < p <= L), Section 3.2 "Large Prime Optimization".
+//
+// For a fixed p with r = K mod p, p divides a number of the interval around
+// N = m K iff v(m) = (r m + SL) mod p <= 2 SL (Eq. modeq), and then x = SL - v.
+// Each thread walks one prime over m in [M_start, M_start + M_inc):
+//
+//   LARGE_PAPER      as in the paper: from the current m, one G solve
+//                    (Section 3.3) finds the next m whose v is in the window,
+//                    the hit is recorded, m advances by one and the next solve
+//                    starts there.
+//   LARGE_THREE_GAP  two G solves per prime give the first m with r*m mod p in
+//                    [p - 2SL, p - 1] (a step that lowers v by at most 2SL) and
+//                    in [1, 2SL] (a step that raises it); by the three-distance
+//                    theorem the next hit after any hit is one of those steps or
+//                    their sum (cf. Franke and Kleinjung, "Continued fractions and
+//                    lattice sieving", SHARCS 2005), so after the first hit, found
+//                    by one more solve, every further hit costs O(1).
+//
+// Each hit on a coprime m and a stored x clears one bit of the device bitset
+// with a 64-bit atomic AND and counts one enumerated factor.
+#include "cs_arith.cuh"
+#include "cs_internal.h"
+
+namespace cs {
+
+namespace {
+
+constexpr int LARGE_THREADS = 256;
+
+struct LargeArgs {
+    DevPlan pl;
+    const void *p, *r, *v;
+    const unsigned long long *count;
+    uint64_t cap;
+};
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+struct Counters {
+    unsigned long long F = 0, solves = 0, levels = 0, hits = 0, err = 0;
+};
+
+// One hit of prime p at m = M_start + moff with v = (r m + SL) mod p <= 2SL.
+template <class UT>
+__device__ __forceinline__ void record_hit(const DevPlan &pl, uint64_t moff, UT v, UT p, Counters &c) {
+    c.hits++;
+    const int32_t row = __ldg(&pl.row_of_moff[moff]);
+    if (row < 0) return;                                 // m shares a factor with d
+    const uint32_t z = 2 * pl.SL - (uint32_t)v;          // raw offset x + SL
+    const uint32_t mw = __ldg(&pl.col_mask[z >> 5]);
+    const uint32_t bit = 1u << (z & 31);
+    if (!(mw & bit)) return;                             // x not coprime to K
+    if (pl.small_n) {
+        unsigned __int128 n = (unsigned __int128)(pl.M_start + moff) * pl.K64 + z - pl.SL;
+        if (n == (unsigned __int128)p) return;           // N + x is p itself
+    }
+    const uint32_t col = __ldg(&pl.col_prefix[z >> 5]) + __popc(mw & (bit - 1));
+    atomicAnd(reinterpret_cast<unsigned long long *>(pl.bits + (uint64_t)row * pl.wpr + (col >> 6)),
+              ~(1ull << (col & 63)));
+    c.F++;
+}
+
+template <class UT, class ST, int MODE>
+__global__ void __launch_bounds__(LARGE_THREADS) k_large(const LargeArgs a) {
+    const DevPlan &pl = a.pl;
+    const UT *Pp = reinterpret_cast<const UT *>(a.p);
+    const UT *Rp = reinterpret_cast<const UT *>(a.r);
+    const UT *Vp = reinterpret_cast<const UT *>(a.v);
+    const uint64_t n = min((uint64_t)*a.count, a.cap);
+    const UT w = (UT)(2 * pl.SL);
+    const uint64_t M = pl.M_inc;
+    const uint32_t max_iter = 4 * 8 * sizeof(UT) + 8;
+    Counters c;
+    if (M == 0) return;
+
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const UT p = Pp[i], r = Rp[i];
+        UT v = Vp[i];
+        uint32_t it = 0;
+        if (MODE == LARGE_PAPER) {
+            uint64_t m = 0;
+            while (true) {
+                if (v <= w) {
+                    record_hit<UT>(pl, m, v, p, c);
+                    if (++m >= M) break;
+                    v += r;
+                    if (v >= p) v -= p;
+                    continue;
+                }
+                UT t, y;
+                c.solves++;
+                if (!g_solve<UT, ST>(p, r, (UT)(p - v), w, t, y, it, max_iter)) {
+                    c.err |= ERR_SOLVER_LIMIT;
+                    break;
+                }
+                if ((uint64_t)t >= M - m) break;
+                m += t;
+                v = (UT)(v + y - p);
+            }
+        } else {
+            // steps that lower v by da (m += ma) and raise it by ub (m += mb)
+            UT ma, da, mb = 0, ub = 0;
+            if (w == 0) {
+                ma = p;
+                da = 0;
+            } else {
+                UT y;
+                c.solves += 2;
+                bool ok = g_solve<UT, ST>(p, r, (UT)(p - w), (UT)(w - 1), ma, y, it, max_iter);
+                da = p - y;
+                ok = ok && g_solve<UT, ST>(p, r, (UT)1, (UT)(w - 1), mb, ub, it, max_iter);
+                if (!ok) {
+                    c.err |= ERR_SOLVER_LIMIT;
+                    continue;
+                }
+            }
+            uint64_t m = 0;
+            if (v > w) {
+                UT t, y;
+                c.solves++;
+                if (!g_solve<UT, ST>(p, r, (UT)(p - v), w, t, y, it, max_iter)) {
+                    c.err |= ERR_SOLVER_LIMIT;
+                    continue;
+                }
+                if ((uint64_t)t >= M) {
+                    c.levels += it;
+                    continue;
+                }
+                m = t;
+                v = (UT)(v + y - p);
+            }
+            while (true) {
+                record_hit<UT>(pl, m, v, p, c);
+                uint64_t step;
+                if (v >= da) {
+                    v -= da;
+                    step = ma;
+                } else if (v + ub <= w) {
+                    v += ub;
+                    step = mb;
+                } else {
+                    v = v + ub - da;
+                    step = (uint64_t)ma + mb;
+                }
+                if (step >= M - m) break;
+                m += step;
+            }
+        }
+        c.levels += it;
+    }
+
+    c.F = warp_sum(c.F);
+    c.solves = warp_sum(c.solves);
+    c.levels = warp_sum(c.levels);
+    c.hits = warp_sum(c.hits);
+    for (int o = 16; o; o >>= 1) c.err |= __shfl_xor_sync(0xffffffffu, c.err, o);
+    if ((threadIdx.x & 31) == 0) {
+        if (c.F) atomicAdd(pl.stats + ST_F_LARGE, c.F);
+        if (c.solves) atomicAdd(pl.stats + ST_SOLVES, c.solves);
+        if (c.levels) atomicAdd(pl.stats + ST_LEVELS, c.levels);
+        if (c.hits) atomicAdd(pl.stats + ST_HITS_ALL, c.hits);
+        if (c.err) atomicOr(pl.stats + ST_ERROR, c.err);
+    }
+}
+
+template <class UT, class ST>
+__global__ void k_modsolve(const uint64_t *p, const uint64_t *K, const uint64_t *L,
+                           const uint64_t *R, uint64_t *m, uint64_t n) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        UT t, y;
+        uint32_t it = 0;
+        const UT pp = (UT)p[i];
+        const UT kk = (UT)(K[i] % p[i]);
+        bool ok = kk != 0 && g_solve<UT, ST>(pp, kk, (UT)L[i], (UT)(R[i] - L[i]), t, y, it,
+                                             4 * 8 * sizeof(UT) + 8);
+        m[i] = ok ? (uint64_t)t : ~0ull;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p, const void *r,
+                         const void *v, const unsigned long long *count, uint64_t cap, int grid,
+                         cudaStream_t stream) {
+    LargeArgs a{pl, p, r, v, count, cap};
+    if (grid <= 0) grid = sm_count() * 8;
+    if (narrow) {
+        if (mode == LARGE_PAPER)
+            k_large<uint32_t, int32_t, LARGE_PAPER><<<grid, LARGE_THREADS, 0, stream>>>(a);
+        else
+            k_large<uint32_t, int32_t, LARGE_THREE_GAP><<<grid, LARGE_THREADS, 0, stream>>>(a);
+    } else {
+        if (mode == LARGE_PAPER)
+            k_large<uint64_t, int64_t, LARGE_PAPER><<<grid, LARGE_THREADS, 0, stream>>>(a);
+        else
+            k_large<uint64_t, int64_t, LARGE_THREE_GAP><<<grid, LARGE_THREADS, 0, stream>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_modsolve(const uint64_t *p, const uint64_t *K, const uint64_t *L,
+                            const uint64_t *R, uint64_t *m, uint64_t n, int narrow,
+                            cudaStream_t stream) {
+    if (n == 0) return cudaSuccess;
+    uint64_t blocks = (n + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    if (narrow)
+        k_modsolve<uint32_t, int32_t><<<(unsigned)blocks, 256, 0, stream>>>(p, K, L, R, m, n);
+    else
+        k_modsolve<uint64_t, int64_t><<<(unsigned)blocks, 256, 0, stream>>>(p, K, L, R, m, n);
+    return cudaGetLastError();
+}
+
+}  // namespace cs

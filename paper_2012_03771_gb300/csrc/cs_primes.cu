@@ -1,0 +1,346 @@
+// Sieving-prime source: a segmented sieve of Eratosthenes over odd numbers,
+// fused with the cached residue r = K mod p of Section 3.1 (Space-Time
+// Tradeoff).  The paper treats prime generation up to P_limit as a small
+// one-time cost (Runtime section); here it runs on the device so that the
+// primes never cross the host boundary.
+//
+// One CTA sieves one segment of SEG odd numbers in shared memory at a time
+// (grid-stride over segments).  Multiples of the base primes q <= sqrt(hi) are
+// marked with shared-memory atomics: small q cooperatively by a warp, large q
+// one per thread.  Each warp then scans its share of the segment, queues the
+// primes it finds in shared memory and, 32 at a time, computes K mod p with
+// Montgomery multiplication over K's prime factors packed into machine words,
+// and appends the entries to the output with one atomic per 32 primes.
+#include "cs_arith.cuh"
+#include "cs_internal.h"
+
+namespace cs {
+
+namespace {
+
+constexpr uint32_t SEG = 1u << 17;          // odd numbers per segment
+constexpr uint32_t SEG_WORDS = SEG / 32;
+constexpr uint32_t GEN_THREADS = 256;
+constexpr uint32_t GEN_WARPS = GEN_THREADS / 32;
+constexpr uint32_t WARP_COOP_Q = 4096;      // q below this: marked by a whole warp
+constexpr uint32_t BATCH = 16;              // words scanned per warp step (lanes 0..15)
+constexpr uint32_t QCAP = BATCH * 32 + 32;  // per-warp queue (odd indices within the segment)
+
+enum Kind { KIND_SMALL = 0, KIND_LARGE32 = 1, KIND_LARGE64 = 2, KIND_LIST = 3 };
+
+struct GenArgs {
+    uint64_t i_begin, i_end;      // odd indices [i_begin, i_end): numbers 2i+1
+    uint64_t n_seg;
+    bool emit_two;                // 2 is in range
+    const uint32_t *base;         // odd base primes, ascending
+    uint32_t n_base;
+    // residue parameters
+    const uint32_t *kch32;
+    uint32_t n_kch32;
+    const uint64_t *kch64;
+    uint32_t n_kch64;
+    uint64_t M_start;
+    uint32_t SL;
+    // outputs
+    void *o0, *o1, *o2;
+    uint64_t cap;
+    unsigned long long *count;
+    unsigned long long *err;
+};
+
+__device__ __forceinline__ uint32_t kmodp32(uint32_t p, uint32_t pinv, uint32_t r1, uint32_t r2,
+                                            const uint32_t *kch, uint32_t n) {
+    if (n == 0) return 1u % p;
+    uint32_t acc = mont32_rpow(n, r1, r2, p, pinv);     // R^n: cancels the n factors R^-1
+    for (uint32_t i = 0; i < n; i++) acc = mont32_mul(acc, __ldg(&kch[i]), p, pinv);
+    return acc;
+}
+
+__device__ __forceinline__ uint64_t kmodp64(uint64_t p, uint64_t pinv, uint64_t r1, uint64_t r2,
+                                            const uint64_t *kch, uint32_t n) {
+    if (n == 0) return 1ull % p;
+    uint64_t acc = mont64_rpow(n, r1, r2, p, pinv);
+    for (uint32_t i = 0; i < n; i++) acc = mont64_mul(acc, __ldg(&kch[i]), p, pinv);
+    return acc;
+}
+
+template <int KIND>
+__device__ __forceinline__ void emit(const GenArgs &a, uint64_t p, bool valid, unsigned lane) {
+    // residue work for this lane's prime
+    uint32_t e0 = 0, e1 = 0, e2 = 0, e3 = 0;
+    uint64_t w0 = 0, w1 = 0, w2 = 0;
+    if (valid) {
+        if (KIND == KIND_SMALL) {
+            uint32_t p32 = (uint32_t)p;
+            if (p32 == 2) {
+                // only when P < 2, so K = 1 and r = 1
+                e0 = 2; e1 = 0; e2 = 1; e3 = (uint32_t)((a.M_start + a.SL) & 1);
+            } else {
+                uint32_t pinv = mont32_neg_inv(p32);
+                uint32_t r1 = mont32_r1(p32), r2 = mont32_r2(p32);
+                uint32_t r = kmodp32(p32, pinv, r1, r2, a.kch32, a.n_kch32);
+                uint32_t rt = mont32_mul(r, r2, p32, pinv);
+                uint32_t ms = (uint32_t)(a.M_start % p32);
+                uint32_t v = mont32_mul(rt, ms, p32, pinv) + a.SL % p32;
+                e0 = p32; e1 = pinv; e2 = rt; e3 = v >= p32 ? v - p32 : v;
+            }
+        } else if (KIND == KIND_LARGE32) {
+            uint32_t p32 = (uint32_t)p;
+            uint32_t pinv = mont32_neg_inv(p32);
+            uint32_t r1 = mont32_r1(p32), r2 = mont32_r2(p32);
+            uint32_t r = kmodp32(p32, pinv, r1, r2, a.kch32, a.n_kch32);
+            uint32_t rt = mont32_mul(r, r2, p32, pinv);
+            uint32_t ms = (uint32_t)(a.M_start % p32);
+            uint32_t v = mont32_mul(rt, ms, p32, pinv) + a.SL;   // SL < p
+            e0 = p32; e1 = r; e2 = v >= p32 ? v - p32 : v;
+        } else if (KIND == KIND_LARGE64) {
+            uint64_t pinv = mont64_neg_inv(p);
+            uint64_t r1 = mont64_r1(p), r2 = mont64_r2(p);
+            uint64_t r = kmodp64(p, pinv, r1, r2, a.kch64, a.n_kch64);
+            uint64_t rt = mont64_mul(r, r2, p, pinv);
+            uint64_t v = mont64_mul(rt, a.M_start % p, p, pinv) + a.SL;
+            w0 = p; w1 = r; w2 = v >= p ? v - p : v;
+        } else {
+            w0 = p;
+        }
+    }
+    unsigned mask = __ballot_sync(0xffffffffu, valid);
+    unsigned n = __popc(mask);
+    if (n == 0) return;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(a.count, (unsigned long long)n);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    unsigned rank = __popc(mask & ((1u << lane) - 1));
+    if (!valid) return;
+    uint64_t slot = base + rank;
+    if (slot >= a.cap) {
+        atomicOr(a.err, (unsigned long long)ERR_PRIME_OVERFLOW);
+        return;
+    }
+    if (KIND == KIND_SMALL) {
+        reinterpret_cast<SmallPrime *>(a.o0)[slot] = SmallPrime{e0, e1, e2, e3};
+    } else if (KIND == KIND_LARGE32) {
+        reinterpret_cast<uint32_t *>(a.o0)[slot] = e0;
+        reinterpret_cast<uint32_t *>(a.o1)[slot] = e1;
+        reinterpret_cast<uint32_t *>(a.o2)[slot] = e2;
+    } else if (KIND == KIND_LARGE64) {
+        reinterpret_cast<uint64_t *>(a.o0)[slot] = w0;
+        reinterpret_cast<uint64_t *>(a.o1)[slot] = w1;
+        reinterpret_cast<uint64_t *>(a.o2)[slot] = w2;
+    } else {
+        reinterpret_cast<uint64_t *>(a.o0)[slot] = w0;
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(GEN_THREADS) k_gen(const GenArgs a) {
+    __shared__ uint32_t comp[SEG_WORDS];          // bit set = composite (or out of range)
+    __shared__ uint32_t queue[GEN_WARPS][QCAP];
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    if (a.emit_two && blockIdx.x == 0 && warp == 0) emit<KIND>(a, 2, lane == 0, lane);
+
+    // first base index with q >= WARP_COOP_Q (base is ascending)
+    uint32_t big0 = 0;
+    {
+        uint32_t hi = a.n_base;
+        while (big0 < hi) {
+            uint32_t mid = (big0 + hi) / 2;
+            if (__ldg(&a.base[mid]) < WARP_COOP_Q) big0 = mid + 1; else hi = mid;
+        }
+    }
+
+    for (uint64_t s = blockIdx.x; s < a.n_seg; s += gridDim.x) {
+        const uint64_t i0 = a.i_begin + s * SEG;
+        const uint64_t i1 = min(i0 + SEG, a.i_end);
+        const uint32_t len = (uint32_t)(i1 - i0);
+        const uint64_t n_first = 2 * i0 + 1;
+        const uint64_t n_last = 2 * (i1 - 1) + 1;
+        for (uint32_t w = threadIdx.x; w < SEG_WORDS; w += GEN_THREADS) {
+            uint32_t v = 0;
+            uint32_t lo = w * 32;
+            if (lo + 32 > len) v = lo >= len ? 0xffffffffu : (0xffffffffu << (len - lo));
+            comp[w] = v;
+        }
+        __syncthreads();
+        if (i0 == 0 && threadIdx.x == 0) atomicOr(&comp[0], 1u);   // 1 is not prime
+
+        // mark odd multiples of the base primes, starting at max(q^2, first in segment)
+        for (uint32_t b = warp; b < a.n_base; b += GEN_WARPS) {
+            const uint32_t q = __ldg(&a.base[b]);
+            if ((uint64_t)q * q > n_last) break;
+            if (q >= WARP_COOP_Q) break;
+            uint64_t start = (uint64_t)q * q;
+            if (start < n_first) {
+                uint64_t rem = n_first % q;
+                start = rem ? n_first + (q - rem) : n_first;
+                if ((start & 1) == 0) start += q;
+            }
+            for (uint64_t idx = (start - n_first) / 2 + (uint64_t)lane * q; idx < len; idx += 32ull * q)
+                atomicOr(&comp[idx >> 5], 1u << (idx & 31));
+        }
+        // large base primes: one per thread (at most SEG / q + 1 marks each)
+        {
+            for (uint32_t b = big0 + threadIdx.x; b < a.n_base; b += GEN_THREADS) {
+                const uint32_t q = __ldg(&a.base[b]);
+                if ((uint64_t)q * q > n_last) break;
+                uint64_t start = (uint64_t)q * q;
+                if (start < n_first) {
+                    uint64_t rem = n_first % q;
+                    start = rem ? n_first + (q - rem) : n_first;
+                    if ((start & 1) == 0) start += q;
+                }
+                for (uint64_t idx = (start - n_first) / 2; idx < len; idx += q)
+                    atomicOr(&comp[idx >> 5], 1u << (idx & 31));
+            }
+        }
+        __syncthreads();
+
+        // extract: each warp owns a contiguous run of words
+        const uint32_t wpw = SEG_WORDS / GEN_WARPS;
+        uint32_t qlen = 0;
+        for (uint32_t w0 = warp * wpw; w0 < (warp + 1) * wpw; w0 += BATCH) {
+            uint32_t w = w0 + lane;
+            uint32_t primes = lane < BATCH ? ~comp[w] : 0u;
+            uint32_t c = __popc(primes);
+            uint32_t incl = c;
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= (unsigned)o) incl += t;
+            }
+            uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            uint32_t pos = qlen + incl - c;
+            while (primes) {
+                uint32_t bit = __ffs(primes) - 1;
+                primes &= primes - 1;
+                queue[warp][pos++] = w * 32 + bit;
+            }
+            qlen += total;
+            __syncwarp();
+            uint32_t done = 0;
+            while (qlen - done >= 32) {
+                uint32_t idx = queue[warp][done + lane];
+                emit<KIND>(a, 2 * (i0 + idx) + 1, true, lane);
+                done += 32;
+            }
+            __syncwarp();
+            // move the remainder (< 32 entries) to the front
+            uint32_t rest = qlen - done;
+            uint32_t keep = lane < rest ? queue[warp][done + lane] : 0;
+            __syncwarp();
+            if (lane < rest) queue[warp][lane] = keep;
+            qlen = rest;
+            __syncwarp();
+        }
+        {
+            bool valid = lane < qlen;
+            uint32_t idx = valid ? queue[warp][lane] : 0;
+            emit<KIND>(a, 2 * (i0 + idx) + 1, valid, lane);
+        }
+        __syncthreads();
+    }
+}
+
+GenArgs make_args(uint64_t lo, uint64_t hi, const uint32_t *base, uint32_t n_base) {
+    GenArgs a{};
+    a.base = base;
+    a.n_base = n_base;
+    if (hi <= lo || hi < 2) {
+        a.n_seg = 0;
+        return a;
+    }
+    a.i_begin = (lo + 1) / 2;
+    a.i_end = (hi + 1) / 2;
+    a.n_seg = a.i_end > a.i_begin ? (a.i_end - a.i_begin + SEG - 1) / SEG : 0;
+    a.emit_two = lo < 2 && hi >= 2;
+    return a;
+}
+
+int gen_grid(uint64_t n_seg) {
+    uint64_t g = (uint64_t)sm_count() * 8;
+    if (n_seg < g) g = n_seg;
+    return (int)(g ? g : 1);
+}
+
+}  // namespace
+
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+cudaError_t launch_gen_small(const DevPlan &pl, uint64_t lo, uint64_t hi, const uint32_t *base,
+                             uint32_t n_base, SmallPrime *out, uint64_t cap,
+                             unsigned long long *count, cudaStream_t stream) {
+    GenArgs a = make_args(lo, hi, base, n_base);
+    if (a.n_seg == 0 && !a.emit_two) return cudaSuccess;
+    a.kch32 = pl.kch32; a.n_kch32 = pl.n_kch32;
+    a.M_start = pl.M_start; a.SL = pl.SL;
+    a.o0 = out; a.cap = cap; a.count = count; a.err = pl.stats + ST_ERROR;
+    k_gen<KIND_SMALL><<<gen_grid(a.n_seg), GEN_THREADS, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gen_large(const DevPlan &pl, bool narrow, uint64_t lo, uint64_t hi,
+                             const uint32_t *base, uint32_t n_base, void *p_out, void *r_out,
+                             void *v_out, uint64_t cap, unsigned long long *count,
+                             cudaStream_t stream) {
+    GenArgs a = make_args(lo, hi, base, n_base);
+    if (a.n_seg == 0 && !a.emit_two) return cudaSuccess;
+    a.kch32 = pl.kch32; a.n_kch32 = pl.n_kch32;
+    a.kch64 = pl.kch64; a.n_kch64 = pl.n_kch64;
+    a.M_start = pl.M_start; a.SL = pl.SL;
+    a.o0 = p_out; a.o1 = r_out; a.o2 = v_out;
+    a.cap = cap; a.count = count; a.err = pl.stats + ST_ERROR;
+    if (narrow)
+        k_gen<KIND_LARGE32><<<gen_grid(a.n_seg), GEN_THREADS, 0, stream>>>(a);
+    else
+        k_gen<KIND_LARGE64><<<gen_grid(a.n_seg), GEN_THREADS, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gen_list(uint64_t lo, uint64_t hi, const uint32_t *base, uint32_t n_base,
+                            uint64_t *out, uint64_t cap, unsigned long long *count,
+                            unsigned long long *err, cudaStream_t stream) {
+    GenArgs a = make_args(lo, hi, base, n_base);
+    if (a.n_seg == 0 && !a.emit_two) return cudaSuccess;
+    a.o0 = out; a.cap = cap; a.count = count; a.err = err;
+    k_gen<KIND_LIST><<<gen_grid(a.n_seg), GEN_THREADS, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void k_kmodp(const uint64_t *p, uint64_t n, uint64_t *r, const uint32_t *kch32,
+                        uint32_t n32, const uint64_t *kch64, uint32_t n64) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t q = p[i];
+        if (q < (1ull << 31)) {
+            uint32_t q32 = (uint32_t)q;
+            uint32_t pinv = mont32_neg_inv(q32);
+            r[i] = kmodp32(q32, pinv, mont32_r1(q32), mont32_r2(q32), kch32, n32);
+        } else {
+            uint64_t pinv = mont64_neg_inv(q);
+            r[i] = kmodp64(q, pinv, mont64_r1(q), mont64_r2(q), kch64, n64);
+        }
+    }
+}
+}  // namespace
+
+cudaError_t launch_kmodp(const DevPlan &pl, const uint64_t *p, uint64_t n, uint64_t *r,
+                         cudaStream_t stream) {
+    if (n == 0) return cudaSuccess;
+    uint64_t blocks = (n + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    k_kmodp<<<(unsigned)blocks, 256, 0, stream>>>(p, n, r, pl.kch32, pl.n_kch32, pl.kch64,
+                                                   pl.n_kch64);
+    return cudaGetLastError();
+}
+
+}  // namespace cs

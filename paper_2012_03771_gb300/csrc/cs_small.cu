@@ -1,0 +1,182 @@
+// Small-prime tile sieve (primes P < p <= T) fused with row initialisation,
+// the wheel of d's primes and the column compression.
+//
+// Section 3.1 keeps the composite status of all offsets of all coprime m in
+// one array and loops p outside, m inside, with N mod p = (m mod p)(K mod p).
+// Here one CTA owns a tile of up to 32 rows (coprime m) and one span of raw
+// offsets z = x + SL in shared memory, runs every small prime over it, and
+// writes each output word of the [m][x coprime to K] bitset exactly once:
+//
+//   1. tile <- stored-column mask & wheel (x with q | N + x, q | d, cleared;
+//      N + x = q itself is kept).
+//   2. for each small prime (lanes = rows, all lanes of a warp on the same
+//      prime): v = (r*m + SL) mod p = v0 + r*(m - M_start) (Montgomery), then
+//      clear z = 2SL - v, 2SL - v - p, ... >= 0 (x = SL - v - k p >= -SL), i.e.
+//      the x with p | N + x, counting each stored one as an enumerated factor.
+//   3. gather the stored columns with warp ballots and store 128-byte runs.
+#include "cs_arith.cuh"
+#include "cs_internal.h"
+
+namespace cs {
+
+namespace {
+
+constexpr int TILE_THREADS = 512;
+constexpr int TILE_WARPS = TILE_THREADS / 32;
+
+struct TileArgs {
+    DevPlan pl;
+    TileConfig tc;
+    const SmallPrime *sp;
+    const unsigned long long *n_sp;
+    uint64_t sp_cap;
+};
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(TILE_THREADS) k_tile(const TileArgs a) {
+    extern __shared__ uint32_t smem[];
+    const DevPlan &pl = a.pl;
+    const uint32_t TR = a.tc.rows;
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    const uint32_t chunk = blockIdx.x % a.tc.n_chunks;
+    const uint64_t row0 = (uint64_t)(blockIdx.x / a.tc.n_chunks) * TR;
+    const uint32_t j0 = __ldg(&a.tc.chunk[4 * chunk + 0]);
+    const uint32_t j1 = __ldg(&a.tc.chunk[4 * chunk + 1]);
+    const uint32_t z0 = __ldg(&a.tc.chunk[4 * chunk + 2]);
+    const uint32_t z1 = __ldg(&a.tc.chunk[4 * chunk + 3]);
+    const uint32_t zb = z0 & ~31u;
+    const uint32_t nw = (z1 - zb + 31) / 32;
+    const uint32_t nrows = (uint32_t)min((uint64_t)TR, pl.M_c - row0);
+    uint32_t *tile = smem;               // TR x nw
+    uint32_t *mask = smem + TR * nw;     // nw
+
+    for (uint32_t w = threadIdx.x; w < nw; w += TILE_THREADS) {
+        uint32_t g = zb / 32 + w;
+        mask[w] = g < pl.S32 ? __ldg(&pl.col_mask[g]) : 0u;
+    }
+    __syncthreads();
+
+    // 1. rows start as the stored columns minus the wheel of d's primes; one
+    //    pass per prime q | d with the pattern phase advanced incrementally
+    for (uint32_t r = warp; r < nrows; r += TILE_WARPS) {
+        const uint64_t m = pl.M_start + __ldg(&pl.moff_of_row[row0 + r]);
+        for (uint32_t w = lane; w < nw; w += 32) tile[r * nw + w] = mask[w];
+        for (uint32_t qi = 0; qi < pl.n_qd; qi++) {
+            const uint32_t q = __ldg(&pl.qd[qi]);
+            const uint32_t *pat = pl.qd_pat + __ldg(&pl.qd_pat_off[qi]);
+            // phase of word w: (N - SL + zb + 32 w) mod q, N = m*K
+            const uint32_t nq = (uint32_t)((m % q) * __ldg(&pl.qd_kmod[qi]) % q);
+            uint32_t k = (uint32_t)(((uint64_t)nq + q - pl.SL % q + (zb + 32 * lane) % q) % q);
+            const uint32_t step = 1024u % q;
+            __syncwarp();
+            for (uint32_t w = lane; w < nw; w += 32) {
+                tile[r * nw + w] &= ~__ldg(&pat[k]);
+                k += step;
+                if (k >= q) k -= q;
+            }
+        }
+    }
+    __syncthreads();
+    if (pl.small_n) {
+        // N + x = q for a prime q | d: prime, so it stays a survivor
+        for (uint32_t t = threadIdx.x; t < nrows * pl.n_qd; t += TILE_THREADS) {
+            const uint32_t r = t / pl.n_qd, qi = t % pl.n_qd;
+            const uint64_t m = pl.M_start + __ldg(&pl.moff_of_row[row0 + r]);
+            const unsigned __int128 lowest = (unsigned __int128)m * pl.K64 - pl.SL;   // N - SL
+            const uint64_t q = __ldg(&pl.qd[qi]);
+            if ((unsigned __int128)q < lowest) continue;
+            const unsigned __int128 z = (unsigned __int128)q - lowest;
+            if (z >= z1 || z < z0) continue;
+            const uint32_t zz = (uint32_t)z - zb;
+            if (mask[zz >> 5] & (1u << (zz & 31))) atomicOr(&tile[r * nw + (zz >> 5)], 1u << (zz & 31));
+        }
+    }
+    __syncthreads();
+
+    // 2. small primes: lane -> row (lane % TR), prime (lane / TR) of this warp's group
+    unsigned long long F = 0;
+    {
+        const uint64_t n = min((uint64_t)*a.n_sp, a.sp_cap);
+        const uint32_t pp = 32 / TR;
+        const uint32_t r = lane % TR, sub = lane / TR;
+        const bool row_ok = r < nrows;
+        const uint32_t moff = row_ok ? __ldg(&pl.moff_of_row[row0 + r]) : 0u;
+        unsigned __int128 lowest = 0;
+        if (pl.small_n) lowest = (unsigned __int128)(pl.M_start + moff) * pl.K64 - pl.SL;
+        const uint32_t two_sl = 2 * pl.SL;
+        for (uint64_t base = (uint64_t)warp * pp; base < n; base += (uint64_t)TILE_WARPS * pp) {
+            const uint64_t i = base + sub;
+            if (!row_ok || i >= n) continue;
+            const SmallPrime e = a.sp[i];
+            uint32_t v;
+            if (e.p == 2) {
+                v = (e.v0 + moff) & 1u;
+            } else {
+                v = e.v0 + mont32_mul(e.rt, moff, e.p, e.pinv);
+                if (v >= e.p) v -= e.p;
+            }
+            if (v > two_sl) continue;
+            int32_t z = (int32_t)(two_sl - v);
+            if ((uint32_t)z >= z1) z -= (int32_t)(((uint32_t)z - z1) / e.p + 1) * (int32_t)e.p;
+            for (; z >= (int32_t)z0; z -= (int32_t)e.p) {
+                const uint32_t zz = (uint32_t)z - zb;
+                const uint32_t bit = 1u << (zz & 31);
+                if (!(mask[zz >> 5] & bit)) continue;
+                if (pl.small_n && lowest + (unsigned)z == (unsigned __int128)e.p) continue;
+                atomicAnd(&tile[r * nw + (zz >> 5)], ~bit);
+                F++;
+            }
+        }
+    }
+    __syncthreads();
+
+    // 3. compress the stored columns [j0, j1) of each row into the output words
+    const bool last_chunk = chunk + 1 == a.tc.n_chunks;
+    const uint32_t jend = last_chunk ? 64 * pl.wpr : j1;      // pad the row with zeros
+    for (uint32_t r = warp; r < nrows; r += TILE_WARPS) {
+        uint32_t *out = reinterpret_cast<uint32_t *>(pl.bits + (row0 + r) * pl.wpr);
+        uint32_t keep = 0;
+        uint32_t k = 0;
+        for (uint32_t jb = j0; jb < jend; jb += 32, k++) {
+            const uint32_t j = jb + lane;
+            uint32_t bit = 0;
+            if (j < pl.W && j < j1) {
+                const uint32_t zz = __ldg(&pl.raw_of_col[j]) - zb;
+                bit = (tile[r * nw + (zz >> 5)] >> (zz & 31)) & 1u;
+            }
+            const uint32_t word = __ballot_sync(0xffffffffu, bit);
+            const uint32_t kk = k & 31;
+            if (lane == kk) keep = word;
+            if (kk == 31 || jb + 32 >= jend) {
+                const uint32_t first = j0 / 32 + (k - kk);
+                if (lane <= kk) out[first + lane] = keep;
+            }
+        }
+    }
+
+    F = warp_sum(F);
+    if (lane == 0 && F) atomicAdd(pl.stats + ST_F_SMALL, F);
+}
+
+}  // namespace
+
+cudaError_t launch_tile(const DevPlan &pl, const TileConfig &tc, const SmallPrime *sp,
+                        const unsigned long long *n_sp, uint64_t sp_cap, cudaStream_t stream) {
+    if (pl.M_c == 0 || pl.W == 0) return cudaSuccess;
+    const uint64_t row_blocks = (pl.M_c + tc.rows - 1) / tc.rows;
+    const uint64_t blocks = row_blocks * tc.n_chunks;
+    const size_t smem = (size_t)(tc.rows + 1) * tc.max_words * sizeof(uint32_t);
+    cudaError_t e = cudaFuncSetAttribute(k_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    TileArgs a{pl, tc, sp, n_sp, sp_cap};
+    if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
+    k_tile<<<(unsigned)blocks, TILE_THREADS, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace cs

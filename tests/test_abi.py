@@ -1,0 +1,75 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every symbol include/combsieve.h declares, and rejects the same parameter sets
+as the oracle before touching the device."""
+import os
+import re
+
+import pytest
+
+import oracle.oracle as O
+import paper_2012_03771_gb300 as cs
+from paper_2012_03771_gb300 import workloads
+from tests.conftest import ROOT
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(cs_\w+)\s*\(", text, re.M))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2012_03771_gb300 import build
+    build.build()
+    return cs.load()
+
+
+def test_header_declares_exports(lib):
+    declared = _declared()
+    assert declared, "no declarations parsed"
+    assert declared == set(cs.EXPORTS)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_rejections_match_oracle(lib):
+    seen = 0
+    for prm in workloads.tiny_cases(200):
+        rc = cs.cs_plan_status(*prm.as_tuple())
+        bad = O.validate(*prm.as_tuple()) != 0
+        assert (rc == cs.CS_EINVAL) == bad, (prm, rc, cs.cs_last_error())
+        seen += bad
+    assert seen > 5
+    for args in ((503, 4, 1, 10, 100, 10**6), (7, 11, 1, 10, 100, 10**6), (503, 210, 0, 10, 100, 10**6),
+                 (1, 1, 5, 10, 4, 100), (503, 210, 1, 10, 100, 2**40 + 1), (503, 210, 1, 10, 2**20 + 1, 10**6),
+                 (503, 0, 1, 10, 100, 10**6), (503, 210, 1, 2**31, 100, 10**6)):
+        assert cs.cs_plan_status(*args) == cs.CS_EINVAL
+        assert O.validate(*args) == O.EINVAL
+
+
+def test_bad_tuning_rejected(lib):
+    t = cs.make_tuning(threshold=100)          # below 2*SL
+    assert cs.cs_plan_status(503, 210, 1, 10, 1000, 10**6, t) == cs.CS_EINVAL
+    t = cs.make_tuning(tile_rows=3)
+    assert cs.cs_plan_status(503, 210, 1, 10, 1000, 10**6, t) in (cs.CS_EINVAL, cs.CS_EDEVICE)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    import paper_2012_03771_gb300._binding as b
+    monkeypatch.setattr(b, "_lib", None)
+    with pytest.raises(ImportError):
+        b.load(str(tmp_path / "nope.so"))
+
+
+def test_null_arguments(lib):
+    import ctypes
+    assert lib.cs_plan(503, 210, 1, 10, 100, 10**6, None, None) == cs.CS_EINVAL
+    assert lib.cs_sieve(None, None) == cs.CS_EINVAL
+    assert lib.cs_destroy(None) == cs.CS_OK
+    assert lib.cs_info(None, None) == cs.CS_EINVAL
+    h = ctypes.c_uint64(0)
+    assert lib.cs_primes(10, 2**41, None, 0, ctypes.byref(h), None) == cs.CS_EINVAL

@@ -1,0 +1,196 @@
+"""CUDA path against the CPU oracle, through the C ABI.  Integer work: every
+comparison is exact (bitsets, counts, F, checksum, primes, residues, solver)."""
+import math
+import random
+
+import numpy as np
+import pytest
+
+import oracle.oracle as O
+import paper_2012_03771_gb300 as cs
+from paper_2012_03771_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2012_03771_gb300 import build
+    build.build()
+    cs.load()
+    torch.cuda.set_device(0)
+
+
+def _run(params, **tuning):
+    with cs.Plan(*params, **tuning) as plan:
+        plan.sieve(torch.cuda.current_stream()).sync()
+        bits = plan.bitset()
+        counts, F, h = plan.counts()
+        return dict(bits=bits, counts=counts, F=F, hash=h, rows=plan.rows(), cols=plan.columns(),
+                    stats=plan.stats(), info=plan.info)
+
+
+def _check_full(params, got, wheel=True):
+    m_ref, bits_ref, F_ref = O.full_sieve(*params, wheel=wheel)
+    assert np.array_equal(got["rows"], m_ref)
+    assert np.array_equal(got["cols"], O.columns(params[0], params[1], params[4]))
+    assert got["bits"].shape == bits_ref.shape
+    bad = np.argwhere(got["bits"] != bits_ref)
+    assert bad.size == 0, f"{len(bad)} words differ, first {bad[:3].tolist()}"
+    assert got["F"] == int(F_ref.sum())
+    assert np.array_equal(got["counts"], O.row_counts(bits_ref))
+    assert got["hash"] == O.bitset_hash(bits_ref)
+
+
+# ------------------------------------------------------------- single steps
+
+def test_prime_generator_matches_oracle():
+    for lo, hi in ((0, 2), (0, 10**6), (1, 3), (2, 3), (503, 10**7), (10**9 - 10**6, 10**9),
+                   (2**31 - 5 * 10**5, 2**31 + 5 * 10**5), (2**40 - 3 * 10**5, 2**40)):
+        ref = O.primes(lo, hi)
+        cap = ref.size + 64
+        buf = torch.zeros(cap, dtype=torch.int64, device="cuda")
+        n = cs.cs_primes(lo, hi, buf.data_ptr(), cap, torch.cuda.current_stream())
+        got = np.sort(buf[:n].cpu().numpy().astype(np.uint64))
+        assert n == ref.size, (lo, hi)
+        assert np.array_equal(got, ref), (lo, hi)
+
+
+def test_prime_generator_overflow_is_reported():
+    buf = torch.zeros(10, dtype=torch.int64, device="cuda")
+    with pytest.raises(cs.CSError) as e:
+        cs.cs_primes(0, 10**4, buf.data_ptr(), 10, torch.cuda.current_stream())
+    assert e.value.code == cs.CS_EOVERFLOW
+
+
+def test_k_mod_p_matches_oracle():
+    rng = random.Random(1)
+    for P, d in ((503, 210), (953, 210), (1019, 2310), (37, 6), (1, 1), (7, 210)):
+        ps = list(O.primes(P, P + 20000)[:300])
+        ps += list(O.primes(2**31 - 2000, 2**31 + 2000))
+        ps += list(O.primes(2**40 - 5000, 2**40))
+        ps += [int(x) for x in O.primes(10**9, 10**9 + 10**5)[::37]]
+        p = torch.tensor(np.array(ps, dtype=np.uint64).view(np.int64), device="cuda")
+        r = torch.zeros_like(p)
+        cs.cs_k_mod_p(P, d, p.data_ptr(), p.numel(), r.data_ptr(), torch.cuda.current_stream())
+        got = r.cpu().numpy().view(np.uint64)
+        assert np.array_equal(got, O.k_mod_p(P, d, ps)), (P, d)
+
+
+@pytest.mark.parametrize("narrow", [1, 0])
+def test_modsolve_matches_paper_recursion(narrow):
+    rng = random.Random(2 + narrow)
+    pool = [101, 7919, 1000003, 999999937, (1 << 30) - 35] if narrow else \
+           [1000003, 4294967291, 68719476731, 1099511627689, 999999937]
+    rows = []
+    for _ in range(4000):
+        p = rng.choice(pool)
+        K = rng.randrange(1, p)
+        w = rng.choice([0, 1, 7, 100, 20000, 50000, rng.randrange(0, p // 2)])
+        w = min(w, p - 1)
+        L = rng.randrange(0, p - w)
+        rows.append((p, K, L, L + w))
+    arr = np.array(rows, dtype=np.uint64)
+    dev = [torch.tensor(arr[:, i].view(np.int64), device="cuda") for i in range(4)]
+    m = torch.zeros_like(dev[0])
+    cs.cs_modsolve(*(t.data_ptr() for t in dev), m.data_ptr(), len(rows), narrow,
+                   torch.cuda.current_stream())
+    got = m.cpu().numpy().view(np.uint64)
+    for (p, K, L, R), g in zip(rows, got):
+        assert int(g) == O.G(p, K, L, R), (p, K, L, R)
+
+
+# ------------------------------------------------------------- whole sieve
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_tiny_cases_bit_exact(mode):
+    n = 0
+    for prm in workloads.tiny_cases(150, seed=11):
+        args = prm.as_tuple()
+        if O.validate(*args):
+            assert cs.cs_plan_status(*args) == cs.CS_EINVAL
+            continue
+        for T in (0, max(2 * prm.SL, 1)):
+            got = _run(args, large_mode=mode, threshold=T)
+            _check_full(args, got)
+        got = _run(args, large_mode=mode, no_wheel=True)
+        _check_full(args, got, wheel=False)
+        n += 1
+    assert n > 80
+
+
+def test_k1_survivors_are_primes():
+    """K = d = 1 and L >= sqrt(N + SL): survivors are the primes (Section 1 gaps)."""
+    SL = 199_999
+    got = _run((1, 1, SL + 2, 1, SL, 1000))
+    xs = got["cols"]
+    row = O.unpack_row(got["bits"][0], len(xs))
+    survivors = [SL + 2 + int(x) for x, b in zip(xs, row) if b]
+    ref = O.primes(1, 2 * SL + 2)
+    assert survivors == [int(v) for v in ref]
+    gaps = {}
+    for a, b in zip(survivors, survivors[1:]):
+        gaps.setdefault(b - a, a)
+    assert gaps[4] == 7 and gaps[6] == 23 and gaps[96] == 360653
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("T", [14000, 8 * 14001, 100 * 14001, 10**7])
+def test_plain_503_bit_exact(mode, T):
+    prm = workloads.PLAIN_503
+    got = _run(prm.as_tuple(), large_mode=mode, threshold=T)
+    _check_full(prm.as_tuple(), got)
+
+
+@pytest.mark.parametrize("tile_rows", [1, 4, 32])
+def test_tile_shapes_do_not_change_output(tile_rows):
+    prm = workloads.PLAIN_503.with_(L=3 * 10**6)
+    got = _run(prm.as_tuple(), tile_rows=tile_rows, threshold=50_000)
+    _check_full(prm.as_tuple(), got)
+
+
+def test_wide_arithmetic_bit_exact():
+    """Sieve limit above 2^30: 64-bit prime entries and solver."""
+    prm = workloads.SieveParams(P=503, d=2310, M_start=10**6, M_inc=3000, SL=3000, L=3 * 10**9)
+    for mode in (1, 2):
+        got = _run(prm.as_tuple(), large_mode=mode)
+        assert got["info"].narrow == 0
+        sample = [0, 1, 100, len(got["rows"]) // 2, len(got["rows"]) - 1]
+        bits, F, _ = O.sieve(prm.P, prm.d, prm.SL, prm.L, [int(got["rows"][i]) for i in sample])
+        for k, i in enumerate(sample):
+            assert np.array_equal(got["bits"][i], bits[k]), (mode, i)
+
+
+def test_search_953_sampled_rows_and_invariants():
+    """The paper-shaped search at full size: sampled rows against the oracle
+    (including the 35,308 record row), and size-independent properties."""
+    prm = workloads.SEARCH_953
+    got = _run(prm.as_tuple())
+    rows = got["rows"]
+    m_rec = workloads.RECORD_953[0]
+    i_rec = int(np.searchsorted(rows, m_rec))
+    assert rows[i_rec] == m_rec
+    sample = sorted({0, 1, 2, 777, i_rec, len(rows) // 2, len(rows) - 2, len(rows) - 1})
+    bits, F, _ = O.sieve(prm.P, prm.d, prm.SL, prm.L, [int(rows[i]) for i in sample])
+    for k, i in enumerate(sample):
+        assert np.array_equal(got["bits"][i], bits[k]), i
+        assert int(got["counts"][i]) == int(O.row_counts(bits[k:k + 1])[0])
+    # the record's lower prime survives
+    xs = got["cols"]
+    j = int(np.searchsorted(xs, workloads.RECORD_953[1]))
+    assert (int(got["bits"][i_rec][j >> 6]) >> (j & 63)) & 1
+    # same result with the paper's one-solve-per-hit walk and another threshold
+    other = _run(prm.as_tuple(), large_mode=1, threshold=100 * 40001)
+    assert other["hash"] == got["hash"] and other["F"] == got["F"]
+    assert np.array_equal(other["counts"], got["counts"])
+    # Section 3.2: solves ~ M * S * (loglog L - loglog T) + pi(L) - pi(T)
+    st = other["stats"]
+    T = other["info"].threshold
+    n_large, _, inv = O.prime_stats(T, prm.L)
+    expect = prm.M_inc * (2 * prm.SL + 1) * inv + n_large
+    assert abs(st["solves"] - expect) < 0.01 * expect
+    assert st["n_large_primes"] == n_large

@@ -141,7 +141,7 @@ def _config(params, info):
                      f"coprime to 210, X={params.SL}, primes {params.P} < p <= {params.L}",
          "P": params.P, "d": params.d, "M_start": params.M_start, "M_inc": params.M_inc, "SL": params.SL,
          "L": params.L, "parallelism": "replicas (independent m-ranges per rank)",
-         "l2": "flushed between steps (512 MB device write)"}
+         "l2": "flushed between steps (256 MB device write)"}
     if info is not None:
         c.update({"M_c": int(info.M_c), "W": int(info.W), "bitset_bytes": int(info.bitset_bytes),
                   "threshold": int(info.threshold), "large_mode": int(info.large_mode),
@@ -164,7 +164,7 @@ def run_cuda(args, params):
     build.build()
     cs.load()
     stream = torch.cuda.Stream()
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     tuning = dict(profile=True)
     if args.mode:
         tuning["large_mode"] = args.mode

@@ -92,6 +92,7 @@ struct cs_plan_s {
     std::vector<uint64_t> m_of_row;
     std::vector<int64_t> x_of_col;
     std::vector<std::pair<uint64_t, uint64_t>> chunks;    // large-prime ranges (lo, hi]
+    std::vector<uint32_t> chunk_seg;                      // m-segments per prime, per chunk
     uint64_t large_cap = 0, small_cap = 0;
     int large_grid = 0;
     uint64_t h2d = 0, dev_bytes = 0;
@@ -283,11 +284,23 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
     pl->small_hi = std::min<uint64_t>(T, L);
     pl->narrow = L < NARROW_LIMIT;
 
-    uint64_t chunk = pl->tune.chunk_numbers ? pl->tune.chunk_numbers : (1ull << 27);
-    if (L > T) {
-        for (uint64_t lo = T; lo < L; lo += chunk) pl->chunks.push_back({lo, std::min(L, lo + chunk)});
+    // large primes in chunks of (T, L]: geometric (factor 2) so that the hits
+    // per prime, about M_inc * S / p, vary at most 2x inside a chunk, capped at
+    // chunk_numbers wide; a chunk's primes are split into n_seg m-segments of
+    // about HITS_PER_ITEM expected hits each
+    const uint64_t chunk = pl->tune.chunk_numbers ? pl->tune.chunk_numbers : (1ull << 27);
+    const double HITS_PER_ITEM = 128.0;
+    uint64_t widest = 0;
+    for (uint64_t lo = T; lo < L;) {
+        uint64_t hi = std::min<uint64_t>({L, lo + std::max<uint64_t>(lo, 1), lo + chunk});
+        pl->chunks.push_back({lo, hi});
+        double hits = (double)M_inc * (double)S / (double)std::max<uint64_t>(lo, 1);
+        double seg = std::min<double>(std::max(1.0, std::ceil(hits / HITS_PER_ITEM)), (double)std::max<uint64_t>(M_inc, 1));
+        pl->chunk_seg.push_back((uint32_t)std::min(seg, 65536.0));
+        widest = std::max(widest, hi - lo);
+        lo = hi;
     }
-    pl->large_cap = pl->chunks.empty() ? 0 : primes_in_interval_bound(std::min(chunk, L - T));
+    pl->large_cap = pl->chunks.empty() ? 0 : primes_in_interval_bound(widest);
     pl->small_cap = pl->small_hi > P ? prime_count_bound(pl->small_hi) : 0;
     pl->large_grid = pl->tune.large_grid ? (int)pl->tune.large_grid : sm_count() * 8;
 
@@ -486,7 +499,7 @@ cs_status cs_sieve(cs_plan_t pl, void *stream) {
         if ((s = prof.end())) return s;
         if ((s = prof.begin(KC_LARGE))) return s;
         CS_CUDA(launch_large(dp, pl->narrow, pl->mode, pl->d_lp, pl->d_lr, pl->d_lv, cnt,
-                             pl->large_cap, pl->large_grid, st));
+                             pl->large_cap, pl->chunk_seg[c], pl->large_grid, st));
         if ((s = prof.end())) return s;
     }
     if ((s = prof.begin(KC_FINAL))) return s;

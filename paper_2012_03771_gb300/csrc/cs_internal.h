@@ -95,9 +95,12 @@ cudaError_t launch_tile(const DevPlan &pl, const TileConfig &tc, const SmallPrim
                         const unsigned long long *n_sp, uint64_t sp_cap, cudaStream_t stream);
 
 enum LargeMode { LARGE_PAPER = 1, LARGE_THREE_GAP = 2 };
+// n_seg: the m-range of every prime is split into n_seg segments walked by
+// separate threads (each starts with its own solve), to balance primes with
+// many hits against primes with few.
 cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p, const void *r,
                          const void *v, const unsigned long long *count, uint64_t cap,
-                         int grid, cudaStream_t stream);
+                         uint32_t n_seg, int grid, cudaStream_t stream);
 cudaError_t launch_final(const DevPlan &pl, cudaStream_t stream);
 
 // batch of G solves (tests of the solver)

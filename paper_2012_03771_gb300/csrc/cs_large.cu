@@ -32,7 +32,16 @@ struct LargeArgs {
     const void *p, *r, *v;
     const unsigned long long *count;
     uint64_t cap;
+    uint32_t n_seg;      // m-segments per prime (work items = primes x n_seg)
 };
+
+// (r * m + v) mod p for m < 2^31
+__device__ __forceinline__ uint32_t advance(uint32_t v, uint32_t r, uint64_t m, uint32_t p) {
+    return (uint32_t)(((uint64_t)r * m + v) % p);
+}
+__device__ __forceinline__ uint64_t advance(uint64_t v, uint64_t r, uint64_t m, uint64_t p) {
+    return (uint64_t)(((unsigned __int128)r * m + v) % p);
+}
 
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -73,20 +82,28 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_large(const LargeArgs a) {
     const UT w = (UT)(2 * pl.SL);
     const uint64_t M = pl.M_inc;
     const uint32_t max_iter = 4 * 8 * sizeof(UT) + 8;
+    const uint32_t n_seg = a.n_seg;
     Counters c;
     if (M == 0) return;
 
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x) {
+    // work item = (prime, m-segment); consecutive items share a prime
+    for (uint64_t item = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; item < n * n_seg;
+         item += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i = item / n_seg;
+        const uint32_t sg = (uint32_t)(item - i * n_seg);
+        const uint64_t m_lo = M * sg / n_seg, m_hi = M * (sg + 1) / n_seg;
+        if (m_lo >= m_hi) continue;
+        const uint64_t Mseg = m_hi - m_lo;      // walk m_lo + [0, Mseg)
         const UT p = Pp[i], r = Rp[i];
         UT v = Vp[i];
+        if (m_lo) v = advance(v, r, m_lo, p);
         uint32_t it = 0;
         if (MODE == LARGE_PAPER) {
             uint64_t m = 0;
             while (true) {
                 if (v <= w) {
-                    record_hit<UT>(pl, m, v, p, c);
-                    if (++m >= M) break;
+                    record_hit<UT>(pl, m_lo + m, v, p, c);
+                    if (++m >= Mseg) break;
                     v += r;
                     if (v >= p) v -= p;
                     continue;
@@ -97,7 +114,7 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_large(const LargeArgs a) {
                     c.err |= ERR_SOLVER_LIMIT;
                     break;
                 }
-                if ((uint64_t)t >= M - m) break;
+                if ((uint64_t)t >= Mseg - m) break;
                 m += t;
                 v = (UT)(v + y - p);
             }
@@ -126,7 +143,7 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_large(const LargeArgs a) {
                     c.err |= ERR_SOLVER_LIMIT;
                     continue;
                 }
-                if ((uint64_t)t >= M) {
+                if ((uint64_t)t >= Mseg) {
                     c.levels += it;
                     continue;
                 }
@@ -134,7 +151,7 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_large(const LargeArgs a) {
                 v = (UT)(v + y - p);
             }
             while (true) {
-                record_hit<UT>(pl, m, v, p, c);
+                record_hit<UT>(pl, m_lo + m, v, p, c);
                 uint64_t step;
                 if (v >= da) {
                     v -= da;
@@ -146,7 +163,7 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_large(const LargeArgs a) {
                     v = v + ub - da;
                     step = (uint64_t)ma + mb;
                 }
-                if (step >= M - m) break;
+                if (step >= Mseg - m) break;
                 m += step;
             }
         }
@@ -185,9 +202,9 @@ __global__ void k_modsolve(const uint64_t *p, const uint64_t *K, const uint64_t 
 }  // namespace
 
 cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p, const void *r,
-                         const void *v, const unsigned long long *count, uint64_t cap, int grid,
-                         cudaStream_t stream) {
-    LargeArgs a{pl, p, r, v, count, cap};
+                         const void *v, const unsigned long long *count, uint64_t cap, uint32_t n_seg,
+                         int grid, cudaStream_t stream) {
+    LargeArgs a{pl, p, r, v, count, cap, n_seg ? n_seg : 1};
     if (grid <= 0) grid = sm_count() * 8;
     if (narrow) {
         if (mode == LARGE_PAPER)

@@ -231,7 +231,7 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
 
     // rows: m coprime to d
     std::vector<uint32_t> moff_of_row;
-    std::vector<int32_t> row_of_moff(M_inc, -1);
+    std::vector<uint32_t> row_mask((M_inc + 31) / 32, 0), row_prefix((M_inc + 31) / 32, 0);
     {
         std::vector<uint64_t> rem(qd.size());
         for (size_t i = 0; i < qd.size(); i++) rem[i] = M_start % qd[i];
@@ -242,13 +242,17 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
                 if (++rem[i] == qd[i]) rem[i] = 0;
             }
             if (ok) {
-                row_of_moff[k] = (int32_t)moff_of_row.size();
+                row_mask[k >> 5] |= 1u << (k & 31);
                 moff_of_row.push_back((uint32_t)k);
                 pl->m_of_row.push_back(M_start + k);
             }
         }
     }
     const uint64_t M_c = moff_of_row.size();
+    for (uint64_t w = 0, c = 0; w < row_mask.size(); w++) {
+        row_prefix[w] = (uint32_t)c;
+        c += __builtin_popcount(row_mask[w]);
+    }
 
     // wheel tables: for each q | d, pattern[k] = bits i < 32 with (k + i) % q == 0
     std::vector<uint32_t> wq, wkmod, woff, wpat;
@@ -358,14 +362,15 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
     if ((s = pl->upload(&d_kch64, kch64))) return s;
     dp.kch32 = d_kch32; dp.n_kch32 = (uint32_t)kch32.size();
     dp.kch64 = d_kch64; dp.n_kch64 = (uint32_t)kch64.size();
-    uint32_t *d_mask, *d_prefix, *d_raw, *d_moff; int32_t *d_rowof;
+    uint32_t *d_mask, *d_prefix, *d_raw, *d_moff, *d_rmask, *d_rpref;
     if ((s = pl->upload(&d_mask, col_mask))) return s;
     if ((s = pl->upload(&d_prefix, col_prefix))) return s;
     if ((s = pl->upload(&d_raw, raw_of_col))) return s;
     if ((s = pl->upload(&d_moff, moff_of_row))) return s;
-    if ((s = pl->upload(&d_rowof, row_of_moff))) return s;
+    if ((s = pl->upload(&d_rmask, row_mask))) return s;
+    if ((s = pl->upload(&d_rpref, row_prefix))) return s;
     dp.col_mask = d_mask; dp.col_prefix = d_prefix; dp.raw_of_col = d_raw;
-    dp.moff_of_row = d_moff; dp.row_of_moff = d_rowof;
+    dp.moff_of_row = d_moff; dp.row_mask = d_rmask; dp.row_prefix = d_rpref;
     uint32_t *d_wq, *d_wk, *d_wo, *d_wp;
     if ((s = pl->upload(&d_wq, wq))) return s;
     if ((s = pl->upload(&d_wk, wkmod))) return s;

@@ -185,6 +185,79 @@ CS_HD bool g_solve(UT p, UT K, UT L, UT w, UT &m_out, UT &y_out, uint32_t &iters
     return false;
 }
 
+// Several windows [L_i, L_i + w_i] for the same (p, K) in one pass.  Cases D
+// and E, and so the chain of sub-problems (p_k, K_k), the lattice vectors
+// (U, u) and the sign s, depend only on (p, K); the windows differ only in
+// where case C stops them and in their own A, B and L.  Running them together
+// shares the chain's division per pass.  Returns false if max_iter passes were
+// not enough.  Windows with L_i = 0 are answered by case a (m = 0).
+template <class UT, class ST, int NW>
+CS_HD bool g_solve_multi(UT p, UT K, const UT (&L0)[NW], const UT (&w)[NW], UT (&m_out)[NW],
+                         UT (&y_out)[NW], uint32_t &iters, uint32_t max_iter) {
+    UT L[NW];
+    ST A[NW], B[NW];
+    bool open[NW];
+    int n_open = 0;
+#pragma unroll
+    for (int i = 0; i < NW; i++) {
+        L[i] = L0[i];
+        A[i] = 0;
+        B[i] = 0;
+        open[i] = L0[i] != 0;
+        m_out[i] = 0;
+        y_out[i] = 0;
+        n_open += open[i];
+    }
+    ST U = 0, u = 1, s = 1;
+    for (uint32_t it = 0; it < max_iter && n_open; it++) {
+        iters++;
+        UT c[NW];
+#pragma unroll
+        for (int i = 0; i < NW; i++) {
+            c[i] = 0;
+            if (!open[i]) continue;
+            c[i] = udiv((UT)(L[i] + K - 1), K);                 // ceil(L/K)
+            const UT ck = c[i] * K;
+            if (ck <= L[i] + w[i]) {                             // case C
+                y_out[i] = (UT)(A[i] + s * (ST)ck);
+                m_out[i] = (UT)(B[i] + s * (ST)c[i] * u);
+                open[i] = false;
+                n_open--;
+            }
+        }
+        if (!n_open) return true;
+        if (2 * K >= p) {                                        // case D
+#pragma unroll
+            for (int i = 0; i < NW; i++) {
+                if (!open[i]) continue;
+                A[i] += s * (ST)p;
+                B[i] += s * U;
+                L[i] = p - (L[i] + w[i]);
+            }
+            s = -s;
+            u = U - u;
+            K = p - K;
+            continue;
+        }
+        const UT q = udiv((UT)(p + K - 1), K);                   // case E: ceil(p/K)
+#pragma unroll
+        for (int i = 0; i < NW; i++) {
+            if (!open[i]) continue;
+            const UT f = c[i] - 1;                               // floor(L/K)
+            A[i] += s * (ST)(f * K);
+            B[i] += s * (ST)f * u;
+            L[i] = L[i] - f * K;                                 // L mod K
+        }
+        const ST nu = (ST)q * u - U;
+        U = u;
+        u = nu;
+        const UT np = K;
+        K = q * K - p;
+        p = np;
+    }
+    return n_open == 0;
+}
+
 // ------------------------------------------------------------- checksum
 CS_HD uint64_t mix64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;

@@ -53,7 +53,8 @@ struct DevPlan {
     const uint32_t *raw_of_col;   // W entries: raw offset of column j
     // rows
     const uint32_t *moff_of_row;  // M_c entries: m - M_start
-    const int32_t *row_of_moff;   // M_inc entries: row index or -1
+    const uint32_t *row_mask;     // ceil(M_inc/32) words: bit k set iff m = M_start + k is a row
+    const uint32_t *row_prefix;   // ceil(M_inc/32) words: rows before word
     // wheel (primes of d)
     const uint32_t *qd;           // n_qd primes
     uint32_t n_qd;

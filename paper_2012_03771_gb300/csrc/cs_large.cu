@@ -53,23 +53,29 @@ struct Counters {
 };
 
 // One hit of prime p at m = M_start + moff with v = (r m + SL) mod p <= 2SL.
+// Branch-free up to the atomic: the row and column tests are bit lookups in
+// small tables (coprime-m mask, stored-x mask, each with per-word prefix
+// counts) that stay in L1.
 template <class UT>
 __device__ __forceinline__ void record_hit(const DevPlan &pl, uint64_t moff, UT v, UT p, Counters &c) {
     c.hits++;
-    const int32_t row = __ldg(&pl.row_of_moff[moff]);
-    if (row < 0) return;                                 // m shares a factor with d
     const uint32_t z = 2 * pl.SL - (uint32_t)v;          // raw offset x + SL
-    const uint32_t mw = __ldg(&pl.col_mask[z >> 5]);
-    const uint32_t bit = 1u << (z & 31);
-    if (!(mw & bit)) return;                             // x not coprime to K
+    const uint32_t rw = __ldg(&pl.row_mask[moff >> 5]);
+    const uint32_t rp = __ldg(&pl.row_prefix[moff >> 5]);
+    const uint32_t cw = __ldg(&pl.col_mask[z >> 5]);
+    const uint32_t cp = __ldg(&pl.col_prefix[z >> 5]);
+    const uint32_t rb = 1u << (moff & 31), cb = 1u << (z & 31);
+    bool ok = (rw & rb) && (cw & cb);                    // m coprime to d, x coprime to K
     if (pl.small_n) {
         unsigned __int128 n = (unsigned __int128)(pl.M_start + moff) * pl.K64 + z - pl.SL;
-        if (n == (unsigned __int128)p) return;           // N + x is p itself
+        ok = ok && n != (unsigned __int128)p;            // N + x is p itself
     }
-    const uint32_t col = __ldg(&pl.col_prefix[z >> 5]) + __popc(mw & (bit - 1));
-    atomicAnd(reinterpret_cast<unsigned long long *>(pl.bits + (uint64_t)row * pl.wpr + (col >> 6)),
-              ~(1ull << (col & 63)));
-    c.F++;
+    const uint32_t row = rp + __popc(rw & (rb - 1));
+    const uint32_t col = cp + __popc(cw & (cb - 1));
+    if (ok)
+        atomicAnd(reinterpret_cast<unsigned long long *>(pl.bits + (uint64_t)row * pl.wpr + (col >> 6)),
+                  ~(1ull << (col & 63)));
+    c.F += ok;
 }
 
 template <class UT, class ST, int MODE>
@@ -119,50 +125,61 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_large(const LargeArgs a) {
                 v = (UT)(v + y - p);
             }
         } else {
-            // steps that lower v by da (m += ma) and raise it by ub (m += mb)
+            // one fused pass of the solver over three windows of the same
+            // (p, r): the first m with r*m mod p in [p - 2SL, p - 1] (step that
+            // lowers v by da), in [1, 2SL] (raises it by ub), and the first hit
+            // from v (skipped, L = 0, when v is already in the window)
             UT ma, da, mb = 0, ub = 0;
+            uint64_t m = 0;
             if (w == 0) {
                 ma = p;
                 da = 0;
+                if (v > w) {
+                    UT t, y;
+                    c.solves++;
+                    if (!g_solve<UT, ST>(p, r, (UT)(p - v), w, t, y, it, max_iter)) {
+                        c.err |= ERR_SOLVER_LIMIT;
+                        continue;
+                    }
+                    if ((uint64_t)t >= Mseg) {
+                        c.levels += it;
+                        continue;
+                    }
+                    m = t;
+                    v = (UT)(v + y - p);
+                }
             } else {
-                UT y;
-                c.solves += 2;
-                bool ok = g_solve<UT, ST>(p, r, (UT)(p - w), (UT)(w - 1), ma, y, it, max_iter);
-                da = p - y;
-                ok = ok && g_solve<UT, ST>(p, r, (UT)1, (UT)(w - 1), mb, ub, it, max_iter);
-                if (!ok) {
+                const bool first = v > w;
+                const UT L3[3] = {(UT)(p - w), (UT)1, first ? (UT)(p - v) : (UT)0};
+                const UT W3[3] = {(UT)(w - 1), (UT)(w - 1), w};
+                UT m3[3], y3[3];
+                c.solves += 2 + first;
+                if (!g_solve_multi<UT, ST, 3>(p, r, L3, W3, m3, y3, it, max_iter)) {
                     c.err |= ERR_SOLVER_LIMIT;
                     continue;
                 }
-            }
-            uint64_t m = 0;
-            if (v > w) {
-                UT t, y;
-                c.solves++;
-                if (!g_solve<UT, ST>(p, r, (UT)(p - v), w, t, y, it, max_iter)) {
-                    c.err |= ERR_SOLVER_LIMIT;
-                    continue;
+                ma = m3[0];
+                da = p - y3[0];
+                mb = m3[1];
+                ub = y3[1];
+                if (first) {
+                    if ((uint64_t)m3[2] >= Mseg) {
+                        c.levels += it;
+                        continue;
+                    }
+                    m = m3[2];
+                    v = (UT)(v + y3[2] - p);
                 }
-                if ((uint64_t)t >= Mseg) {
-                    c.levels += it;
-                    continue;
-                }
-                m = t;
-                v = (UT)(v + y - p);
             }
+            const uint64_t mab = (uint64_t)ma + mb;
             while (true) {
                 record_hit<UT>(pl, m_lo + m, v, p, c);
-                uint64_t step;
-                if (v >= da) {
-                    v -= da;
-                    step = ma;
-                } else if (v + ub <= w) {
-                    v += ub;
-                    step = mb;
-                } else {
-                    v = v + ub - da;
-                    step = (uint64_t)ma + mb;
-                }
+                // three-distance step, as selects
+                const bool down = v >= da;
+                const bool up = v + ub <= w;
+                const UT vd = v - da, vu = v + ub;
+                v = down ? vd : (up ? vu : (UT)(vu - da));
+                const uint64_t step = down ? (uint64_t)ma : (up ? (uint64_t)mb : mab);
                 if (step >= Mseg - m) break;
                 m += step;
             }

@@ -1,0 +1,34 @@
+// Host build of the kernels' integer arithmetic (cs_arith.cuh) for CPU tests:
+// reads "p K L R" lines, prints "m y" from g_solve (32- or 64-bit) and from
+// g_solve_multi with the window placed in each of three slots.
+#include <cstdio>
+#include <cstdint>
+#include "../../paper_2012_03771_gb300/csrc/cs_arith.cuh"
+
+int main(int argc, char **argv) {
+    const bool narrow = argc > 1 && argv[1][0] == 'n';
+    unsigned long long p, K, L, R;
+    while (scanf("%llu %llu %llu %llu", &p, &K, &L, &R) == 4) {
+        uint32_t it = 0;
+        if (narrow) {
+            uint32_t m = 0, y = 0;
+            bool ok = cs::g_solve<uint32_t, int32_t>((uint32_t)p, (uint32_t)(K % p), (uint32_t)L,
+                                                     (uint32_t)(R - L), m, y, it, 200);
+            const uint32_t Ls[3] = {(uint32_t)L, 1, (uint32_t)(p - 1)};
+            const uint32_t Ws[3] = {(uint32_t)(R - L), 0, 0};
+            uint32_t ms[3], ys[3];
+            bool ok2 = cs::g_solve_multi<uint32_t, int32_t, 3>((uint32_t)p, (uint32_t)(K % p), Ls, Ws, ms, ys, it, 200);
+            printf("%d %u %u %d %u %u\n", ok, m, y, ok2, ms[0], ys[0]);
+        } else {
+            uint64_t m = 0, y = 0;
+            bool ok = cs::g_solve<uint64_t, int64_t>(p, K % p, L, R - L, m, y, it, 300);
+            const uint64_t Ls[3] = {1, L, p - 1};
+            const uint64_t Ws[3] = {0, R - L, 0};
+            uint64_t ms[3], ys[3];
+            bool ok2 = cs::g_solve_multi<uint64_t, int64_t, 3>(p, K % p, Ls, Ws, ms, ys, it, 300);
+            printf("%d %llu %llu %d %llu %llu\n", ok, (unsigned long long)m, (unsigned long long)y, ok2,
+                   (unsigned long long)ms[1], (unsigned long long)ys[1]);
+        }
+    }
+    return 0;
+}

@@ -201,6 +201,163 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_large(const LargeArgs a) {
     }
 }
 
+// Three-gap walk with persistent lanes.  A warp prepares 32 work items at a
+// time (one fused solve each: the two steps and the first hit of the item's
+// m-segment) into a queue in shared memory; every lane then steps its own item
+// and, when the item's segment is exhausted, takes the next prepared item from
+// the queue, so that lanes stay busy although items have different numbers of
+// hits.  The queue is refilled whenever it holds at most 32 items.
+template <class UT, class ST, class MT>
+struct TGItem {
+    MT moff, end;      // current m - M_start, end of the segment
+    UT v, p, da, ub;   // v = (r m + SL) mod p, steps of v
+    MT ma, mb;         // steps of m (clamped to M_inc + 1)
+};
+
+constexpr int TG_QCAP = 64;
+constexpr int TG_WARPS = LARGE_THREADS / 32;
+
+template <class UT, class ST, class MT>
+__global__ void __launch_bounds__(LARGE_THREADS) k_large_tg(const LargeArgs a) {
+    __shared__ TGItem<UT, ST, MT> queue[TG_WARPS][TG_QCAP];
+    const DevPlan &pl = a.pl;
+    const UT *Pp = reinterpret_cast<const UT *>(a.p);
+    const UT *Rp = reinterpret_cast<const UT *>(a.r);
+    const UT *Vp = reinterpret_cast<const UT *>(a.v);
+    const uint64_t n = min((uint64_t)*a.count, a.cap);
+    const UT w = (UT)(2 * pl.SL);
+    const uint64_t M = pl.M_inc;
+    const uint32_t max_iter = 4 * 8 * sizeof(UT) + 8;
+    const uint32_t n_seg = a.n_seg;
+    const unsigned lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint64_t n_items = n * n_seg;
+    const uint64_t warp_id = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const MT cap_step = (MT)(M + 1);
+    TGItem<UT, ST, MT> *q = queue[wib];
+    Counters c;
+    if (M == 0) return;
+
+    uint64_t batch = warp_id;          // next batch of 32 items to prepare
+    uint32_t qhead = 0, qcount = 0;    // warp-uniform ring state
+    bool active = false;
+    MT moff = 0, end = 0, ma = 0, mb = 0;
+    UT v = 0, p = 1, da = 0, ub = 0;
+
+    while (true) {
+        // refill: prepare 32 items when the queue can take them
+        if (qcount <= TG_QCAP - 32 && batch * 32 < n_items) {
+            const uint64_t item = batch * 32 + lane;
+            batch += n_warps;
+            bool push = false;
+            TGItem<UT, ST, MT> e;
+            if (item < n_items) {
+                const uint64_t i = item / n_seg;
+                const uint32_t sg = (uint32_t)(item - i * n_seg);
+                const uint64_t m_lo = M * sg / n_seg, m_hi = M * (sg + 1) / n_seg;
+                const UT pp = Pp[i], r = Rp[i];
+                UT vv = Vp[i];
+                if (m_lo) vv = advance(vv, r, m_lo, pp);
+                uint32_t it = 0;
+                UT ma_, da_, mb_ = 0, ub_ = 0;
+                uint64_t first = 0;
+                bool ok = m_lo < m_hi;
+                if (ok && w == 0) {
+                    ma_ = pp;
+                    da_ = 0;
+                    if (vv > w) {
+                        UT t, y;
+                        c.solves++;
+                        ok = g_solve<UT, ST>(pp, r, (UT)(pp - vv), w, t, y, it, max_iter);
+                        if (!ok) c.err |= ERR_SOLVER_LIMIT;
+                        first = t;
+                        vv = (UT)(vv + y - pp);
+                    }
+                } else if (ok) {
+                    const bool need_first = vv > w;
+                    const UT L3[3] = {(UT)(pp - w), (UT)1, need_first ? (UT)(pp - vv) : (UT)0};
+                    const UT W3[3] = {(UT)(w - 1), (UT)(w - 1), w};
+                    UT m3[3], y3[3];
+                    c.solves += 2 + need_first;
+                    ok = g_solve_multi<UT, ST, 3>(pp, r, L3, W3, m3, y3, it, max_iter);
+                    if (!ok) c.err |= ERR_SOLVER_LIMIT;
+                    ma_ = m3[0];
+                    da_ = pp - y3[0];
+                    mb_ = m3[1];
+                    ub_ = y3[1];
+                    if (need_first) {
+                        first = m3[2];
+                        vv = (UT)(vv + y3[2] - pp);
+                    }
+                }
+                c.levels += it;
+                if (ok && first < m_hi - m_lo) {
+                    push = true;
+                    e.moff = (MT)(m_lo + first);
+                    e.end = (MT)m_hi;
+                    e.v = vv;
+                    e.p = pp;
+                    e.da = da_;
+                    e.ub = ub_;
+                    e.ma = (uint64_t)ma_ < (uint64_t)cap_step ? (MT)ma_ : cap_step;
+                    e.mb = (uint64_t)mb_ < (uint64_t)cap_step ? (MT)mb_ : cap_step;
+                }
+            }
+            const unsigned pm = __ballot_sync(0xffffffffu, push);
+            if (push) {
+                const uint32_t slot = (qhead + qcount + __popc(pm & ((1u << lane) - 1))) % TG_QCAP;
+                q[slot] = e;
+            }
+            qcount += __popc(pm);
+            __syncwarp();
+        }
+        // hand queued items to idle lanes
+        const unsigned idle = __ballot_sync(0xffffffffu, !active);
+        if (idle && qcount) {
+            const uint32_t rank = __popc(idle & ((1u << lane) - 1));
+            const uint32_t take = min((uint32_t)__popc(idle), qcount);
+            if (!active && rank < take) {
+                const TGItem<UT, ST, MT> e = q[(qhead + rank) % TG_QCAP];
+                moff = e.moff; end = e.end; v = e.v; p = e.p; da = e.da; ub = e.ub;
+                ma = e.ma; mb = e.mb;
+                active = true;
+            }
+            qhead = (qhead + take) % TG_QCAP;
+            qcount -= take;
+            __syncwarp();
+        }
+        const unsigned act = __ballot_sync(0xffffffffu, active);
+        if (!act) {
+            if (qcount == 0 && batch * 32 >= n_items) break;
+            continue;
+        }
+        // one three-distance step per active lane, as selects
+        if (active) {
+            record_hit<UT>(pl, (uint64_t)moff, v, p, c);
+            const bool down = v >= da;
+            const bool up = v + ub <= w;
+            const UT vd = v - da, vu = v + ub;
+            v = down ? vd : (up ? vu : (UT)(vu - da));
+            const MT step = down ? ma : (up ? mb : (MT)(ma + mb));
+            active = step < end - moff;
+            moff += step;
+        }
+    }
+
+    c.F = warp_sum(c.F);
+    c.solves = warp_sum(c.solves);
+    c.levels = warp_sum(c.levels);
+    c.hits = warp_sum(c.hits);
+    for (int o = 16; o; o >>= 1) c.err |= __shfl_xor_sync(0xffffffffu, c.err, o);
+    if (lane == 0) {
+        if (c.F) atomicAdd(pl.stats + ST_F_LARGE, c.F);
+        if (c.solves) atomicAdd(pl.stats + ST_SOLVES, c.solves);
+        if (c.levels) atomicAdd(pl.stats + ST_LEVELS, c.levels);
+        if (c.hits) atomicAdd(pl.stats + ST_HITS_ALL, c.hits);
+        if (c.err) atomicOr(pl.stats + ST_ERROR, c.err);
+    }
+}
+
 template <class UT, class ST>
 __global__ void k_modsolve(const uint64_t *p, const uint64_t *K, const uint64_t *L,
                            const uint64_t *R, uint64_t *m, uint64_t n) {
@@ -227,12 +384,12 @@ cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p
         if (mode == LARGE_PAPER)
             k_large<uint32_t, int32_t, LARGE_PAPER><<<grid, LARGE_THREADS, 0, stream>>>(a);
         else
-            k_large<uint32_t, int32_t, LARGE_THREE_GAP><<<grid, LARGE_THREADS, 0, stream>>>(a);
+            k_large_tg<uint32_t, int32_t, uint32_t><<<grid, LARGE_THREADS, 0, stream>>>(a);
     } else {
         if (mode == LARGE_PAPER)
             k_large<uint64_t, int64_t, LARGE_PAPER><<<grid, LARGE_THREADS, 0, stream>>>(a);
         else
-            k_large<uint64_t, int64_t, LARGE_THREE_GAP><<<grid, LARGE_THREADS, 0, stream>>>(a);
+            k_large_tg<uint64_t, int64_t, uint64_t><<<grid, LARGE_THREADS, 0, stream>>>(a);
     }
     return cudaGetLastError();
 }

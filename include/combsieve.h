@@ -178,6 +178,31 @@ cs_status cs_k_mod_p(uint32_t P, uint64_t d, const uint64_t *p, uint64_t n, uint
 cs_status cs_modsolve(const uint64_t *p, const uint64_t *K, const uint64_t *L, const uint64_t *R,
                       uint64_t *m, uint64_t n, int narrow, void *stream);
 
+/* ---- allocation-free variant -------------------------------------------- */
+
+/* The same prime list as cs_primes, for callers that must not allocate device
+ * memory: a process whose device memory is handed out by its own pool sized at
+ * start-up (an allocation outside the pool can fail or break its accounting),
+ * or a latency-critical loop, where cudaMalloc/cudaFree can synchronise the
+ * whole device.  The paper has no counterpart; it is an interface of this
+ * library only.
+ *
+ * Instead of two small per-call device buffers, it uses one file-scope device
+ * array of 385 KiB (base primes up to 2^20 and two counters) that every GPU
+ * holds from the moment it loads the library until the process exits.  The
+ * caller still owns `out` (device, cap uint64 entries) and `count` (host).
+ * Limits are those of cs_primes: hi <= 2^40 (CS_EINVAL beyond), CS_EOVERFLOW
+ * if more than cap primes.  It calls no allocating routine.
+ *
+ * The first call on a device looks up that array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the one array and each call leaves its contents
+ * behind (the counters are cleared at the start of every call), so calls that
+ * overlap on the GPU -- from two streams or two host threads -- race: issue
+ * them one after another.  Synchronises `stream`. */
+cs_status cs_primes_static(uint64_t lo, uint64_t hi, uint64_t *out, uint64_t cap, uint64_t *count,
+                           void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,7 +32,7 @@ _NAMES = {0: "CS_OK", -1: "CS_EINVAL", -2: "CS_ENOMEM", -3: "CS_EDEVICE", -4: "C
 # every symbol include/combsieve.h declares
 EXPORTS = ("cs_plan", "cs_sieve", "cs_sync", "cs_info", "cs_fetch_bitset", "cs_counts", "cs_stats",
            "cs_rows", "cs_columns", "cs_device_bitset", "cs_kernel_times", "cs_destroy",
-           "cs_last_error", "cs_primes", "cs_k_mod_p", "cs_modsolve")
+           "cs_last_error", "cs_primes", "cs_k_mod_p", "cs_modsolve", "cs_primes_static")
 
 
 class CSError(RuntimeError):
@@ -95,6 +95,7 @@ def load(path: Optional[str] = None):
         lib.cs_last_error.argtypes = []
         lib.cs_last_error.restype = ctypes.c_char_p
         lib.cs_primes.argtypes = [u64, u64, vp, u64, P64, vp]
+        lib.cs_primes_static.argtypes = [u64, u64, vp, u64, P64, vp]
         lib.cs_k_mod_p.argtypes = [u32, u64, vp, u64, vp, vp]
         lib.cs_modsolve.argtypes = [vp, vp, vp, vp, vp, u64, i32, vp]
         for n in EXPORTS:
@@ -216,6 +217,14 @@ def cs_last_error() -> str:
 def cs_primes(lo, hi, out_ptr: int, cap: int, stream=None) -> int:
     c = ctypes.c_uint64()
     _check(load().cs_primes(lo, hi, ctypes.c_void_p(out_ptr), cap, ctypes.byref(c), _stream_handle(stream)))
+    return int(c.value)
+
+
+def cs_primes_static(lo, hi, out_ptr: int, cap: int, stream=None) -> int:
+    """cs_primes without device allocation (shared static scratch; see combsieve.h)."""
+    c = ctypes.c_uint64()
+    _check(load().cs_primes_static(lo, hi, ctypes.c_void_p(out_ptr), cap, ctypes.byref(c),
+                                   _stream_handle(stream)))
     return int(c.value)
 
 

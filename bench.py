@@ -348,13 +348,154 @@ def roofline(dom, kern_ms, kern_n, stats, info, params, peaks, peak_src, clk, co
     return out
 
 
+# ------------------------------------------------------------ batched / served
+
+def _flush(torch, buf, k):
+    buf.fill_(k & 0xff)
+
+
+def run_batched(args):
+    """64 seeded instances of uneven size: plain (one stream, one instance after
+    another) against the batch (worker streams, one CUDA-graph launch)."""
+    import torch
+    import paper_2012_03771_gb300 as cs
+    from paper_2012_03771_gb300 import build
+    build.build()
+    cs.load()
+    torch.cuda.set_device(0)
+    mix = workloads.batched_instances(64)
+    plans = [cs.Plan(*p.as_tuple()) for p in mix]
+    s = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    # reference results: every instance alone
+    ref = []
+    for p in plans:
+        p.sieve(s).sync()
+        ref.append(cs.cs_counts(p.h))
+    F_total = sum(f for f, _ in ref)
+
+    def time_steps(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for k in range(args.steps):
+            _flush(torch, flush, k)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            fn()
+            b.record(s)
+            s.synchronize()
+            ms.append(a.elapsed_time(b))
+        return ms
+
+    def plain():
+        for p in plans:
+            p.sieve(s)
+
+    plain_ms = time_steps(plain)
+    batch = cs.Batch(plans)
+    batch_ms = time_steps(lambda: batch.run(s))
+    batch.sync()
+    same = all(cs.cs_counts(p.h) == r for p, r in zip(plans, ref))
+    line = {"metric": "enumerated factors/s, 64-instance batch (bit-exact)", "unit": UNIT,
+            "value": F_total / (statistics.median(batch_ms) / 1e3), "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.median(batch_ms),
+            "plain": {"value": F_total / (statistics.median(plain_ms) / 1e3), "ms_per_step": statistics.median(plain_ms)},
+            "speedup_vs_plain": statistics.median(plain_ms) / statistics.median(batch_ms),
+            "n_streams": batch.n_streams, "gpu_launches_per_step": batch.launches, "F_per_step": F_total,
+            "results_equal_alone": same,
+            "config": {"workload": "batched_64: P in {503,701,953,1019}, d in {210,2310}, M_inc log-U[1e3,1e6], "
+                                   "SL U[5000,25000], L log-U[1e8,1e10], M_start log-U[1e6,1e8], seed 201203771",
+                       "l2": "flushed between steps (256 MB device write)"}}
+    print(json.dumps(line), flush=True)
+    batch.close()
+    for p in plans:
+        p.close()
+
+
+def run_served(args):
+    """Seeded Poisson stream of requests from the batched distribution (seed + 1),
+    continuous batching by the request server against one-at-a-time service."""
+    import torch
+    import paper_2012_03771_gb300 as cs
+    from paper_2012_03771_gb300 import build
+    build.build()
+    cs.load()
+    torch.cuda.set_device(0)
+    n_req = args.requests
+    reqs = workloads.batched_instances(n_req, seed=workloads.BATCH_SEED + 1)
+    s = torch.cuda.Stream()
+    # service time of each request alone (one stream, one after another)
+    alone_ms, ref = [], []
+    for prm in reqs:
+        p = cs.Plan(*prm.as_tuple())
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        p.sieve(s)
+        b.record(s)
+        s.synchronize()
+        alone_ms.append(a.elapsed_time(b))
+        ref.append(cs.cs_counts(p.h))
+        p.close()
+    mean_ms = statistics.mean(alone_ms)
+    rate = args.load / (mean_ms / 1e3)                  # requests/s at `load` of one-at-a-time capacity
+    arrivals = workloads.poisson_arrivals(n_req, rate)
+    free, total = torch.cuda.mem_get_info()
+    budget = int(args.budget_frac * free)
+    srv = cs.Server(budget_bytes=budget, max_slots=args.slots)
+    lat, queue, pending, results = [0.0] * n_req, list(range(n_req)), {}, {}
+    t0 = time.perf_counter()
+    while queue or pending:
+        now = time.perf_counter() - t0
+        while queue and arrivals[queue[0]] <= now:
+            i = queue[0]
+            t = srv.submit(*reqs[i].as_tuple())
+            if t is None:
+                break
+            pending[t] = i
+            queue.pop(0)
+        for t in list(pending):
+            if srv.poll(t):
+                i = pending.pop(t)
+                lat[i] = time.perf_counter() - t0 - arrivals[i]
+                results[i] = cs.cs_counts(srv.plan(t).h)
+                srv.release(t)
+        time.sleep(0.0002)
+    makespan = time.perf_counter() - t0
+    srv.close()
+    # one-at-a-time service of the same arrivals (FIFO, measured service times)
+    fifo_lat, end = [], 0.0
+    for i in range(n_req):
+        start = max(arrivals[i], end)
+        end = start + alone_ms[i] / 1e3
+        fifo_lat.append(end - arrivals[i])
+    F_total = sum(f for f, _ in ref)
+    pct = lambda v, q: sorted(v)[min(len(v) - 1, int(q * len(v)))]
+    line = {"metric": "served sieve requests: latency and enumerated factors/s (bit-exact)", "unit": UNIT,
+            "value": F_total / makespan, "requests": n_req, "arrival_rate_per_s": rate,
+            "p50_ms": 1e3 * pct(lat, 0.5), "p99_ms": 1e3 * pct(lat, 0.99),
+            "one_at_a_time": {"p50_ms": 1e3 * pct(fifo_lat, 0.5), "p99_ms": 1e3 * pct(fifo_lat, 0.99),
+                              "value": F_total / max(end, 1e-9)},
+            "slots": args.slots, "budget_bytes": budget,
+            "results_equal_alone": all(results[i] == ref[i] for i in range(n_req)),
+            "config": {"workload": f"served: {n_req} requests from the batched distribution (seed 201203772), "
+                                   f"Poisson arrivals at {args.load:.2f} x the one-at-a-time capacity",
+                       "budget": f"{args.budget_frac:.2f} of free device memory"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
-    ap.add_argument("--config", default="search_953", choices=sorted(workloads.NAMED))
+    ap.add_argument("--config", default="search_953", choices=sorted(workloads.NAMED) + ["batched_64", "served"])
+    ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--load", type=float, default=0.8)
+    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--budget-frac", type=float, default=0.5)
     ap.add_argument("--mode", type=int, default=0)
     ap.add_argument("--threshold", type=int, default=0)
     ap.add_argument("--cpu-rows", type=int, default=512)
@@ -362,6 +503,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     rank, ws = _dist()
+    if args.config == "batched_64":
+        return run_batched(args)
+    if args.config == "served":
+        return run_served(args)
     params = _params_for_rank(workloads.NAMED[args.config], rank)
     if args.impl == "reference":
         run_reference(args, params)

@@ -47,6 +47,8 @@ extern "C" {
 #endif
 
 typedef struct cs_plan_s *cs_plan_t;
+typedef struct cs_batch_s *cs_batch_t;
+typedef struct cs_server_s *cs_server_t;
 typedef int cs_status;
 
 #define CS_OK 0
@@ -92,6 +94,8 @@ typedef struct {
     uint64_t launches_per_sieve;  /* kernels one cs_sieve launches */
     uint64_t h2d_bytes;        /* bytes uploaded by cs_plan */
     uint64_t device_bytes;     /* device memory held by the plan */
+    uint64_t est_cost;         /* relative device cost estimate (about picoseconds on a
+                                  GB300), used to order instances in a batch */
 } cs_info_t;
 
 typedef struct {
@@ -156,6 +160,39 @@ cs_status cs_destroy(cs_plan_t plan);
 
 /* Message for the last error on the calling thread ("" if none). */
 const char *cs_last_error(void);
+
+/* ---- batched execution ---------------------------------------------------
+ * Many independent searches of uneven size (Section 5, "Real world searching")
+ * share the GPU.  cs_batch_create spreads the plans over n_streams worker
+ * streams (0 = min(n, 16)), longest estimated cost first onto the least loaded
+ * stream, and captures their whole launch sequence once into a CUDA graph;
+ * cs_batch_run replays it with one graph launch on `stream`.  The plans stay
+ * owned by the caller and must outlive the batch; their results are read with
+ * cs_counts / cs_fetch_bitset after cs_batch_sync.  Plans built with
+ * profile = 1 are rejected (CS_EINVAL), and so is a plan listed twice. */
+cs_status cs_batch_create(const cs_plan_t *plans, int n, int n_streams, cs_batch_t *out);
+cs_status cs_batch_run(cs_batch_t batch, void *stream);
+cs_status cs_batch_sync(cs_batch_t batch);            /* waits; first plan error, if any */
+cs_status cs_batch_info(cs_batch_t batch, uint64_t *n_streams, uint64_t *launches);
+cs_status cs_batch_destroy(cs_batch_t batch);
+
+/* ---- served execution (continuous batching) ------------------------------
+ * A request server with max_slots streams and a device-memory budget.
+ * cs_submit builds the request's plan (stream-ordered allocation on a free
+ * slot's stream, so it does not wait for running requests) and starts its
+ * sieve; it returns CS_EAGAIN when no slot is free or the plan's device memory
+ * would exceed the budget, in which case nothing was kept.  A request's work
+ * overlaps on the device with the requests already running.  cs_poll reports
+ * completion (and frees the slot); the bitset stays resident, readable through
+ * the borrowed plan of cs_server_plan, until cs_release. */
+cs_status cs_server_start(uint64_t budget_bytes, int max_slots, const cs_tuning *tune, cs_server_t *out);
+cs_status cs_submit(cs_server_t server, uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc,
+                    uint32_t SL, uint64_t L, uint64_t *ticket);
+cs_status cs_poll(cs_server_t server, uint64_t ticket, int *done);
+cs_status cs_server_plan(cs_server_t server, uint64_t ticket, cs_plan_t *plan);
+cs_status cs_release(cs_server_t server, uint64_t ticket);
+cs_status cs_server_usage(cs_server_t server, uint64_t *used_bytes, uint64_t *busy_slots, uint64_t *resident);
+cs_status cs_server_stop(cs_server_t server);   /* releases every ticket */
 
 /* ---- single steps of the path, on caller-owned DEVICE buffers ---------- */
 

@@ -32,7 +32,10 @@ _NAMES = {0: "CS_OK", -1: "CS_EINVAL", -2: "CS_ENOMEM", -3: "CS_EDEVICE", -4: "C
 # every symbol include/combsieve.h declares
 EXPORTS = ("cs_plan", "cs_sieve", "cs_sync", "cs_info", "cs_fetch_bitset", "cs_counts", "cs_stats",
            "cs_rows", "cs_columns", "cs_device_bitset", "cs_kernel_times", "cs_destroy",
-           "cs_last_error", "cs_primes", "cs_k_mod_p", "cs_modsolve", "cs_primes_static")
+           "cs_last_error", "cs_primes", "cs_k_mod_p", "cs_modsolve", "cs_primes_static",
+           "cs_batch_create", "cs_batch_run", "cs_batch_sync", "cs_batch_info", "cs_batch_destroy",
+           "cs_server_start", "cs_submit", "cs_poll", "cs_server_plan", "cs_release", "cs_server_usage",
+           "cs_server_stop")
 
 
 class CSError(RuntimeError):
@@ -54,7 +57,8 @@ class cs_info_t(ctypes.Structure):
                 ("tile_rows", ctypes.c_uint32), ("large_mode", ctypes.c_uint32),
                 ("narrow", ctypes.c_uint32), ("wheel", ctypes.c_uint32),
                 ("n_large_chunks", ctypes.c_uint64), ("launches_per_sieve", ctypes.c_uint64),
-                ("h2d_bytes", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64)]
+                ("h2d_bytes", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
+                ("est_cost", ctypes.c_uint64)]
 
 
 class cs_stats_t(ctypes.Structure):
@@ -98,6 +102,18 @@ def load(path: Optional[str] = None):
         lib.cs_primes_static.argtypes = [u64, u64, vp, u64, P64, vp]
         lib.cs_k_mod_p.argtypes = [u32, u64, vp, u64, vp, vp]
         lib.cs_modsolve.argtypes = [vp, vp, vp, vp, vp, u64, i32, vp]
+        lib.cs_batch_create.argtypes = [ctypes.POINTER(vp), i32, i32, ctypes.POINTER(vp)]
+        lib.cs_batch_run.argtypes = [vp, vp]
+        lib.cs_batch_sync.argtypes = [vp]
+        lib.cs_batch_info.argtypes = [vp, P64, P64]
+        lib.cs_batch_destroy.argtypes = [vp]
+        lib.cs_server_start.argtypes = [u64, i32, ctypes.POINTER(cs_tuning), ctypes.POINTER(vp)]
+        lib.cs_submit.argtypes = [vp, u32, u64, u64, u64, u32, u64, P64]
+        lib.cs_poll.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_int)]
+        lib.cs_server_plan.argtypes = [vp, u64, ctypes.POINTER(vp)]
+        lib.cs_release.argtypes = [vp, u64]
+        lib.cs_server_usage.argtypes = [vp, P64, P64, P64]
+        lib.cs_server_stop.argtypes = [vp]
         for n in EXPORTS:
             if n not in ("cs_device_bitset", "cs_last_error"):
                 getattr(lib, n).restype = i32
@@ -302,6 +318,97 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------- batch / server
+
+class Batch:
+    """A CUDA-graph batch over existing plans (cs_batch_*); plans must outlive it."""
+
+    def __init__(self, plans, n_streams=0):
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p.h.value for p in self.plans])
+        self.h = ctypes.c_void_p()
+        _check(load().cs_batch_create(arr, len(self.plans), n_streams, ctypes.byref(self.h)))
+        ns, nl = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load().cs_batch_info(self.h, ctypes.byref(ns), ctypes.byref(nl)))
+        self.n_streams, self.launches = int(ns.value), int(nl.value)
+
+    def run(self, stream=None):
+        _check(load().cs_batch_run(self.h, _stream_handle(stream)))
+        return self
+
+    def sync(self):
+        _check(load().cs_batch_sync(self.h))
+        return self
+
+    def close(self):
+        if self.h:
+            load().cs_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _BorrowedPlan(Plan):
+    def __init__(self, h):
+        self.h = h
+        self.info = cs_info(h)
+
+    def close(self):
+        self.h = None
+
+
+class Server:
+    """Continuous-batching request server (cs_server_*)."""
+
+    def __init__(self, budget_bytes, max_slots=8, **tuning):
+        self.h = ctypes.c_void_p()
+        t = make_tuning(**tuning) if tuning else None
+        _check(load().cs_server_start(budget_bytes, max_slots, ctypes.byref(t) if t else None,
+                                      ctypes.byref(self.h)))
+
+    def submit(self, P, d, M_start, M_inc, SL, L):
+        """Ticket, or None when the request is not admitted now (CS_EAGAIN)."""
+        t = ctypes.c_uint64()
+        rc = load().cs_submit(self.h, P, d, M_start, M_inc, SL, L, ctypes.byref(t))
+        if rc == CS_EAGAIN:
+            return None
+        _check(rc)
+        return int(t.value)
+
+    def poll(self, ticket) -> bool:
+        done = ctypes.c_int()
+        _check(load().cs_poll(self.h, ticket, ctypes.byref(done)))
+        return bool(done.value)
+
+    def plan(self, ticket) -> Plan:
+        h = ctypes.c_void_p()
+        _check(load().cs_server_plan(self.h, ticket, ctypes.byref(h)))
+        return _BorrowedPlan(h)
+
+    def release(self, ticket):
+        _check(load().cs_release(self.h, ticket))
+
+    def usage(self):
+        u, b, r = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load().cs_server_usage(self.h, ctypes.byref(u), ctypes.byref(b), ctypes.byref(r)))
+        return int(u.value), int(b.value), int(r.value)
+
+    def close(self):
+        if self.h:
+            load().cs_server_stop(self.h)
+            self.h = None
 
     def __del__(self):
         try:

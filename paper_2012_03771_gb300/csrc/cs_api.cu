@@ -93,7 +93,7 @@ struct cs_plan_s {
     std::vector<int64_t> x_of_col;
     std::vector<std::pair<uint64_t, uint64_t>> chunks;    // large-prime ranges (lo, hi]
     std::vector<uint32_t> chunk_seg;                      // m-segments per prime, per chunk
-    uint64_t large_cap = 0, small_cap = 0;
+    uint64_t large_cap = 0, small_cap = 0, est_cost = 0;
     int large_grid = 0;
     uint64_t h2d = 0, dev_bytes = 0;
     // device
@@ -109,6 +109,11 @@ struct cs_plan_s {
     cudaEvent_t done = nullptr;
     bool sieved = false;
     cs_status sticky = CS_OK;
+    // stream-ordered allocation (plans built by the request server): device
+    // buffers come from cudaMallocAsync on alloc_stream and go back with
+    // cudaFreeAsync, so building or freeing a plan does not wait for other work
+    cudaStream_t alloc_stream = nullptr;
+    bool async_alloc = false;
     // profiling
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[KC_N];
     size_t prof_used[KC_N] = {0, 0, 0, 0, 0};
@@ -120,13 +125,19 @@ struct cs_plan_s {
                 cudaEventDestroy(e.first);
                 cudaEventDestroy(e.second);
             }
-        for (void *p : allocs) cudaFree(p);
+        for (void *p : allocs) {
+            if (async_alloc)
+                cudaFreeAsync(p, alloc_stream);
+            else
+                cudaFree(p);
+        }
     }
 
     template <class T>
     cs_status dalloc(T **p, size_t count) {
         size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-        cudaError_t e = cudaMalloc((void **)p, bytes);
+        cudaError_t e = async_alloc ? cudaMallocAsync((void **)p, bytes, alloc_stream)
+                                    : cudaMalloc((void **)p, bytes);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
         allocs.push_back(*p);
         dev_bytes += bytes;
@@ -137,7 +148,11 @@ struct cs_plan_s {
         cs_status s = dalloc(p, v.size());
         if (s) return s;
         if (!v.empty()) {
-            cudaError_t e = cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+            // async mode: the plan builder synchronises alloc_stream before the
+            // host vectors go out of scope
+            cudaError_t e = async_alloc
+                                ? cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, alloc_stream)
+                                : cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
             if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy H2D");
             h2d += v.size() * sizeof(T);
         }
@@ -348,6 +363,25 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
     }
 
     pl->M_c = M_c; pl->W = W; pl->wpr = wpr; pl->S = S; pl->S32 = S32;
+    CS_CUDA(prepare_tile(optin));
+
+    // relative cost, for ordering instances in a batch: tile pairs, walk hits,
+    // large primes (each weighted by its measured per-unit time on a GB300)
+    {
+        auto pi = [](double x) { return x < 3 ? 0.0 : x / std::log(x); };
+        const double Td = (double)T, Ld = (double)std::max<uint64_t>(L, 2);
+        const double small = (double)M_c * std::max(0.0, pi((double)pl->small_hi) - pi((double)P));
+        double hits = 0, large = 0;
+        if (L > T && T > 2) {
+            hits = (double)M_inc * (double)S * std::log(std::log(Ld) / std::log(Td));
+            large = pi(Ld) - pi(Td);
+        }
+        // per-unit times measured on search_953: 7.4 ps per (row, small prime)
+        // pair, ~7 ps per walk hit, ~150 ps per large prime (generation, K mod p
+        // and the walk's solves), ~5 us per kernel launch
+        pl->est_cost = (uint64_t)(small * 7.4 + hits * 7.0 + large * 150.0 +
+                                  5e6 * (3.0 + 2.0 * (double)pl->chunks.size()));
+    }
 
     // device memory and tables
     DevPlan &dp = pl->dp;
@@ -409,6 +443,7 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
         pl->d_lp = a; pl->d_lr = b; pl->d_lv = c;
     }
     CS_CUDA(cudaEventCreateWithFlags(&pl->done, cudaEventDisableTiming));
+    if (pl->async_alloc) CS_CUDA(cudaStreamSynchronize(pl->alloc_stream));
     return CS_OK;
 }
 
@@ -452,14 +487,17 @@ struct Prof {
 
 }  // namespace
 
-extern "C" {
+namespace cs {
 
-cs_status cs_plan(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL,
-                  uint64_t L, const cs_tuning *tune, cs_plan_t *out) {
+cs_status plan_create(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL,
+                      uint64_t L, const cs_tuning *tune, cudaStream_t alloc_stream, bool async_alloc,
+                      cs_plan_t *out) {
     if (!out) return fail(CS_EINVAL, "out is NULL");
     *out = nullptr;
     cs_plan_s *pl = new (std::nothrow) cs_plan_s();
     if (!pl) return fail(CS_ENOMEM, "host allocation failed");
+    pl->alloc_stream = alloc_stream;
+    pl->async_alloc = async_alloc;
     cs_status s;
     try {
         s = build_plan(pl, P, d, M_start, M_inc, SL, L, tune);
@@ -473,6 +511,20 @@ cs_status cs_plan(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint
     *out = pl;
     g_err.clear();
     return CS_OK;
+}
+
+void plan_set_sieved(cs_plan_t pl, bool sieved) { pl->sieved = sieved; }
+bool plan_profiled(cs_plan_t pl) { return pl->tune.profile != 0; }
+cudaEvent_t plan_done_event(cs_plan_t pl) { return pl->done; }
+cs_status set_error(cs_status code, const char *msg) { return fail(code, msg); }
+
+}  // namespace cs
+
+extern "C" {
+
+cs_status cs_plan(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL,
+                  uint64_t L, const cs_tuning *tune, cs_plan_t *out) {
+    return cs::plan_create(P, d, M_start, M_inc, SL, L, tune, nullptr, false, out);
 }
 
 cs_status cs_sieve(cs_plan_t pl, void *stream) {
@@ -544,6 +596,7 @@ cs_status cs_info(cs_plan_t pl, cs_info_t *out) {
                               (pl->M_c ? 1 : 0) + 2 * pl->chunks.size();
     out->h2d_bytes = pl->h2d;
     out->device_bytes = pl->dev_bytes;
+    out->est_cost = pl->est_cost;
     return CS_OK;
 }
 

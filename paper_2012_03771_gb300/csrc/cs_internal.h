@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/combsieve.h"
+
 namespace cs {
 
 // device statistics, one uint64 each (index into Plan::d_stats)
@@ -94,6 +96,8 @@ struct TileConfig {
 };
 cudaError_t launch_tile(const DevPlan &pl, const TileConfig &tc, const SmallPrime *sp,
                         const unsigned long long *n_sp, uint64_t sp_cap, cudaStream_t stream);
+// sets k_tile's dynamic shared-memory limit (called when a plan is built)
+cudaError_t prepare_tile(int max_dynamic_smem);
 
 enum LargeMode { LARGE_PAPER = 1, LARGE_THREE_GAP = 2 };
 // n_seg: the m-range of every prime is split into n_seg segments walked by
@@ -110,5 +114,16 @@ cudaError_t launch_modsolve(const uint64_t *p, const uint64_t *K, const uint64_t
                             cudaStream_t stream);
 
 int sm_count();
+
+// ---- plan internals used by the batch and server runtime (cs_runtime.cu) ----
+// Builds a plan; with async_alloc its device memory is stream-ordered on
+// alloc_stream (cudaMallocAsync / cudaFreeAsync).
+cs_status plan_create(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL,
+                      uint64_t L, const cs_tuning *tune, cudaStream_t alloc_stream, bool async_alloc,
+                      cs_plan_t *out);
+void plan_set_sieved(cs_plan_t pl, bool sieved);
+bool plan_profiled(cs_plan_t pl);
+cudaEvent_t plan_done_event(cs_plan_t pl);
+cs_status set_error(cs_status code, const char *msg);
 
 }  // namespace cs

@@ -1,0 +1,312 @@
+// Batched and served execution of many independent sieve instances.
+//
+// The searches of Section 5 ("Real world searching") sieve many combinations
+// of P#/d and m-ranges of very uneven size.  Two runtimes share the GPU among
+// them:
+//
+// * Batch: a fixed set of plans, spread over worker streams with the longest
+//   first (greedy longest-processing-time assignment on each plan's cost
+//   estimate), the whole launch sequence captured once into a CUDA graph and
+//   replayed with one launch.
+// * Server: requests arrive over time; a request is admitted when a slot (a
+//   stream) is free and its device memory fits the budget, its plan is built
+//   with stream-ordered allocation and sieved on the slot's stream, so it
+//   overlaps with the requests already running; its bitset stays resident until
+//   the caller releases the ticket.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/combsieve.h"
+#include "cs_internal.h"
+
+using namespace cs;
+
+struct cs_batch_s {
+    std::vector<cs_plan_t> plans;
+    std::vector<cudaStream_t> streams;
+    cudaStream_t origin = nullptr;
+    cudaEvent_t fork = nullptr, done = nullptr;
+    std::vector<cudaEvent_t> join;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool launched = false;
+    uint64_t launches = 0;
+
+    ~cs_batch_s() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        for (auto e : join) cudaEventDestroy(e);
+        if (fork) cudaEventDestroy(fork);
+        if (done) cudaEventDestroy(done);
+        for (auto s : streams) cudaStreamDestroy(s);
+        if (origin) cudaStreamDestroy(origin);
+    }
+};
+
+struct ServerTicket {
+    cs_plan_t plan = nullptr;
+    int slot = -1;
+    uint64_t bytes = 0;
+};
+
+struct cs_server_s {
+    uint64_t budget = 0, used = 0;
+    std::vector<cudaStream_t> slots;
+    std::vector<uint64_t> slot_ticket;      // 0 = free
+    std::unordered_map<uint64_t, ServerTicket> tickets;
+    uint64_t next_ticket = 1;
+    cs_tuning tune{};
+    bool has_tune = false;
+    std::mutex mu;
+
+    ~cs_server_s() {
+        for (auto &kv : tickets) cs_destroy(kv.second.plan);
+        for (auto s : slots) cudaStreamDestroy(s);
+    }
+};
+
+namespace {
+
+cs_status cuda_err(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return CS_OK;
+    return set_error(e == cudaErrorMemoryAllocation ? CS_ENOMEM : CS_EDEVICE, what);
+}
+
+}  // namespace
+
+extern "C" {
+
+cs_status cs_batch_create(const cs_plan_t *plans, int n, int n_streams, cs_batch_t *out) {
+    if (!out || !plans || n <= 0) return set_error(CS_EINVAL, "need plans, n >= 1 and out");
+    *out = nullptr;
+    if (n_streams <= 0) n_streams = std::min(n, 16);
+    n_streams = std::min(std::max(n_streams, 1), std::min(n, 64));
+    std::vector<std::pair<uint64_t, int>> order;
+    for (int i = 0; i < n; i++) {
+        if (!plans[i]) return set_error(CS_EINVAL, "NULL plan in batch");
+        if (plan_profiled(plans[i])) return set_error(CS_EINVAL, "batched plans must not be built with profile = 1");
+        for (int j = 0; j < i; j++)
+            if (plans[j] == plans[i]) return set_error(CS_EINVAL, "a plan appears twice in the batch");
+        cs_info_t info;
+        cs_status s = cs_info(plans[i], &info);
+        if (s) return s;
+        order.push_back({info.est_cost, i});
+    }
+    std::sort(order.begin(), order.end(), [](auto &a, auto &b) { return a.first > b.first; });
+    // longest first onto the least-loaded stream
+    std::vector<std::vector<int>> lane(n_streams);
+    std::vector<uint64_t> load(n_streams, 0);
+    for (auto &o : order) {
+        int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        lane[k].push_back(o.second);
+        load[k] += o.first;
+    }
+
+    cs_batch_s *b = new (std::nothrow) cs_batch_s();
+    if (!b) return set_error(CS_ENOMEM, "host allocation failed");
+    b->plans.assign(plans, plans + n);
+    cs_status s = CS_OK;
+#define BT(call)                                          \
+    do {                                                  \
+        s = cuda_err((call), #call);                      \
+        if (s) { delete b; return s; }                    \
+    } while (0)
+    BT(cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking));
+    BT(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    BT(cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming));
+    for (int k = 0; k < n_streams; k++) {
+        cudaStream_t st;
+        BT(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        b->streams.push_back(st);
+        cudaEvent_t ev;
+        BT(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        b->join.push_back(ev);
+    }
+    BT(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
+    cs_status cap = CS_OK;
+    cudaError_t e = cudaEventRecord(b->fork, b->origin);
+    for (int k = 0; k < n_streams && e == cudaSuccess && !cap; k++) {
+        e = cudaStreamWaitEvent(b->streams[k], b->fork, 0);
+        for (int i : lane[k]) {
+            if (e != cudaSuccess || cap) break;
+            cap = cs_sieve(b->plans[i], b->streams[k]);
+            cs_info_t info;
+            if (!cap && !cs_info(b->plans[i], &info)) b->launches += info.launches_per_sieve;
+        }
+        if (e == cudaSuccess && !cap) e = cudaEventRecord(b->join[k], b->streams[k]);
+        if (e == cudaSuccess && !cap) e = cudaStreamWaitEvent(b->origin, b->join[k], 0);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(b->origin, &g);
+    b->graph = g;
+    for (cs_plan_t p : b->plans) plan_set_sieved(p, false);   // recorded, not run yet
+    if (cap) { delete b; return cap; }
+    BT(e);
+    BT(e2);
+    BT(cudaGraphInstantiate(&b->exec, b->graph, 0));
+#undef BT
+    *out = b;
+    return CS_OK;
+}
+
+cs_status cs_batch_run(cs_batch_t b, void *stream) {
+    if (!b) return set_error(CS_EINVAL, "batch is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    cs_status s = cuda_err(cudaGraphLaunch(b->exec, st), "cudaGraphLaunch");
+    if (s) return s;
+    s = cuda_err(cudaEventRecord(b->done, st), "cudaEventRecord");
+    if (s) return s;
+    for (cs_plan_t p : b->plans) plan_set_sieved(p, true);
+    b->launched = true;
+    return CS_OK;
+}
+
+cs_status cs_batch_sync(cs_batch_t b) {
+    if (!b) return set_error(CS_EINVAL, "batch is NULL");
+    if (!b->launched) return set_error(CS_ESTATE, "cs_batch_run has not been called");
+    cs_status s = cuda_err(cudaEventSynchronize(b->done), "cudaEventSynchronize");
+    if (s) return s;
+    for (cs_plan_t p : b->plans) {
+        s = cs_sync(p);
+        if (s) return s;
+    }
+    return CS_OK;
+}
+
+cs_status cs_batch_info(cs_batch_t b, uint64_t *n_streams, uint64_t *launches) {
+    if (!b) return set_error(CS_EINVAL, "batch is NULL");
+    if (n_streams) *n_streams = b->streams.size();
+    if (launches) *launches = b->launches;
+    return CS_OK;
+}
+
+cs_status cs_batch_destroy(cs_batch_t b) {
+    if (!b) return CS_OK;
+    if (b->launched) cudaEventSynchronize(b->done);
+    delete b;
+    return CS_OK;
+}
+
+// ------------------------------------------------------------------ server
+
+cs_status cs_server_start(uint64_t budget_bytes, int max_slots, const cs_tuning *tune, cs_server_t *out) {
+    if (!out || max_slots <= 0 || max_slots > 256 || budget_bytes == 0)
+        return set_error(CS_EINVAL, "need out, 1 <= max_slots <= 256 and a budget");
+    *out = nullptr;
+    cs_server_s *sv = new (std::nothrow) cs_server_s();
+    if (!sv) return set_error(CS_ENOMEM, "host allocation failed");
+    sv->budget = budget_bytes;
+    if (tune) {
+        sv->tune = *tune;
+        sv->tune.profile = 0;
+        sv->has_tune = true;
+    }
+    for (int i = 0; i < max_slots; i++) {
+        cudaStream_t st;
+        cs_status s = cuda_err(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "cudaStreamCreate");
+        if (s) { delete sv; return s; }
+        sv->slots.push_back(st);
+        sv->slot_ticket.push_back(0);
+    }
+    *out = sv;
+    return CS_OK;
+}
+
+cs_status cs_submit(cs_server_t sv, uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL,
+                    uint64_t L, uint64_t *ticket) {
+    if (!sv || !ticket) return set_error(CS_EINVAL, "NULL argument");
+    *ticket = 0;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    int slot = -1;
+    for (size_t i = 0; i < sv->slots.size(); i++)
+        if (!sv->slot_ticket[i]) { slot = (int)i; break; }
+    if (slot < 0) return set_error(CS_EAGAIN, "no free slot");
+    cudaStream_t st = sv->slots[slot];
+    cs_plan_t plan = nullptr;
+    cs_status s = plan_create(P, d, M_start, M_inc, SL, L, sv->has_tune ? &sv->tune : nullptr, st, true, &plan);
+    if (s) return s;
+    cs_info_t info;
+    cs_info(plan, &info);
+    if (sv->used + info.device_bytes > sv->budget) {
+        cs_destroy(plan);
+        return set_error(CS_EAGAIN, "device memory budget exhausted");
+    }
+    s = cs_sieve(plan, st);
+    if (s) {
+        cs_destroy(plan);
+        return s;
+    }
+    uint64_t id = sv->next_ticket++;
+    sv->tickets[id] = ServerTicket{plan, slot, info.device_bytes};
+    sv->slot_ticket[slot] = id;
+    sv->used += info.device_bytes;
+    *ticket = id;
+    return CS_OK;
+}
+
+cs_status cs_poll(cs_server_t sv, uint64_t ticket, int *done) {
+    if (!sv || !done) return set_error(CS_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->tickets.find(ticket);
+    if (it == sv->tickets.end()) return set_error(CS_EINVAL, "unknown ticket");
+    cudaError_t e = cudaEventQuery(plan_done_event(it->second.plan));
+    if (e == cudaErrorNotReady) {
+        *done = 0;
+        return CS_OK;
+    }
+    if (e != cudaSuccess) return cuda_err(e, "cudaEventQuery");
+    *done = 1;
+    // the result stays resident; the slot (stream) is free for the next request
+    if (it->second.slot >= 0) {
+        sv->slot_ticket[it->second.slot] = 0;
+        it->second.slot = -1;
+    }
+    return CS_OK;
+}
+
+cs_status cs_server_plan(cs_server_t sv, uint64_t ticket, cs_plan_t *plan) {
+    if (!sv || !plan) return set_error(CS_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->tickets.find(ticket);
+    if (it == sv->tickets.end()) return set_error(CS_EINVAL, "unknown ticket");
+    *plan = it->second.plan;
+    return CS_OK;
+}
+
+cs_status cs_release(cs_server_t sv, uint64_t ticket) {
+    if (!sv) return set_error(CS_EINVAL, "server is NULL");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->tickets.find(ticket);
+    if (it == sv->tickets.end()) return set_error(CS_EINVAL, "unknown ticket");
+    cs_destroy(it->second.plan);
+    if (it->second.slot >= 0) sv->slot_ticket[it->second.slot] = 0;
+    sv->used -= it->second.bytes;
+    sv->tickets.erase(it);
+    return CS_OK;
+}
+
+cs_status cs_server_usage(cs_server_t sv, uint64_t *used_bytes, uint64_t *busy_slots, uint64_t *resident) {
+    if (!sv) return set_error(CS_EINVAL, "server is NULL");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (used_bytes) *used_bytes = sv->used;
+    if (busy_slots) {
+        uint64_t b = 0;
+        for (auto t : sv->slot_ticket) b += t != 0;
+        *busy_slots = b;
+    }
+    if (resident) *resident = sv->tickets.size();
+    return CS_OK;
+}
+
+cs_status cs_server_stop(cs_server_t sv) {
+    if (!sv) return CS_OK;
+    delete sv;
+    return CS_OK;
+}
+
+}  // extern "C"

@@ -171,12 +171,16 @@ cudaError_t launch_tile(const DevPlan &pl, const TileConfig &tc, const SmallPrim
     const uint64_t row_blocks = (pl.M_c + tc.rows - 1) / tc.rows;
     const uint64_t blocks = row_blocks * tc.n_chunks;
     const size_t smem = (size_t)(tc.rows + 1) * tc.max_words * sizeof(uint32_t);
-    cudaError_t e = cudaFuncSetAttribute(k_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     TileArgs a{pl, tc, sp, n_sp, sp_cap};
     if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
     k_tile<<<(unsigned)blocks, TILE_THREADS, smem, stream>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t prepare_tile(int max_dynamic_smem) {
+    // raise the kernel's dynamic shared-memory limit once, outside any launch
+    // sequence (so that cs_sieve itself enqueues launches only)
+    return cudaFuncSetAttribute(k_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dynamic_smem);
 }
 
 }  // namespace cs

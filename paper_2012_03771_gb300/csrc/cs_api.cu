@@ -562,7 +562,14 @@ cs_status cs_sieve(cs_plan_t pl, void *stream) {
     if ((s = prof.begin(KC_FINAL))) return s;
     CS_CUDA(launch_final(dp, st));
     if ((s = prof.end())) return s;
-    CS_CUDA(cudaEventRecord(pl->done, st));
+    // inside a stream capture the completion event becomes an event-record node
+    // of the graph, so that it is recorded each time the graph runs
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CS_CUDA(cudaStreamIsCapturing(st, &cap));
+    if (cap == cudaStreamCaptureStatusActive)
+        CS_CUDA(cudaEventRecordWithFlags(pl->done, st, cudaEventRecordExternal));
+    else
+        CS_CUDA(cudaEventRecord(pl->done, st));
     pl->sieved = true;
     return CS_OK;
 }

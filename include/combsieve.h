@@ -135,6 +135,11 @@ cs_status cs_info(cs_plan_t plan, cs_info_t *out);
  * plan's last cs_sieve. */
 cs_status cs_fetch_bitset(cs_plan_t plan, uint64_t *host, size_t n_words);
 
+/* Rows [row0, row0 + n_rows) of the bitset (n_rows * words_per_row words) to
+ * caller-owned host memory, for consumers that need only part of a large
+ * bitset.  CS_EINVAL if the range exceeds M_c.  Waits. */
+cs_status cs_fetch_rows(cs_plan_t plan, uint64_t row0, uint64_t n_rows, uint64_t *host, size_t n_words);
+
 /* Per-row survivor counts (n_rows >= M_c uint32, may be NULL), F and hash
  * (either may be NULL), copied to caller-owned host memory.  Waits. */
 cs_status cs_counts(cs_plan_t plan, uint32_t *per_row, size_t n_rows, uint64_t *F, uint64_t *hash);

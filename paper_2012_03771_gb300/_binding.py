@@ -35,7 +35,7 @@ EXPORTS = ("cs_plan", "cs_sieve", "cs_sync", "cs_info", "cs_fetch_bitset", "cs_c
            "cs_last_error", "cs_primes", "cs_k_mod_p", "cs_modsolve", "cs_primes_static",
            "cs_batch_create", "cs_batch_run", "cs_batch_sync", "cs_batch_info", "cs_batch_destroy",
            "cs_server_start", "cs_submit", "cs_poll", "cs_server_plan", "cs_release", "cs_server_usage",
-           "cs_server_stop")
+           "cs_server_stop", "cs_fetch_rows")
 
 
 class CSError(RuntimeError):
@@ -88,6 +88,7 @@ def load(path: Optional[str] = None):
         lib.cs_sync.argtypes = [vp]
         lib.cs_info.argtypes = [vp, ctypes.POINTER(cs_info_t)]
         lib.cs_fetch_bitset.argtypes = [vp, vp, sz]
+        lib.cs_fetch_rows.argtypes = [vp, u64, u64, vp, sz]
         lib.cs_counts.argtypes = [vp, vp, sz, P64, P64]
         lib.cs_stats.argtypes = [vp, ctypes.POINTER(cs_stats_t)]
         lib.cs_rows.argtypes = [vp, vp, sz]
@@ -183,6 +184,12 @@ def cs_info(plan) -> cs_info_t:
 
 def cs_fetch_bitset(plan, out: np.ndarray):
     _check(load().cs_fetch_bitset(plan, _ptr(out), out.size))
+    return out
+
+
+def cs_fetch_rows(plan, row0: int, out: np.ndarray):
+    """Rows row0 .. row0 + out.shape[0] - 1 into out ([n, words_per_row] uint64)."""
+    _check(load().cs_fetch_rows(plan, row0, out.shape[0], _ptr(out), out.size))
     return out
 
 
@@ -289,6 +296,10 @@ class Plan:
             out = np.zeros((self.M_c, self.wpr), dtype=np.uint64)
         cs_fetch_bitset(self.h, out.reshape(-1))
         return out
+
+    def fetch_rows(self, row0, n):
+        out = np.zeros((n, self.wpr), dtype=np.uint64)
+        return cs_fetch_rows(self.h, row0, out)
 
     def counts(self):
         per_row = np.zeros(max(self.M_c, 1), dtype=np.uint32)

@@ -621,6 +621,21 @@ cs_status cs_fetch_bitset(cs_plan_t pl, uint64_t *host, size_t n_words) {
     return CS_OK;
 }
 
+cs_status cs_fetch_rows(cs_plan_t pl, uint64_t row0, uint64_t n_rows, uint64_t *host, size_t n_words) {
+    if (!pl) return fail(CS_EINVAL, "plan is NULL");
+    if (row0 > pl->M_c || n_rows > pl->M_c - row0) return fail(CS_EINVAL, "row range beyond M_c");
+    const uint64_t need = n_rows * pl->wpr;
+    if (need && !host) return fail(CS_EINVAL, "host is NULL");
+    if (n_words < need) return fail(CS_ESIZE, "host buffer smaller than n_rows * words_per_row");
+    cs_status s = wait_plan(pl);
+    if (s) return s;
+    if (need) {
+        CS_CUDA(cudaMemcpyAsync(host, pl->dp.bits + row0 * pl->wpr, need * 8, cudaMemcpyDeviceToHost, pl->stream));
+        CS_CUDA(cudaStreamSynchronize(pl->stream));
+    }
+    return CS_OK;
+}
+
 cs_status cs_counts(cs_plan_t pl, uint32_t *per_row, size_t n_rows, uint64_t *F, uint64_t *hash) {
     if (!pl) return fail(CS_EINVAL, "plan is NULL");
     if (per_row && n_rows < pl->M_c) return fail(CS_ESIZE, "per_row smaller than M_c");

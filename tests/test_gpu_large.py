@@ -1,0 +1,77 @@
+"""The large single search at full size: K = 1019#/210, m in [1.64e8, 1.74e8)
+coprime to 210 (2.29M rows), X = 25000, primes up to 1e11 generated on the
+device (64-bit arithmetic), 4.77 GB device bitset.  Sampled rows against the
+oracle (one by one, all 4.1e9 primes), the 36,702 record gap of Section 1.1, and
+size-independent properties."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle.oracle as O
+import paper_2012_03771_gb300 as cs
+from paper_2012_03771_gb300 import workloads
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def large():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2012_03771_gb300 import build
+    build.build()
+    cs.load()
+    torch.cuda.set_device(0)
+    prm = workloads.LARGE_1019
+    with cs.Plan(*prm.as_tuple()) as p:
+        p.sieve(torch.cuda.current_stream()).sync()
+        out = dict(rows=p.rows(), cols=p.columns(), stats=p.stats(), info=p.info)
+        out["counts"], out["F"], out["hash"] = p.counts()
+        m_rec = workloads.RECORD_1019[0]
+        i_rec = int(np.searchsorted(out["rows"], m_rec))
+        assert out["rows"][i_rec] == m_rec
+        n = len(out["rows"])
+        out["sample"] = sorted({0, i_rec, n // 2, n - 1})
+        # only the sampled rows come back (the whole bitset is 4.77 GB)
+        out["bits"] = {i: p.fetch_rows(i, 1)[0] for i in out["sample"]}
+    return prm, out
+
+
+def test_large_sampled_rows_match_oracle(large):
+    prm, out = large
+    pick = out["sample"]
+    ref, F, _ = O.sieve(prm.P, prm.d, prm.SL, prm.L, [int(out["rows"][i]) for i in pick])
+    for k, i in enumerate(pick):
+        assert np.array_equal(out["bits"][i], ref[k]), i
+        assert int(out["counts"][i]) == int(O.row_counts(ref[k:k + 1])[0])
+
+
+def test_large_record_gap(large):
+    prm, out = large
+    m, x_lo, gap = workloads.RECORD_1019
+    i = int(np.searchsorted(out["rows"], m))
+    xs = out["cols"]
+    row = O.unpack_row(out["bits"][i], len(xs))
+    alive = {int(x) for x, b in zip(xs, row) if b}
+    N = m * math.prod(q for q in O._simple_primes(prm.P) if prm.d % q)
+    x_hi = x_lo + gap
+    assert x_lo in alive and x_hi in alive
+    assert pow(2, N + x_lo - 1, N + x_lo) == 1 and pow(2, N + x_hi - 1, N + x_hi) == 1
+    inside = [x for x in alive if x_lo < x < x_hi]
+    assert inside and not any(pow(2, N + x - 1, N + x) == 1 for x in inside)
+
+
+def test_large_invariants(large):
+    prm, out = large
+    st = out["stats"]
+    assert out["info"].narrow == 0
+    assert st["F"] == out["F"] and st["survivors"] == int(out["counts"].sum())
+    T = int(out["info"].threshold)
+    n_large, _, inv = O.prime_stats(T, prm.L)
+    assert st["n_large_primes"] == n_large                 # every prime in (T, 1e11] generated
+    S = 2 * prm.SL + 1
+    expect_hits = prm.M_inc * S * inv                       # Section 3.2: M S sum 1/p
+    assert abs(st["hits_all"] - expect_hits) < 0.005 * expect_hits

@@ -26,6 +26,10 @@ sys.path.insert(0, ROOT)
 
 from paper_2012_03771_gb300 import workloads  # noqa: E402
 
+def metric_of(params) -> str:
+    return f"enumerated factors/s at L={params.L:.0e} (bit-exact bitset + per-m counts)"
+
+
 METRIC = "enumerated factors/s at L=1e9 (bit-exact bitset + per-m counts)"
 UNIT = "factors/s"
 KC_NAMES = ["gen_small", "tile_sieve", "gen_large", "large_walk", "final"]
@@ -127,18 +131,18 @@ def run_reference(args, params):
         ts += dt
     value = Fs / ts
     sample = f"{nr} of the search's coprime m per step (evenly spaced), all primes <= L"
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": metric_of(params), "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * ts / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-            "data": "synthetic", "config": _config(params, None),
+            "data": "synthetic", "config": _config(params, None, args.config),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def _config(params, info):
-    c = {"workload": f"search_953: K=953#/210, m in [{params.M_start}, {params.M_start + params.M_inc}) "
-                     f"coprime to 210, X={params.SL}, primes {params.P} < p <= {params.L}",
+def _config(params, info, name="search_953"):
+    c = {"workload": f"{name}: K={params.P}#/{params.d}, m in [{params.M_start}, {params.M_start + params.M_inc}) "
+                     f"coprime to {params.d}, X={params.SL}, primes {params.P} < p <= {params.L}",
          "P": params.P, "d": params.d, "M_start": params.M_start, "M_inc": params.M_inc, "SL": params.SL,
          "L": params.L, "parallelism": "replicas (independent m-ranges per rank)",
          "l2": "flushed between steps (256 MB device write)"}
@@ -263,11 +267,11 @@ def run_cuda(args, params):
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "metric": metric_of(params), "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32" if info.narrow else "u64",
             "data": "synthetic (parameters of the paper-shaped search; primes generated on device)",
-            "config": _config(params, info),
+            "config": _config(params, info, args.config),
             "intervals_per_s": intervals_s,
             "F_per_step": int(F_ref), "hash": f"{h_ref:#018x}",
             "stats": stats,

@@ -54,10 +54,24 @@ struct ServerTicket {
     uint64_t bytes = 0;
 };
 
+namespace {
+// Priority level of a request from its cost estimate (about picoseconds of
+// device time): below 1 ms level 0, below 10 ms level 1, and so on.
+int level_of(uint64_t est_cost, int n_levels) {
+    double ms = (double)est_cost * 1e-9;
+    int lv = 0;
+    for (double lim = 1.0; lv < n_levels - 1 && ms >= lim; lim *= 10.0) lv++;
+    return lv;
+}
+}  // namespace
+
 struct cs_server_s {
     uint64_t budget = 0, used = 0;
+    // slot k owns one stream per priority level: slots[k * n_levels + level];
+    // level 0 is the highest priority and takes the cheapest requests
     std::vector<cudaStream_t> slots;
-    std::vector<uint64_t> slot_ticket;      // 0 = free
+    int n_levels = 1;
+    std::vector<uint64_t> slot_ticket;      // per slot, 0 = free
     std::unordered_map<uint64_t, ServerTicket> tickets;
     uint64_t next_ticket = 1;
     cs_tuning tune{};
@@ -206,11 +220,19 @@ cs_status cs_server_start(uint64_t budget_bytes, int max_slots, const cs_tuning 
         sv->tune.profile = 0;
         sv->has_tune = true;
     }
+    int least = 0, greatest = 0;
+    cs_status s0 = cuda_err(cudaDeviceGetStreamPriorityRange(&least, &greatest), "cudaDeviceGetStreamPriorityRange");
+    if (s0) { delete sv; return s0; }
+    sv->n_levels = std::min(4, least - greatest + 1);   // greatest is numerically lowest
+    if (sv->n_levels < 1) sv->n_levels = 1;
     for (int i = 0; i < max_slots; i++) {
-        cudaStream_t st;
-        cs_status s = cuda_err(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "cudaStreamCreate");
-        if (s) { delete sv; return s; }
-        sv->slots.push_back(st);
+        for (int lv = 0; lv < sv->n_levels; lv++) {
+            cudaStream_t st;
+            cs_status s = cuda_err(cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, greatest + lv),
+                                   "cudaStreamCreateWithPriority");
+            if (s) { delete sv; return s; }
+            sv->slots.push_back(st);
+        }
         sv->slot_ticket.push_back(0);
     }
     *out = sv;
@@ -223,12 +245,14 @@ cs_status cs_submit(cs_server_t sv, uint32_t P, uint64_t d, uint64_t M_start, ui
     *ticket = 0;
     std::lock_guard<std::mutex> lk(sv->mu);
     int slot = -1;
-    for (size_t i = 0; i < sv->slots.size(); i++)
+    for (size_t i = 0; i < sv->slot_ticket.size(); i++)
         if (!sv->slot_ticket[i]) { slot = (int)i; break; }
     if (slot < 0) return set_error(CS_EAGAIN, "no free slot");
-    cudaStream_t st = sv->slots[slot];
+    // build on the slot's lowest-priority stream, sieve on the stream of the
+    // request's priority level (both belong to the slot, which is idle)
+    cudaStream_t st_alloc = sv->slots[slot * sv->n_levels + sv->n_levels - 1];
     cs_plan_t plan = nullptr;
-    cs_status s = plan_create(P, d, M_start, M_inc, SL, L, sv->has_tune ? &sv->tune : nullptr, st, true, &plan);
+    cs_status s = plan_create(P, d, M_start, M_inc, SL, L, sv->has_tune ? &sv->tune : nullptr, st_alloc, true, &plan);
     if (s) return s;
     cs_info_t info;
     cs_info(plan, &info);
@@ -236,6 +260,7 @@ cs_status cs_submit(cs_server_t sv, uint32_t P, uint64_t d, uint64_t M_start, ui
         cs_destroy(plan);
         return set_error(CS_EAGAIN, "device memory budget exhausted");
     }
+    cudaStream_t st = sv->slots[slot * sv->n_levels + level_of(info.est_cost, sv->n_levels)];
     s = cs_sieve(plan, st);
     if (s) {
         cs_destroy(plan);

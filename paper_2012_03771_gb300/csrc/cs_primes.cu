@@ -18,7 +18,8 @@ namespace cs {
 
 namespace {
 
-constexpr uint32_t SEG = 1u << 17;          // odd numbers per segment
+constexpr uint32_t SEG = 1u << 17;          // odd numbers per segment (maximum)
+constexpr uint32_t SEG_MIN = 1u << 12;      // smallest segment: 8 warps x 16-word batches
 constexpr uint32_t SEG_WORDS = SEG / 32;
 constexpr uint32_t GEN_THREADS = 256;
 constexpr uint32_t GEN_WARPS = GEN_THREADS / 32;
@@ -31,6 +32,7 @@ enum Kind { KIND_SMALL = 0, KIND_LARGE32 = 1, KIND_LARGE64 = 2, KIND_LIST = 3 };
 struct GenArgs {
     uint64_t i_begin, i_end;      // odd indices [i_begin, i_end): numbers 2i+1
     uint64_t n_seg;
+    uint32_t seg;                 // odd numbers per segment (multiple of SEG_MIN, <= SEG)
     bool emit_two;                // 2 is in range
     const uint32_t *base;         // odd base primes, ascending
     uint32_t n_base;
@@ -151,12 +153,13 @@ __global__ void __launch_bounds__(GEN_THREADS) k_gen(const GenArgs a) {
     }
 
     for (uint64_t s = blockIdx.x; s < a.n_seg; s += gridDim.x) {
-        const uint64_t i0 = a.i_begin + s * SEG;
-        const uint64_t i1 = min(i0 + SEG, a.i_end);
+        const uint64_t i0 = a.i_begin + s * a.seg;
+        const uint64_t i1 = min(i0 + a.seg, a.i_end);
+        const uint32_t seg_words = a.seg / 32;
         const uint32_t len = (uint32_t)(i1 - i0);
         const uint64_t n_first = 2 * i0 + 1;
         const uint64_t n_last = 2 * (i1 - 1) + 1;
-        for (uint32_t w = threadIdx.x; w < SEG_WORDS; w += GEN_THREADS) {
+        for (uint32_t w = threadIdx.x; w < seg_words; w += GEN_THREADS) {
             uint32_t v = 0;
             uint32_t lo = w * 32;
             if (lo + 32 > len) v = lo >= len ? 0xffffffffu : (0xffffffffu << (len - lo));
@@ -197,7 +200,7 @@ __global__ void __launch_bounds__(GEN_THREADS) k_gen(const GenArgs a) {
         __syncthreads();
 
         // extract: each warp owns a contiguous run of words
-        const uint32_t wpw = SEG_WORDS / GEN_WARPS;
+        const uint32_t wpw = seg_words / GEN_WARPS;
         uint32_t qlen = 0;
         for (uint32_t w0 = warp * wpw; w0 < (warp + 1) * wpw; w0 += BATCH) {
             uint32_t w = w0 + lane;
@@ -251,7 +254,14 @@ GenArgs make_args(uint64_t lo, uint64_t hi, const uint32_t *base, uint32_t n_bas
     }
     a.i_begin = (lo + 1) / 2;
     a.i_end = (hi + 1) / 2;
-    a.n_seg = a.i_end > a.i_begin ? (a.i_end - a.i_begin + SEG - 1) / SEG : 0;
+    // segment size: enough segments for every SM to get several, within
+    // [SEG_MIN, SEG]
+    const uint64_t odds = a.i_end > a.i_begin ? a.i_end - a.i_begin : 0;
+    uint64_t want = odds / ((uint64_t)sm_count() * 4);
+    uint32_t seg = SEG_MIN;
+    while (seg < SEG && seg < want) seg *= 2;
+    a.seg = seg;
+    a.n_seg = odds ? (odds + seg - 1) / seg : 0;
     a.emit_two = lo < 2 && hi >= 2;
     return a;
 }

@@ -327,7 +327,7 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
     int dev = 0, optin = 0;
     CS_CUDA(cudaGetDevice(&dev));
     CS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    const uint64_t budget = std::min<uint64_t>((uint64_t)optin, 200 * 1024) / 4;   // words
+    const uint64_t budget = (std::min<uint64_t>((uint64_t)optin, 200 * 1024) - tile_stage_bytes()) / 4;   // words
     std::vector<uint32_t> chunk_tab;
     uint32_t TR = pl->tune.tile_rows;
     if (TR && (TR > 32 || (TR & (TR - 1)))) return fail(CS_EINVAL, "tile_rows must be 1..32, a power of 2");

@@ -98,6 +98,8 @@ cudaError_t launch_tile(const DevPlan &pl, const TileConfig &tc, const SmallPrim
                         const unsigned long long *n_sp, uint64_t sp_cap, cudaStream_t stream);
 // sets k_tile's dynamic shared-memory limit (called when a plan is built)
 cudaError_t prepare_tile(int max_dynamic_smem);
+// shared memory the tile kernel uses besides the tile itself
+size_t tile_stage_bytes();
 
 enum LargeMode { LARGE_PAPER = 1, LARGE_THREE_GAP = 2 };
 // n_seg: the m-range of every prime is split into n_seg segments walked by

@@ -21,7 +21,8 @@ namespace cs {
 
 namespace {
 
-constexpr int TILE_THREADS = 512;
+constexpr int TILE_THREADS = 1024;
+constexpr int SP_STAGE = 1024;      // small-prime records staged in shared memory at a time
 constexpr int TILE_WARPS = TILE_THREADS / 32;
 
 struct TileArgs {
@@ -98,9 +99,12 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile(const TileArgs a) {
     }
     __syncthreads();
 
-    // 2. small primes: lane -> row (lane % TR), prime (lane / TR) of this warp's group
+    // 2. small primes: lane -> row (lane % TR), prime (lane / TR) of this warp's
+    //    group; the prime records are staged through shared memory so that the
+    //    inner loop reads them with shared-memory latency
     unsigned long long F = 0;
     {
+        SmallPrime *stage = reinterpret_cast<SmallPrime *>(smem + (TR + 1) * a.tc.max_words);
         const uint64_t n = min((uint64_t)*a.n_sp, a.sp_cap);
         const uint32_t pp = 32 / TR;
         const uint32_t r = lane % TR, sub = lane / TR;
@@ -109,27 +113,33 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile(const TileArgs a) {
         unsigned __int128 lowest = 0;
         if (pl.small_n) lowest = (unsigned __int128)(pl.M_start + moff) * pl.K64 - pl.SL;
         const uint32_t two_sl = 2 * pl.SL;
-        for (uint64_t base = (uint64_t)warp * pp; base < n; base += (uint64_t)TILE_WARPS * pp) {
-            const uint64_t i = base + sub;
-            if (!row_ok || i >= n) continue;
-            const SmallPrime e = a.sp[i];
-            uint32_t v;
-            if (e.p == 2) {
-                v = (e.v0 + moff) & 1u;
-            } else {
-                v = e.v0 + mont32_mul(e.rt, moff, e.p, e.pinv);
-                if (v >= e.p) v -= e.p;
-            }
-            if (v > two_sl) continue;
-            int32_t z = (int32_t)(two_sl - v);
-            if ((uint32_t)z >= z1) z -= (int32_t)(((uint32_t)z - z1) / e.p + 1) * (int32_t)e.p;
-            for (; z >= (int32_t)z0; z -= (int32_t)e.p) {
-                const uint32_t zz = (uint32_t)z - zb;
-                const uint32_t bit = 1u << (zz & 31);
-                if (!(mask[zz >> 5] & bit)) continue;
-                if (pl.small_n && lowest + (unsigned)z == (unsigned __int128)e.p) continue;
-                atomicAnd(&tile[r * nw + (zz >> 5)], ~bit);
-                F++;
+        for (uint64_t c0 = 0; c0 < n; c0 += SP_STAGE) {
+            const uint32_t cn = (uint32_t)min((uint64_t)SP_STAGE, n - c0);
+            __syncthreads();
+            for (uint32_t k = threadIdx.x; k < cn; k += TILE_THREADS) stage[k] = a.sp[c0 + k];
+            __syncthreads();
+            for (uint32_t base = warp * pp; base < cn; base += TILE_WARPS * pp) {
+                const uint32_t i = base + sub;
+                if (!row_ok || i >= cn) continue;
+                const SmallPrime e = stage[i];
+                uint32_t v;
+                if (e.p == 2) {
+                    v = (e.v0 + moff) & 1u;
+                } else {
+                    v = e.v0 + mont32_mul(e.rt, moff, e.p, e.pinv);
+                    if (v >= e.p) v -= e.p;
+                }
+                if (v > two_sl) continue;
+                int32_t z = (int32_t)(two_sl - v);
+                if ((uint32_t)z >= z1) z -= (int32_t)(((uint32_t)z - z1) / e.p + 1) * (int32_t)e.p;
+                for (; z >= (int32_t)z0; z -= (int32_t)e.p) {
+                    const uint32_t zz = (uint32_t)z - zb;
+                    const uint32_t bit = 1u << (zz & 31);
+                    if (!(mask[zz >> 5] & bit)) continue;
+                    if (pl.small_n && lowest + (unsigned)z == (unsigned __int128)e.p) continue;
+                    atomicAnd(&tile[r * nw + (zz >> 5)], ~bit);
+                    F++;
+                }
             }
         }
     }
@@ -170,12 +180,14 @@ cudaError_t launch_tile(const DevPlan &pl, const TileConfig &tc, const SmallPrim
     if (pl.M_c == 0 || pl.W == 0) return cudaSuccess;
     const uint64_t row_blocks = (pl.M_c + tc.rows - 1) / tc.rows;
     const uint64_t blocks = row_blocks * tc.n_chunks;
-    const size_t smem = (size_t)(tc.rows + 1) * tc.max_words * sizeof(uint32_t);
+    const size_t smem = (size_t)(tc.rows + 1) * tc.max_words * sizeof(uint32_t) + SP_STAGE * sizeof(SmallPrime);
     TileArgs a{pl, tc, sp, n_sp, sp_cap};
     if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
     k_tile<<<(unsigned)blocks, TILE_THREADS, smem, stream>>>(a);
     return cudaGetLastError();
 }
+
+size_t tile_stage_bytes() { return SP_STAGE * sizeof(SmallPrime); }
 
 cudaError_t prepare_tile(int max_dynamic_smem) {
     // raise the kernel's dynamic shared-memory limit once, outside any launch

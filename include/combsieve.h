@@ -49,6 +49,7 @@ extern "C" {
 typedef struct cs_plan_s *cs_plan_t;
 typedef struct cs_batch_s *cs_batch_t;
 typedef struct cs_server_s *cs_server_t;
+typedef struct cs_cache_s *cs_cache_t;
 typedef int cs_status;
 
 #define CS_OK 0
@@ -165,6 +166,25 @@ cs_status cs_destroy(cs_plan_t plan);
 
 /* Message for the last error on the calling thread ("" if none). */
 const char *cs_last_error(void);
+
+/* ---- residue cache ---------------------------------------------------------
+ * Device-resident primes p <= L_max with r = K mod p for one K = P#/d
+ * (Section 3.1's cached residue, kept for many searches with the same K).
+ * Memory: about 8 bytes per prime below 2^30 and 16 above, plus slack (for
+ * L_max = 1e10 about 8 GB).  cs_cache_fill enqueues the generation of all
+ * primes on `stream` (a few milliseconds per 1e9 of range).  Plans built with
+ * cs_plan_cached read their large primes from the cache instead of generating
+ * them: the cache must be filled before their cs_sieve is enqueued (cs_sieve
+ * orders itself after the fill with events) and must outlive them.  A batch
+ * whose plans use caches fills those caches itself at every cs_batch_run. */
+cs_status cs_cache_create(uint32_t P, uint64_t d, uint64_t L_max, cs_cache_t *out);
+cs_status cs_cache_fill(cs_cache_t cache, void *stream);
+cs_status cs_cache_info(cs_cache_t cache, uint64_t *n_chunks, uint64_t *device_bytes, uint64_t *n_primes);
+cs_status cs_cache_destroy(cs_cache_t cache);
+/* cs_plan with its large primes taken from `cache` (same P and d, L <= L_max);
+ * the output is identical to cs_plan's. */
+cs_status cs_plan_cached(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL,
+                         uint64_t L, const cs_tuning *tune, cs_cache_t cache, cs_plan_t *out);
 
 /* ---- batched execution ---------------------------------------------------
  * Many independent searches of uneven size (Section 5, "Real world searching")

@@ -35,7 +35,8 @@ EXPORTS = ("cs_plan", "cs_sieve", "cs_sync", "cs_info", "cs_fetch_bitset", "cs_c
            "cs_last_error", "cs_primes", "cs_k_mod_p", "cs_modsolve", "cs_primes_static",
            "cs_batch_create", "cs_batch_run", "cs_batch_sync", "cs_batch_info", "cs_batch_destroy",
            "cs_server_start", "cs_submit", "cs_poll", "cs_server_plan", "cs_release", "cs_server_usage",
-           "cs_server_stop", "cs_fetch_rows")
+           "cs_server_stop", "cs_fetch_rows", "cs_cache_create", "cs_cache_fill", "cs_cache_info",
+           "cs_cache_destroy", "cs_plan_cached")
 
 
 class CSError(RuntimeError):
@@ -115,6 +116,12 @@ def load(path: Optional[str] = None):
         lib.cs_release.argtypes = [vp, u64]
         lib.cs_server_usage.argtypes = [vp, P64, P64, P64]
         lib.cs_server_stop.argtypes = [vp]
+        lib.cs_cache_create.argtypes = [u32, u64, u64, ctypes.POINTER(vp)]
+        lib.cs_cache_fill.argtypes = [vp, vp]
+        lib.cs_cache_info.argtypes = [vp, P64, P64, P64]
+        lib.cs_cache_destroy.argtypes = [vp]
+        lib.cs_plan_cached.argtypes = [u32, u64, u64, u64, u32, u64, ctypes.POINTER(cs_tuning), vp,
+                                       ctypes.POINTER(vp)]
         for n in EXPORTS:
             if n not in ("cs_device_bitset", "cs_last_error"):
                 getattr(lib, n).restype = i32
@@ -262,13 +269,50 @@ def cs_modsolve(p_ptr, K_ptr, L_ptr, R_ptr, m_ptr, n, narrow, stream=None):
 
 # ---------------------------------------------------------------- wrapper
 
-class Plan:
-    """One sieve instance: owns a cs_plan_t and its device memory."""
+class Cache:
+    """Device-resident primes and K mod p for one K = P#/d (cs_cache_*)."""
 
-    def __init__(self, P, d, M_start, M_inc, SL, L, **tuning):
+    def __init__(self, P, d, L_max):
+        self.h = ctypes.c_void_p()
+        self.key = (P, d)
+        _check(load().cs_cache_create(P, d, L_max, ctypes.byref(self.h)))
+
+    def fill(self, stream=None):
+        _check(load().cs_cache_fill(self.h, _stream_handle(stream)))
+        return self
+
+    def info(self, count=False):
+        n, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load().cs_cache_info(self.h, ctypes.byref(n), ctypes.byref(b), ctypes.byref(c) if count else None))
+        return int(n.value), int(b.value), (int(c.value) if count else None)
+
+    def close(self):
+        if self.h:
+            load().cs_cache_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan:
+    """One sieve instance: owns a cs_plan_t and its device memory.  With
+    cache=Cache(P, d, ...) its large primes come from the residue cache."""
+
+    def __init__(self, P, d, M_start, M_inc, SL, L, cache=None, **tuning):
         self.params = (P, d, M_start, M_inc, SL, L)
         self.tuning = make_tuning(**tuning) if tuning else None
-        self.h = cs_plan(P, d, M_start, M_inc, SL, L, self.tuning)
+        if cache is None:
+            self.h = cs_plan(P, d, M_start, M_inc, SL, L, self.tuning)
+        else:
+            self.h = ctypes.c_void_p()
+            _check(load().cs_plan_cached(P, d, M_start, M_inc, SL, L,
+                                         ctypes.byref(self.tuning) if self.tuning else None, cache.h,
+                                         ctypes.byref(self.h)))
+        self.cache = cache
         self.info = cs_info(self.h)
 
     @property

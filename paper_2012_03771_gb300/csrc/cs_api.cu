@@ -114,6 +114,9 @@ struct cs_plan_s {
     // cudaFreeAsync, so building or freeing a plan does not wait for other work
     cudaStream_t alloc_stream = nullptr;
     bool async_alloc = false;
+    // residue cache: large primes come from these cache chunks (indices)
+    cs_cache_t cache = nullptr;
+    std::vector<size_t> cache_idx;
     // profiling
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[KC_N];
     size_t prof_used[KC_N] = {0, 0, 0, 0, 0};
@@ -180,7 +183,7 @@ bool split_primes(uint32_t P, uint64_t d, std::vector<uint32_t> &qK, std::vector
 }
 
 cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc,
-                     uint32_t SL, uint64_t L, const cs_tuning *tune) {
+                     uint32_t SL, uint64_t L, const cs_tuning *tune, cs_cache_t cache) {
     if (d == 0 || P > MAX_P) return fail(CS_EINVAL, "d must be >= 1 and P <= 2^20");
     if (SL > MAX_SL) return fail(CS_EINVAL, "SL must be <= 2^20");
     if (L > MAX_L) return fail(CS_EINVAL, "L must be <= 2^40");
@@ -309,17 +312,38 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
     // about HITS_PER_ITEM expected hits each
     const uint64_t chunk = pl->tune.chunk_numbers ? pl->tune.chunk_numbers : (1ull << 27);
     const double HITS_PER_ITEM = 128.0;
-    uint64_t widest = 0;
-    for (uint64_t lo = T; lo < L;) {
-        uint64_t hi = std::min<uint64_t>({L, lo + std::max<uint64_t>(lo, 1), lo + chunk});
-        pl->chunks.push_back({lo, hi});
+    auto segs_for = [&](uint64_t lo) {
         double hits = (double)M_inc * (double)S / (double)std::max<uint64_t>(lo, 1);
         double seg = std::min<double>(std::max(1.0, std::ceil(hits / HITS_PER_ITEM)), (double)std::max<uint64_t>(M_inc, 1));
-        pl->chunk_seg.push_back((uint32_t)std::min(seg, 65536.0));
-        widest = std::max(widest, hi - lo);
-        lo = hi;
+        return (uint32_t)std::min(seg, 65536.0);
+    };
+    uint64_t widest = 0;
+    if (cache) {
+        // the cache's chunks that overlap (T, L]; the walk skips primes outside
+        ResidueCacheView cv;
+        cache_view(cache, &cv);
+        if (cv.P != P || cv.d != d) return fail(CS_EINVAL, "cache was built for another P or d");
+        if (L > cv.L_max) return fail(CS_EINVAL, "cache does not reach L");
+        pl->cache = cache;
+        for (size_t k = 0; k < cv.n_chunks; k++) {
+            const CacheChunk &ch = cv.chunks[k];
+            if (ch.hi <= T || ch.lo >= L) continue;
+            const uint64_t lo = std::max(ch.lo, T), hi = std::min(ch.hi, L);
+            pl->chunks.push_back({lo, hi});
+            pl->chunk_seg.push_back(segs_for(lo));
+            pl->cache_idx.push_back(k);
+        }
+        pl->large_cap = 0;
+    } else {
+        for (uint64_t lo = T; lo < L;) {
+            uint64_t hi = std::min<uint64_t>({L, lo + std::max<uint64_t>(lo, 1), lo + chunk});
+            pl->chunks.push_back({lo, hi});
+            pl->chunk_seg.push_back(segs_for(lo));
+            widest = std::max(widest, hi - lo);
+            lo = hi;
+        }
+        pl->large_cap = pl->chunks.empty() ? 0 : primes_in_interval_bound(widest);
     }
-    pl->large_cap = pl->chunks.empty() ? 0 : primes_in_interval_bound(widest);
     pl->small_cap = pl->small_hi > P ? prime_count_bound(pl->small_hi) : 0;
     pl->large_grid = pl->tune.large_grid ? (int)pl->tune.large_grid : sm_count() * 8;
 
@@ -379,7 +403,7 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
         // per-unit times measured on search_953: 7.4 ps per (row, small prime)
         // pair, ~7 ps per walk hit, ~150 ps per large prime (generation, K mod p
         // and the walk's solves), ~5 us per kernel launch
-        pl->est_cost = (uint64_t)(small * 7.4 + hits * 7.0 + large * 150.0 +
+        pl->est_cost = (uint64_t)(small * 7.4 + hits * 7.0 + large * (cache ? 60.0 : 150.0) +
                                   5e6 * (3.0 + 2.0 * (double)pl->chunks.size()));
     }
 
@@ -434,7 +458,7 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
 
     if ((s = pl->dalloc(&pl->d_small, pl->small_cap))) return s;
     if ((s = pl->dalloc(&pl->d_counts, 1 + pl->chunks.size()))) return s;
-    if (!pl->chunks.empty()) {
+    if (!pl->chunks.empty() && !pl->cache) {
         size_t el = pl->narrow ? 4 : 8;
         uint8_t *a, *b, *c;
         if ((s = pl->dalloc(&a, pl->large_cap * el))) return s;
@@ -491,7 +515,7 @@ namespace cs {
 
 cs_status plan_create(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL,
                       uint64_t L, const cs_tuning *tune, cudaStream_t alloc_stream, bool async_alloc,
-                      cs_plan_t *out) {
+                      cs_cache_t cache, cs_plan_t *out) {
     if (!out) return fail(CS_EINVAL, "out is NULL");
     *out = nullptr;
     cs_plan_s *pl = new (std::nothrow) cs_plan_s();
@@ -500,7 +524,7 @@ cs_status plan_create(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, 
     pl->async_alloc = async_alloc;
     cs_status s;
     try {
-        s = build_plan(pl, P, d, M_start, M_inc, SL, L, tune);
+        s = build_plan(pl, P, d, M_start, M_inc, SL, L, tune, cache);
     } catch (const std::bad_alloc &) {
         s = fail(CS_ENOMEM, "host allocation failed");
     }
@@ -514,6 +538,7 @@ cs_status plan_create(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, 
 }
 
 void plan_set_sieved(cs_plan_t pl, bool sieved) { pl->sieved = sieved; }
+cs_cache_t plan_cache(cs_plan_t pl) { return pl->cache; }
 bool plan_profiled(cs_plan_t pl) { return pl->tune.profile != 0; }
 cudaEvent_t plan_done_event(cs_plan_t pl) { return pl->done; }
 cs_status set_error(cs_status code, const char *msg) { return fail(code, msg); }
@@ -524,7 +549,13 @@ extern "C" {
 
 cs_status cs_plan(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL,
                   uint64_t L, const cs_tuning *tune, cs_plan_t *out) {
-    return cs::plan_create(P, d, M_start, M_inc, SL, L, tune, nullptr, false, out);
+    return cs::plan_create(P, d, M_start, M_inc, SL, L, tune, nullptr, false, nullptr, out);
+}
+
+cs_status cs_plan_cached(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL,
+                         uint64_t L, const cs_tuning *tune, cs_cache_t cache, cs_plan_t *out) {
+    if (!cache) return fail(CS_EINVAL, "cache is NULL");
+    return cs::plan_create(P, d, M_start, M_inc, SL, L, tune, nullptr, false, cache, out);
 }
 
 cs_status cs_sieve(cs_plan_t pl, void *stream) {
@@ -547,7 +578,23 @@ cs_status cs_sieve(cs_plan_t pl, void *stream) {
     if ((s = prof.begin(KC_TILE))) return s;
     CS_CUDA(launch_tile(dp, pl->tc, pl->d_small, pl->d_counts, pl->small_cap, st));
     if ((s = prof.end())) return s;
-    for (size_t c = 0; c < pl->chunks.size(); c++) {
+    cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
+    CS_CUDA(cudaStreamIsCapturing(st, &capst));
+    if (pl->cache) {
+        ResidueCacheView cv;
+        cache_view(pl->cache, &cv);
+        for (size_t c = 0; c < pl->chunks.size(); c++) {
+            const CacheChunk &ch = cv.chunks[pl->cache_idx[c]];
+            if (!ch.filled && capst != cudaStreamCaptureStatusActive)
+                return fail(CS_ESTATE, "the residue cache has not been filled (cs_cache_fill)");
+            CS_CUDA(cudaStreamWaitEvent(st, ch.ready, 0));
+            if ((s = prof.begin(KC_LARGE))) return s;
+            CS_CUDA(launch_large(dp, ch.narrow, pl->mode, ch.p, ch.r, nullptr, ch.count, ch.cap,
+                                 pl->chunk_seg[c], pl->large_grid, st, pl->T, pl->L));
+            if ((s = prof.end())) return s;
+        }
+    }
+    for (size_t c = 0; c < pl->chunks.size() && !pl->cache; c++) {
         unsigned long long *cnt = pl->d_counts + 1 + c;
         if ((s = prof.begin(KC_GEN_LARGE))) return s;
         CS_CUDA(launch_gen_large(dp, pl->narrow, pl->chunks[c].first, pl->chunks[c].second,
@@ -564,9 +611,7 @@ cs_status cs_sieve(cs_plan_t pl, void *stream) {
     if ((s = prof.end())) return s;
     // inside a stream capture the completion event becomes an event-record node
     // of the graph, so that it is recorded each time the graph runs
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    CS_CUDA(cudaStreamIsCapturing(st, &cap));
-    if (cap == cudaStreamCaptureStatusActive)
+    if (capst == cudaStreamCaptureStatusActive)
         CS_CUDA(cudaEventRecordWithFlags(pl->done, st, cudaEventRecordExternal));
     else
         CS_CUDA(cudaEventRecord(pl->done, st));
@@ -580,6 +625,13 @@ cs_status cs_sync(cs_plan_t pl) {
     if (s) return s;
     unsigned long long err = 0;
     CS_CUDA(cudaMemcpy(&err, pl->dp.stats + ST_ERROR, sizeof(err), cudaMemcpyDeviceToHost));
+    if (pl->cache) {
+        ResidueCacheView cv;
+        cache_view(pl->cache, &cv);
+        unsigned long long cerr = 0;
+        CS_CUDA(cudaMemcpy(&cerr, cv.err, sizeof(cerr), cudaMemcpyDeviceToHost));
+        err |= cerr;
+    }
     if (err & ERR_PRIME_OVERFLOW) return fail(CS_EOVERFLOW, "prime buffer overflow");
     if (err & ERR_SOLVER_LIMIT) return fail(CS_EDEVICE, "modular solver exceeded its pass bound");
     return CS_OK;
@@ -600,7 +652,7 @@ cs_status cs_info(cs_plan_t pl, cs_info_t *out) {
     out->wheel = pl->wheel;
     out->n_large_chunks = pl->chunks.size();
     out->launches_per_sieve = (pl->small_hi > pl->P ? 1 : 0) + (pl->M_c && pl->W ? 1 : 0) +
-                              (pl->M_c ? 1 : 0) + 2 * pl->chunks.size();
+                              (pl->M_c ? 1 : 0) + (pl->cache ? 1 : 2) * pl->chunks.size();
     out->h2d_bytes = pl->h2d;
     out->device_bytes = pl->dev_bytes;
     out->est_cost = pl->est_cost;

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "../../include/combsieve.h"
 
 namespace cs {
@@ -80,6 +82,11 @@ cudaError_t launch_gen_large(const DevPlan &pl, bool narrow, uint64_t lo, uint64
                              const uint32_t *base, uint32_t n_base, void *p_out, void *r_out,
                              void *v_out, uint64_t cap, unsigned long long *count,
                              cudaStream_t stream);
+// Primes p in (lo, hi] with r = K mod p for the K of kp (kch32/kch64 only),
+// for a residue cache; narrow: 32-bit fields (hi < 2^30).
+cudaError_t launch_gen_pr(const DevPlan &kp, bool narrow, uint64_t lo, uint64_t hi, const uint32_t *base,
+                          uint32_t n_base, void *p_out, void *r_out, uint64_t cap,
+                          unsigned long long *count, unsigned long long *err, cudaStream_t stream);
 // Plain prime list (uint64) in (lo, hi], no residues (for tests of the generator).
 cudaError_t launch_gen_list(uint64_t lo, uint64_t hi, const uint32_t *base, uint32_t n_base,
                             uint64_t *out, uint64_t cap, unsigned long long *count,
@@ -105,9 +112,13 @@ enum LargeMode { LARGE_PAPER = 1, LARGE_THREE_GAP = 2 };
 // n_seg: the m-range of every prime is split into n_seg segments walked by
 // separate threads (each starts with its own solve), to balance primes with
 // many hits against primes with few.
+// v may be NULL: then v0 = (r M_start + SL) mod p is computed per prime, and
+// only primes with p_lo < p <= p_hi are walked (a residue-cache chunk holds
+// primes outside the plan's range).
 cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p, const void *r,
                          const void *v, const unsigned long long *count, uint64_t cap,
-                         uint32_t n_seg, int grid, cudaStream_t stream);
+                         uint32_t n_seg, int grid, cudaStream_t stream, uint64_t p_lo = 0,
+                         uint64_t p_hi = ~0ull);
 cudaError_t launch_final(const DevPlan &pl, cudaStream_t stream);
 
 // batch of G solves (tests of the solver)
@@ -117,12 +128,42 @@ cudaError_t launch_modsolve(const uint64_t *p, const uint64_t *K, const uint64_t
 
 int sm_count();
 
+// ---- residue cache (cs_cache.cu) ----
+// Primes and K mod p for one K = P#/d, on a fixed grid of chunks of (0, L_max]:
+// (0, 2^16], then chunks that double in width up to 2^27, then 2^27 wide.
+struct CacheChunk {
+    uint64_t lo, hi;                   // primes lo < p <= hi
+    bool narrow;                       // hi < 2^30: 32-bit p and r
+    void *p = nullptr, *r = nullptr;   // cap entries each
+    unsigned long long *count = nullptr;
+    uint64_t cap = 0;
+    cudaEvent_t ready = nullptr;       // recorded after the chunk's generation
+    bool filled = false;               // a generation has been enqueued since the last capture
+};
+struct ResidueCacheView {
+    uint32_t P;
+    uint64_t d, L_max;
+    CacheChunk *chunks;
+    size_t n_chunks;
+    unsigned long long *err;           // device error flags of the cache's generation
+};
+bool cache_view(cs_cache_t cache, ResidueCacheView *out);
+// Enqueues the generation of every chunk with lo < L (all if L = 0) on stream
+// (only the chunks never filled, if only_missing); inside a stream capture the
+// chunks are marked not filled for later plain use.
+cs_status cache_fill_upto(cs_cache_t cache, uint64_t L, cudaStream_t stream, bool only_missing);
+std::mutex &cache_mutex(cs_cache_t cache);
+// Extends the grid (and allocates) so that it covers L.
+cs_status cache_extend(cs_cache_t cache, uint64_t L);
+cs_status cache_new(uint32_t P, uint64_t d, uint64_t L_max, cs_cache_t *out);
+
 // ---- plan internals used by the batch and server runtime (cs_runtime.cu) ----
 // Builds a plan; with async_alloc its device memory is stream-ordered on
 // alloc_stream (cudaMallocAsync / cudaFreeAsync).
 cs_status plan_create(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL,
                       uint64_t L, const cs_tuning *tune, cudaStream_t alloc_stream, bool async_alloc,
-                      cs_plan_t *out);
+                      cs_cache_t cache, cs_plan_t *out);
+cs_cache_t plan_cache(cs_plan_t pl);
 void plan_set_sieved(cs_plan_t pl, bool sieved);
 bool plan_profiled(cs_plan_t pl);
 cudaEvent_t plan_done_event(cs_plan_t pl);

@@ -33,7 +33,16 @@ struct LargeArgs {
     const unsigned long long *count;
     uint64_t cap;
     uint32_t n_seg;      // m-segments per prime (work items = primes x n_seg)
+    uint64_t p_lo, p_hi; // walk only p_lo < p <= p_hi (v == NULL: shared cache chunk)
 };
+
+// v0 = (r * M_start + SL) mod p, for primes from a shared residue cache
+__device__ __forceinline__ uint32_t start_v(uint32_t r, uint64_t M_start, uint32_t SL, uint32_t p) {
+    return (uint32_t)(((uint64_t)r * (M_start % p) + SL) % p);
+}
+__device__ __forceinline__ uint64_t start_v(uint64_t r, uint64_t M_start, uint32_t SL, uint64_t p) {
+    return (uint64_t)(((unsigned __int128)r * (M_start % p) + SL) % p);
+}
 
 // (r * m + v) mod p for m < 2^31
 __device__ __forceinline__ uint32_t advance(uint32_t v, uint32_t r, uint64_t m, uint32_t p) {
@@ -101,7 +110,8 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_large(const LargeArgs a) {
         if (m_lo >= m_hi) continue;
         const uint64_t Mseg = m_hi - m_lo;      // walk m_lo + [0, Mseg)
         const UT p = Pp[i], r = Rp[i];
-        UT v = Vp[i];
+        if ((uint64_t)p <= a.p_lo || (uint64_t)p > a.p_hi) continue;
+        UT v = Vp ? Vp[i] : start_v(r, pl.M_start, pl.SL, p);
         if (m_lo) v = advance(v, r, m_lo, p);
         uint32_t it = 0;
         if (MODE == LARGE_PAPER) {
@@ -256,12 +266,12 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_large_tg(const LargeArgs a) {
                 const uint32_t sg = (uint32_t)(item - i * n_seg);
                 const uint64_t m_lo = M * sg / n_seg, m_hi = M * (sg + 1) / n_seg;
                 const UT pp = Pp[i], r = Rp[i];
-                UT vv = Vp[i];
-                if (m_lo) vv = advance(vv, r, m_lo, pp);
+                bool ok = m_lo < m_hi && (uint64_t)pp > a.p_lo && (uint64_t)pp <= a.p_hi;
+                UT vv = ok ? (Vp ? Vp[i] : start_v(r, pl.M_start, pl.SL, pp)) : (UT)0;
+                if (ok && m_lo) vv = advance(vv, r, m_lo, pp);
                 uint32_t it = 0;
                 UT ma_, da_, mb_ = 0, ub_ = 0;
                 uint64_t first = 0;
-                bool ok = m_lo < m_hi;
                 if (ok && w == 0) {
                     ma_ = pp;
                     da_ = 0;
@@ -377,8 +387,8 @@ __global__ void k_modsolve(const uint64_t *p, const uint64_t *K, const uint64_t 
 
 cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p, const void *r,
                          const void *v, const unsigned long long *count, uint64_t cap, uint32_t n_seg,
-                         int grid, cudaStream_t stream) {
-    LargeArgs a{pl, p, r, v, count, cap, n_seg ? n_seg : 1};
+                         int grid, cudaStream_t stream, uint64_t p_lo, uint64_t p_hi) {
+    LargeArgs a{pl, p, r, v, count, cap, n_seg ? n_seg : 1, p_lo, p_hi};
     if (grid <= 0) grid = sm_count() * 8;
     if (narrow) {
         if (mode == LARGE_PAPER)

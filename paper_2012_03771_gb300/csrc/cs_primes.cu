@@ -27,7 +27,9 @@ constexpr uint32_t WARP_COOP_Q = 4096;      // q below this: marked by a whole w
 constexpr uint32_t BATCH = 16;              // words scanned per warp step (lanes 0..15)
 constexpr uint32_t QCAP = BATCH * 32 + 32;  // per-warp queue (odd indices within the segment)
 
-enum Kind { KIND_SMALL = 0, KIND_LARGE32 = 1, KIND_LARGE64 = 2, KIND_LIST = 3 };
+// SMALL: tile records; LARGE32/64: (p, r, v0) of one plan; LIST: p only;
+// PR32/64: (p, r) for a residue cache shared by plans with the same K
+enum Kind { KIND_SMALL = 0, KIND_LARGE32 = 1, KIND_LARGE64 = 2, KIND_LIST = 3, KIND_PR32 = 4, KIND_PR64 = 5 };
 
 struct GenArgs {
     uint64_t i_begin, i_end;      // odd indices [i_begin, i_end): numbers 2i+1
@@ -102,6 +104,15 @@ __device__ __forceinline__ void emit(const GenArgs &a, uint64_t p, bool valid, u
             uint64_t rt = mont64_mul(r, r2, p, pinv);
             uint64_t v = mont64_mul(rt, a.M_start % p, p, pinv) + a.SL;
             w0 = p; w1 = r; w2 = v >= p ? v - p : v;
+        } else if (KIND == KIND_PR32) {
+            uint32_t p32 = (uint32_t)p;
+            uint32_t pinv = mont32_neg_inv(p32);
+            e0 = p32;
+            e1 = kmodp32(p32, pinv, mont32_r1(p32), mont32_r2(p32), a.kch32, a.n_kch32);
+        } else if (KIND == KIND_PR64) {
+            uint64_t pinv = mont64_neg_inv(p);
+            w0 = p;
+            w1 = kmodp64(p, pinv, mont64_r1(p), mont64_r2(p), a.kch64, a.n_kch64);
         } else {
             w0 = p;
         }
@@ -129,6 +140,12 @@ __device__ __forceinline__ void emit(const GenArgs &a, uint64_t p, bool valid, u
         reinterpret_cast<uint64_t *>(a.o0)[slot] = w0;
         reinterpret_cast<uint64_t *>(a.o1)[slot] = w1;
         reinterpret_cast<uint64_t *>(a.o2)[slot] = w2;
+    } else if (KIND == KIND_PR32) {
+        reinterpret_cast<uint32_t *>(a.o0)[slot] = e0;
+        reinterpret_cast<uint32_t *>(a.o1)[slot] = e1;
+    } else if (KIND == KIND_PR64) {
+        reinterpret_cast<uint64_t *>(a.o0)[slot] = w0;
+        reinterpret_cast<uint64_t *>(a.o1)[slot] = w1;
     } else {
         reinterpret_cast<uint64_t *>(a.o0)[slot] = w0;
     }
@@ -312,6 +329,22 @@ cudaError_t launch_gen_large(const DevPlan &pl, bool narrow, uint64_t lo, uint64
         k_gen<KIND_LARGE32><<<gen_grid(a.n_seg), GEN_THREADS, 0, stream>>>(a);
     else
         k_gen<KIND_LARGE64><<<gen_grid(a.n_seg), GEN_THREADS, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gen_pr(const DevPlan &kp, bool narrow, uint64_t lo, uint64_t hi, const uint32_t *base,
+                          uint32_t n_base, void *p_out, void *r_out, uint64_t cap,
+                          unsigned long long *count, unsigned long long *err, cudaStream_t stream) {
+    GenArgs a = make_args(lo, hi, base, n_base);
+    if (a.n_seg == 0 && !a.emit_two) return cudaSuccess;
+    a.kch32 = kp.kch32; a.n_kch32 = kp.n_kch32;
+    a.kch64 = kp.kch64; a.n_kch64 = kp.n_kch64;
+    a.o0 = p_out; a.o1 = r_out;
+    a.cap = cap; a.count = count; a.err = err;
+    if (narrow)
+        k_gen<KIND_PR32><<<gen_grid(a.n_seg), GEN_THREADS, 0, stream>>>(a);
+    else
+        k_gen<KIND_PR64><<<gen_grid(a.n_seg), GEN_THREADS, 0, stream>>>(a);
     return cudaGetLastError();
 }
 

@@ -77,10 +77,16 @@ struct cs_server_s {
     cs_tuning tune{};
     bool has_tune = false;
     std::mutex mu;
+    // residue caches shared by all requests with the same (P, d), resident for
+    // the server's lifetime (outside the request budget)
+    std::vector<std::pair<std::pair<uint32_t, uint64_t>, cs_cache_t>> caches;
+    cudaStream_t cache_stream = nullptr;
 
     ~cs_server_s() {
         for (auto &kv : tickets) cs_destroy(kv.second.plan);
+        for (auto &c : caches) cs_cache_destroy(c.second);
         for (auto s : slots) cudaStreamDestroy(s);
+        if (cache_stream) cudaStreamDestroy(cache_stream);
     }
 };
 
@@ -121,6 +127,17 @@ cs_status cs_batch_create(const cs_plan_t *plans, int n, int n_streams, cs_batch
         load[k] += o.first;
     }
 
+    // residue caches used by the plans, with the largest L each must reach
+    std::vector<std::pair<cs_cache_t, uint64_t>> caches;
+    for (int i = 0; i < n; i++) {
+        cs_cache_t c = plan_cache(plans[i]);
+        if (!c) continue;
+        cs_info_t info;
+        cs_info(plans[i], &info);
+        auto it = std::find_if(caches.begin(), caches.end(), [&](auto &x) { return x.first == c; });
+        if (it == caches.end()) caches.push_back({c, 0});
+    }
+
     cs_batch_s *b = new (std::nothrow) cs_batch_s();
     if (!b) return set_error(CS_ENOMEM, "host allocation failed");
     b->plans.assign(plans, plans + n);
@@ -133,7 +150,7 @@ cs_status cs_batch_create(const cs_plan_t *plans, int n, int n_streams, cs_batch
     BT(cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking));
     BT(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
     BT(cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming));
-    for (int k = 0; k < n_streams; k++) {
+    for (int k = 0; k < n_streams + (int)caches.size(); k++) {
         cudaStream_t st;
         BT(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
         b->streams.push_back(st);
@@ -144,6 +161,18 @@ cs_status cs_batch_create(const cs_plan_t *plans, int n, int n_streams, cs_batch
     BT(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
     cs_status cap = CS_OK;
     cudaError_t e = cudaEventRecord(b->fork, b->origin);
+    // each cache is regenerated once per run on its own stream; the plans'
+    // walks wait for the chunks they read (events inside the graph)
+    for (size_t k = 0; k < caches.size() && e == cudaSuccess && !cap; k++) {
+        cudaStream_t cst = b->streams[n_streams + k];
+        e = cudaStreamWaitEvent(cst, b->fork, 0);
+        if (e == cudaSuccess) {
+            std::lock_guard<std::mutex> lk(cache_mutex(caches[k].first));
+            cap = cache_fill_upto(caches[k].first, 0, cst, false);
+        }
+        if (e == cudaSuccess && !cap) e = cudaEventRecord(b->join[n_streams + k], cst);
+        if (e == cudaSuccess && !cap) e = cudaStreamWaitEvent(b->origin, b->join[n_streams + k], 0);
+    }
     for (int k = 0; k < n_streams && e == cudaSuccess && !cap; k++) {
         e = cudaStreamWaitEvent(b->streams[k], b->fork, 0);
         for (int i : lane[k]) {
@@ -222,6 +251,8 @@ cs_status cs_server_start(uint64_t budget_bytes, int max_slots, const cs_tuning 
     }
     int least = 0, greatest = 0;
     cs_status s0 = cuda_err(cudaDeviceGetStreamPriorityRange(&least, &greatest), "cudaDeviceGetStreamPriorityRange");
+    if (!s0) s0 = cuda_err(cudaStreamCreateWithPriority(&sv->cache_stream, cudaStreamNonBlocking, greatest),
+                           "cudaStreamCreateWithPriority");
     if (s0) { delete sv; return s0; }
     sv->n_levels = std::min(4, least - greatest + 1);   // greatest is numerically lowest
     if (sv->n_levels < 1) sv->n_levels = 1;
@@ -248,11 +279,29 @@ cs_status cs_submit(cs_server_t sv, uint32_t P, uint64_t d, uint64_t M_start, ui
     for (size_t i = 0; i < sv->slot_ticket.size(); i++)
         if (!sv->slot_ticket[i]) { slot = (int)i; break; }
     if (slot < 0) return set_error(CS_EAGAIN, "no free slot");
+    // the (P, d) residue cache: created or extended to L, missing chunks
+    // generated on the cache stream (the plan's walks wait on their events)
+    cs_cache_t cache = nullptr;
+    for (auto &c : sv->caches)
+        if (c.first.first == P && c.first.second == d) cache = c.second;
+    cs_status s = CS_OK;
+    if (!cache) {
+        s = cache_new(P, d, L, &cache);
+        if (s) return s;
+        sv->caches.push_back({{P, d}, cache});
+    }
+    {
+        std::lock_guard<std::mutex> lk(cache_mutex(cache));
+        s = cache_extend(cache, L);
+        if (!s) s = cache_fill_upto(cache, L, sv->cache_stream, true);
+    }
+    if (s) return s;
     // build on the slot's lowest-priority stream, sieve on the stream of the
     // request's priority level (both belong to the slot, which is idle)
     cudaStream_t st_alloc = sv->slots[slot * sv->n_levels + sv->n_levels - 1];
     cs_plan_t plan = nullptr;
-    cs_status s = plan_create(P, d, M_start, M_inc, SL, L, sv->has_tune ? &sv->tune : nullptr, st_alloc, true, &plan);
+    s = plan_create(P, d, M_start, M_inc, SL, L, sv->has_tune ? &sv->tune : nullptr, st_alloc, true,
+                    cache, &plan);
     if (s) return s;
     cs_info_t info;
     cs_info(plan, &info);

@@ -157,3 +157,77 @@ def test_server_admission_by_memory_and_slots():
         assert one.submit(*prm.as_tuple()) is not None
     one.close()
     srv.close()
+
+
+# ------------------------------------------------------------- residue cache
+
+def test_cached_plans_equal_plain_plans():
+    """Large primes from the shared (p, K mod p) cache give the same bits."""
+    cases = [workloads.PLAIN_503,
+             workloads.SieveParams(P=503, d=2310, M_start=10**6, M_inc=3000, SL=3000, L=3 * 10**9),
+             workloads.SieveParams(P=503, d=210, M_start=7, M_inc=400, SL=2000, L=2 * 10**6)]
+    for prm in cases:
+        ref = _alone(prm)
+        cache = cs.Cache(prm.P, prm.d, 4 * 10**9)
+        cache.fill(torch.cuda.current_stream())
+        for mode in (1, 2):
+            with cs.Plan(*prm.as_tuple(), cache=cache, large_mode=mode) as p:
+                p.sieve(torch.cuda.current_stream()).sync()
+                counts, F, h = p.counts()
+                assert (F, h) == ref[1:], (prm, mode)
+                assert np.array_equal(counts, ref[0])
+        n_chunks, nbytes, n_primes = cache.info(count=True)
+        cache.close()
+
+
+def test_cache_holds_every_prime():
+    cache = cs.Cache(953, 210, 2 * 10**8)
+    cache.fill()
+    _, _, n = cache.info(count=True)
+    count, _, _ = O.prime_stats(0, _cache_limit(2 * 10**8))
+    assert n == count
+    cache.close()
+
+
+def _cache_limit(L):
+    """Upper end of the cache grid that covers L: (0, 2^16], then doubling
+    chunks up to 2^27 wide, then 2^27 wide."""
+    hi = 1 << 16
+    while hi < L:
+        hi += min(hi, 1 << 27)
+    return hi
+
+
+def test_cached_plan_needs_a_filled_cache():
+    prm = _small_mix(1, seed=10)[0]
+    cache = cs.Cache(prm.P, prm.d, prm.L)
+    with cs.Plan(*prm.as_tuple(), cache=cache) as p:
+        with pytest.raises(cs.CSError) as e:
+            p.sieve()
+        assert e.value.code == cs.CS_ESTATE
+    with pytest.raises(cs.CSError):
+        cs.Plan(prm.P, prm.d, prm.M_start, prm.M_inc, prm.SL, _cache_limit(prm.L) + 1, cache=cache)
+    cache.close()
+
+
+def test_batch_of_cached_plans_equals_alone():
+    mix = _small_mix(10, seed=11)
+    ref = [_alone(prm) for prm in mix]
+    caches = {}
+    for prm in mix:
+        key = (prm.P, prm.d)
+        caches[key] = max(caches.get(key, 0), prm.L)
+    caches = {k: cs.Cache(k[0], k[1], L) for k, L in caches.items()}
+    plans = [cs.Plan(*prm.as_tuple(), cache=caches[(prm.P, prm.d)]) for prm in mix]
+    batch = cs.Batch(plans, n_streams=3)
+    for _ in range(2):
+        batch.run().sync()
+        for p, (counts, F, h) in zip(plans, ref):
+            c2, F2, h2 = p.counts()
+            assert (F2, h2) == (F, h)
+            assert np.array_equal(c2, counts)
+    batch.close()
+    for p in plans:
+        p.close()
+    for c in caches.values():
+        c.close()

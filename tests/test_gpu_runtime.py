@@ -131,8 +131,13 @@ def test_server_results_equal_alone():
 
 def test_server_admission_by_memory_and_slots():
     prm = _small_mix(1, seed=9)[0]
-    with cs.Plan(*prm.as_tuple()) as p:
-        need = int(p.info.device_bytes)
+    probe = cs.Server(budget_bytes=1 << 40, max_slots=1)     # device bytes of one request
+    t0 = probe.submit(*prm.as_tuple())
+    need = probe.usage()[0]
+    while not probe.poll(t0):
+        time.sleep(0.001)
+    probe.close()
+    assert need > 0
     srv = cs.Server(budget_bytes=need + need // 2, max_slots=4)
     t1 = srv.submit(*prm.as_tuple())
     assert t1 is not None

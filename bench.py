@@ -405,12 +405,12 @@ def run_batched(args):
         lim[(prm.P, prm.d)] = max(lim.get((prm.P, prm.d), 0), prm.L)
     caches = {k: cs.Cache(k[0], k[1], L) for k, L in lim.items()}
     cplans = [cs.Plan(*prm.as_tuple(), cache=caches[(prm.P, prm.d)]) for prm in mix]
-    batch = cs.Batch(cplans)
+    batch = cs.Batch(cplans, n_streams=args.batch_streams)
     batch_ms = time_steps(lambda: batch.run(s))
     batch.sync()
     same = all(cs.cs_counts(p.h) == r for p, r in zip(cplans, ref))
     # the graph over worker streams alone, without the shared cache
-    batch_nc = cs.Batch(plans)
+    batch_nc = cs.Batch(plans, n_streams=args.batch_streams)
     nocache_ms = time_steps(lambda: batch_nc.run(s))
     batch_nc.sync()
     same = same and all(cs.cs_counts(p.h) == r for p, r in zip(plans, ref))
@@ -518,6 +518,7 @@ def main():
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--load", type=float, default=0.8)
     ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--batch-streams", type=int, default=0)
     ap.add_argument("--budget-frac", type=float, default=0.5)
     ap.add_argument("--mode", type=int, default=0)
     ap.add_argument("--threshold", type=int, default=0)

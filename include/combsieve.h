@@ -189,7 +189,9 @@ cs_status cs_plan_cached(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_in
 /* ---- batched execution ---------------------------------------------------
  * Many independent searches of uneven size (Section 5, "Real world searching")
  * share the GPU.  cs_batch_create spreads the plans over n_streams worker
- * streams (0 = min(n, 16)), longest estimated cost first onto the least loaded
+ * streams (0 = 1 when the plans use residue caches, else min(n, 2): each
+ * instance fills the GPU, so more concurrent instances mostly cost L2
+ * locality), longest estimated cost first onto the least loaded
  * stream, and captures their whole launch sequence once into a CUDA graph;
  * cs_batch_run replays it with one graph launch on `stream`.  The plans stay
  * owned by the caller and must outlive the batch; their results are read with

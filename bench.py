@@ -482,7 +482,12 @@ def run_served(args):
             if srv.poll(t):
                 i = pending.pop(t)
                 lat[i] = time.perf_counter() - t0 - arrivals[i]
-                results[i] = cs.cs_counts(srv.plan(t).h)
+                bp = srv.plan(t)
+                try:
+                    cs.cs_sync(bp.h)
+                    results[i] = cs.cs_counts(bp.h)
+                except cs.CSError as e:
+                    results[i] = ("error", str(e))
                 srv.release(t)
         time.sleep(0.0002)
     makespan = time.perf_counter() - t0
@@ -495,6 +500,10 @@ def run_served(args):
         fifo_lat.append(end - arrivals[i])
     F_total = sum(f for f, _ in ref)
     pct = lambda v, q: sorted(v)[min(len(v) - 1, int(q * len(v)))]
+    bad = [i for i in range(n_req) if results[i] != ref[i]]
+    for i in bad[:8]:
+        print(json.dumps({"mismatch": i, "params": reqs[i].as_tuple(), "got": str(results[i]),
+                          "alone": list(ref[i])}), file=sys.stderr, flush=True)
     line = {"metric": "served sieve requests: latency and enumerated factors/s (bit-exact)", "unit": UNIT,
             "value": F_total / makespan, "requests": n_req, "arrival_rate_per_s": rate,
             "p50_ms": 1e3 * pct(lat, 0.5), "p99_ms": 1e3 * pct(lat, 0.99),

@@ -114,6 +114,12 @@ struct cs_plan_s {
     // cudaFreeAsync, so building or freeing a plan does not wait for other work
     cudaStream_t alloc_stream = nullptr;
     bool async_alloc = false;
+    cudaStream_t own_upload = nullptr;    // private upload stream of a plain plan
+    cudaStream_t upload_stream() {
+        if (async_alloc) return alloc_stream;
+        if (!own_upload) cudaStreamCreateWithFlags(&own_upload, cudaStreamNonBlocking);
+        return own_upload;
+    }
     // residue cache: large primes come from these cache chunks (indices)
     cs_cache_t cache = nullptr;
     std::vector<size_t> cache_idx;
@@ -122,6 +128,7 @@ struct cs_plan_s {
     size_t prof_used[KC_N] = {0, 0, 0, 0, 0};
 
     ~cs_plan_s() {
+        if (own_upload) cudaStreamDestroy(own_upload);
         if (done) cudaEventDestroy(done);
         for (int k = 0; k < KC_N; k++)
             for (auto &e : prof_ev[k]) {
@@ -151,11 +158,12 @@ struct cs_plan_s {
         cs_status s = dalloc(p, v.size());
         if (s) return s;
         if (!v.empty()) {
-            // async mode: the plan builder synchronises alloc_stream before the
-            // host vectors go out of scope
-            cudaError_t e = async_alloc
-                                ? cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, alloc_stream)
-                                : cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+            // every upload goes on one stream that the plan builder synchronises
+            // before the host vectors go out of scope and before any kernel can
+            // read the tables (a plain cudaMemcpy from pageable memory may return
+            // before its DMA lands and is ordered only on the legacy stream)
+            cudaError_t e = cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice,
+                                            upload_stream());
             if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy H2D");
             h2d += v.size() * sizeof(T);
         }
@@ -467,7 +475,11 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
         pl->d_lp = a; pl->d_lr = b; pl->d_lv = c;
     }
     CS_CUDA(cudaEventCreateWithFlags(&pl->done, cudaEventDisableTiming));
-    if (pl->async_alloc) CS_CUDA(cudaStreamSynchronize(pl->alloc_stream));
+    CS_CUDA(cudaStreamSynchronize(pl->upload_stream()));
+    if (pl->own_upload) {
+        cudaStreamDestroy(pl->own_upload);
+        pl->own_upload = nullptr;
+    }
     return CS_OK;
 }
 

@@ -47,6 +47,19 @@ struct cs_cache_s {
 
 namespace {
 
+// Host-to-device copy that has landed when it returns: on a private stream,
+// synchronised (a plain cudaMemcpy from pageable memory may return before its
+// DMA completes and is ordered only on the legacy default stream).
+cudaError_t upload_now(void *dst, const void *src, size_t bytes) {
+    cudaStream_t st;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    e = src ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) : cudaMemsetAsync(dst, 0, bytes, st);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    return e != cudaSuccess ? e : e2;
+}
+
 constexpr uint64_t GRID0 = 1ull << 16;
 constexpr uint64_t GRID_MAX_WIDTH = 1ull << 27;
 constexpr uint64_t NARROW = 1ull << 30;
@@ -140,7 +153,7 @@ cs_status cache_extend(cs_cache_t c, uint64_t L) {
         void *b;
         cs_status s;
         if ((s = c->alloc(&b, base.size() * 4))) return s;
-        if (!base.empty() && (s = cuda_err(cudaMemcpy(b, base.data(), base.size() * 4, cudaMemcpyHostToDevice), "cudaMemcpy")))
+        if (!base.empty() && (s = cuda_err(upload_now(b, base.data(), base.size() * 4), "upload")))
             return s;
         c->base = static_cast<uint32_t *>(b);
         c->n_base = (uint32_t)base.size();
@@ -189,9 +202,9 @@ cs_status cache_new(uint32_t P, uint64_t d, uint64_t L_max, cs_cache_t *out) {
     if (!s) s = c->alloc(&k32, kch32.size() * 4);
     if (!s) s = c->alloc(&k64, kch64.size() * 8);
     if (!s) s = c->alloc(&err, 8);
-    if (!s && !kch32.empty()) s = cuda_err(cudaMemcpy(k32, kch32.data(), kch32.size() * 4, cudaMemcpyHostToDevice), "cudaMemcpy");
-    if (!s && !kch64.empty()) s = cuda_err(cudaMemcpy(k64, kch64.data(), kch64.size() * 8, cudaMemcpyHostToDevice), "cudaMemcpy");
-    if (!s) s = cuda_err(cudaMemset(err, 0, 8), "cudaMemset");
+    if (!s && !kch32.empty()) s = cuda_err(upload_now(k32, kch32.data(), kch32.size() * 4), "upload");
+    if (!s && !kch64.empty()) s = cuda_err(upload_now(k64, kch64.data(), kch64.size() * 8), "upload");
+    if (!s) s = cuda_err(upload_now(err, nullptr, 8), "memset");
     if (s) { delete c; return s; }
     c->kp.kch32 = static_cast<uint32_t *>(k32);
     c->kp.n_kch32 = (uint32_t)kch32.size();

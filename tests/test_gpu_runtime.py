@@ -117,6 +117,7 @@ def test_server_results_equal_alone():
         for t in list(pending):
             if srv.poll(t):
                 plan = srv.plan(t)
+                plan.sync()                                  # device status of the request
                 counts, F, h = plan.counts()
                 results[pending.pop(t)] = (counts.copy(), F, h)
                 srv.release(t)

@@ -225,6 +225,7 @@ struct TGItem {
 };
 
 constexpr int TG_QCAP = 64;
+constexpr int TG_STEPS = 4;
 constexpr int TG_WARPS = LARGE_THREADS / 32;
 
 template <class UT, class ST, class MT>
@@ -341,8 +342,9 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_large_tg(const LargeArgs a) {
             if (qcount == 0 && batch * 32 >= n_items) break;
             continue;
         }
-        // one three-distance step per active lane, as selects
-        if (active) {
+        // up to TG_STEPS three-distance steps per active lane between queue
+        // checks (each step as selects)
+        for (int u = 0; u < TG_STEPS && active; u++) {
             record_hit<UT>(pl, (uint64_t)moff, v, p, c);
             const bool down = v >= da;
             const bool up = v + ub <= w;

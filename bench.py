@@ -33,6 +33,8 @@ def metric_of(params) -> str:
 METRIC = "enumerated factors/s at L=1e9 (bit-exact bitset + per-m counts)"
 UNIT = "factors/s"
 KC_NAMES = ["gen_small", "tile_sieve", "gen_large", "large_walk", "final"]
+# autotuner results for this GPU, one line per (P, d, SL, ceil(log2 L))
+TUNE_FILE = os.path.join(ROOT, "paper_2012_03771_gb300", "tune_gb300.txt")
 
 
 def _peaks():
@@ -170,6 +172,12 @@ def run_cuda(args, params):
     stream = torch.cuda.Stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     tuning = dict(profile=True)
+    tuned = None
+    if not args.threshold and not args.mode and not args.no_autotune:
+        # the autotuner's choice for this parameter set, from the committed
+        # tuning file (timed on the device and appended there if missing)
+        tuned = cs.cs_autotune(*params.as_tuple(), cache_path=TUNE_FILE)
+        tuning.update(tuned)
     if args.mode:
         tuning["large_mode"] = args.mode
     if args.threshold:
@@ -271,7 +279,7 @@ def run_cuda(args, params):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32" if info.narrow else "u64",
             "data": "synthetic (parameters of the paper-shaped search; primes generated on device)",
-            "config": _config(params, info, args.config),
+            "config": dict(_config(params, info, args.config), autotuned=tuned is not None),
             "intervals_per_s": intervals_s,
             "F_per_step": int(F_ref), "hash": f"{h_ref:#018x}",
             "stats": stats,
@@ -535,6 +543,7 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=512)
     ap.add_argument("--ref-rows", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     rank, ws = _dist()
     if args.config == "batched_64":

@@ -167,6 +167,18 @@ cs_status cs_destroy(cs_plan_t plan);
 /* Message for the last error on the calling thread ("" if none). */
 const char *cs_last_error(void);
 
+/* ---- autotuning -------------------------------------------------------------
+ * Picks the threshold T (as a multiple of S) and the tile height for a
+ * parameter set by timing candidates on the device, on a proxy instance with
+ * the same P, d and SL, M_inc clipped to 1e5 and L to 1e9.  The choice is kept
+ * per (P, d, SL, ceil(log2 L)) in memory and, if cache_path is not NULL,
+ * appended to that text file and read back by later calls (one line per key).
+ * *out receives a complete tuning (large_mode = 2).  Validation errors as for
+ * cs_plan.  Tuning fields left at 0 in any plan may also be set from the
+ * environment: CS_THRESHOLD, CS_TILE_ROWS, CS_LARGE_MODE, CS_LARGE_GRID. */
+cs_status cs_autotune(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL, uint64_t L,
+                      const char *cache_path, cs_tuning *out);
+
 /* ---- residue cache ---------------------------------------------------------
  * Device-resident primes p <= L_max with r = K mod p for one K = P#/d
  * (Section 3.1's cached residue, kept for many searches with the same K).

@@ -36,7 +36,7 @@ EXPORTS = ("cs_plan", "cs_sieve", "cs_sync", "cs_info", "cs_fetch_bitset", "cs_c
            "cs_batch_create", "cs_batch_run", "cs_batch_sync", "cs_batch_info", "cs_batch_destroy",
            "cs_server_start", "cs_submit", "cs_poll", "cs_server_plan", "cs_release", "cs_server_usage",
            "cs_server_stop", "cs_fetch_rows", "cs_cache_create", "cs_cache_fill", "cs_cache_info",
-           "cs_cache_destroy", "cs_plan_cached")
+           "cs_cache_destroy", "cs_plan_cached", "cs_autotune")
 
 
 class CSError(RuntimeError):
@@ -117,6 +117,7 @@ def load(path: Optional[str] = None):
         lib.cs_server_usage.argtypes = [vp, P64, P64, P64]
         lib.cs_server_stop.argtypes = [vp]
         lib.cs_cache_create.argtypes = [u32, u64, u64, ctypes.POINTER(vp)]
+        lib.cs_autotune.argtypes = [u32, u64, u64, u64, u32, u64, ctypes.c_char_p, ctypes.POINTER(cs_tuning)]
         lib.cs_cache_fill.argtypes = [vp, vp]
         lib.cs_cache_info.argtypes = [vp, P64, P64, P64]
         lib.cs_cache_destroy.argtypes = [vp]
@@ -265,6 +266,14 @@ def cs_k_mod_p(P, d, p_ptr: int, n: int, r_ptr: int, stream=None):
 def cs_modsolve(p_ptr, K_ptr, L_ptr, R_ptr, m_ptr, n, narrow, stream=None):
     _check(load().cs_modsolve(*(ctypes.c_void_p(x) for x in (p_ptr, K_ptr, L_ptr, R_ptr, m_ptr)),
                               n, int(narrow), _stream_handle(stream)))
+
+
+def cs_autotune(P, d, M_start, M_inc, SL, L, cache_path: Optional[str] = None) -> dict:
+    """Tuning chosen by the library's autotuner (see combsieve.h)."""
+    t = cs_tuning()
+    _check(load().cs_autotune(P, d, M_start, M_inc, SL, L, cache_path.encode() if cache_path else None,
+                              ctypes.byref(t)))
+    return {"threshold": int(t.threshold), "tile_rows": int(t.tile_rows), "large_mode": int(t.large_mode)}
 
 
 # ---------------------------------------------------------------- wrapper

@@ -2,6 +2,7 @@
 // factor words, device memory and the order of kernel launches for one sieve.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -190,19 +191,46 @@ bool split_primes(uint32_t P, uint64_t d, std::vector<uint32_t> &qK, std::vector
     return rest == 1;
 }
 
-cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc,
-                     uint32_t SL, uint64_t L, const cs_tuning *tune, cs_cache_t cache) {
+cs_status check_params(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL, uint64_t L,
+                       std::vector<uint32_t> &qK, std::vector<uint32_t> &qd) {
     if (d == 0 || P > MAX_P) return fail(CS_EINVAL, "d must be >= 1 and P <= 2^20");
     if (SL > MAX_SL) return fail(CS_EINVAL, "SL must be <= 2^20");
     if (L > MAX_L) return fail(CS_EINVAL, "L must be <= 2^40");
     if (M_start < 1 || M_start > MAX_M || M_inc > MAX_M - M_start)
         return fail(CS_EINVAL, "need 1 <= M_start and M_start + M_inc <= 2^40");
     if (M_inc >= (1ull << 31)) return fail(CS_EINVAL, "M_inc must be < 2^31");
-    std::vector<uint32_t> qK, qd;
     if (!split_primes(P, d, qK, qd)) return fail(CS_EINVAL, "d must be squarefree and divide P#");
+    // every N + x >= 2: M_start*K - SL >= 2 (only K < 2^64 can fail it)
+    unsigned __int128 K = 1;
+    for (uint32_t q : qK) {
+        K *= q;
+        if (K > (unsigned __int128)UINT64_MAX) return CS_OK;
+    }
+    if ((unsigned __int128)M_start * K < (unsigned __int128)SL + 2) return fail(CS_EINVAL, "need M_start*K - SL >= 2");
+    return CS_OK;
+}
+
+// tuning fields left at 0 may be set from the environment
+void env_tuning(cs_tuning &t) {
+    auto get = [](const char *n) -> uint64_t {
+        const char *v = getenv(n);
+        return v ? strtoull(v, nullptr, 10) : 0;
+    };
+    if (!t.threshold) t.threshold = get("CS_THRESHOLD");
+    if (!t.tile_rows) t.tile_rows = (uint32_t)get("CS_TILE_ROWS");
+    if (!t.large_mode) t.large_mode = (uint32_t)get("CS_LARGE_MODE");
+    if (!t.large_grid) t.large_grid = (uint32_t)get("CS_LARGE_GRID");
+}
+
+cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc,
+                     uint32_t SL, uint64_t L, const cs_tuning *tune, cs_cache_t cache) {
+    std::vector<uint32_t> qK, qd;
+    cs_status sv = check_params(P, d, M_start, M_inc, SL, L, qK, qd);
+    if (sv) return sv;
 
     pl->P = P; pl->d = d; pl->M_start = M_start; pl->M_inc = M_inc; pl->SL = SL; pl->L = L;
     if (tune) pl->tune = *tune;
+    env_tuning(pl->tune);
     pl->wheel = !pl->tune.no_wheel;
 
     // K as 32- and 64-bit factor words; K itself when it fits in 64 bits
@@ -554,6 +582,10 @@ cs_cache_t plan_cache(cs_plan_t pl) { return pl->cache; }
 bool plan_profiled(cs_plan_t pl) { return pl->tune.profile != 0; }
 cudaEvent_t plan_done_event(cs_plan_t pl) { return pl->done; }
 cs_status set_error(cs_status code, const char *msg) { return fail(code, msg); }
+cs_status validate_params(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL, uint64_t L) {
+    std::vector<uint32_t> qK, qd;
+    return check_params(P, d, M_start, M_inc, SL, L, qK, qd);
+}
 
 }  // namespace cs
 

@@ -168,5 +168,7 @@ void plan_set_sieved(cs_plan_t pl, bool sieved);
 bool plan_profiled(cs_plan_t pl);
 cudaEvent_t plan_done_event(cs_plan_t pl);
 cs_status set_error(cs_status code, const char *msg);
+// parameter checks of cs_plan, without device work
+cs_status validate_params(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL, uint64_t L);
 
 }  // namespace cs

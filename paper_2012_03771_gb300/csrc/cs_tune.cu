@@ -1,0 +1,134 @@
+// Autotuner for the small/large prime threshold T and the tile height.
+//
+// Section 3.2 leaves the threshold open ("naively p > 10 S"; the runtime
+// model's C_mult is about 50).  Here it trades two kernels: the tile sieve costs
+// about M_c per small prime, the walk about M_inc S / p hits plus a few solves
+// per large prime.  Both grow with M_inc at the same rate, so the best T hardly
+// depends on M_inc; it depends on S, on the primes near T and on the GPU.  The
+// tuner therefore times candidate settings on a proxy with the same P, d and SL,
+// M_inc clipped to 1e5 and L to 1e9 (a few tens of milliseconds per run), and
+// keeps the winner per (P, d, SL, ceil(log2 L)) in memory and, if a path is
+// given, in a text file that later processes read back.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/combsieve.h"
+#include "cs_internal.h"
+
+using namespace cs;
+
+namespace {
+
+using Key = std::tuple<uint32_t, uint64_t, uint32_t, uint32_t>;   // P, d, SL, ceil(log2 L)
+struct Choice {
+    uint64_t T_over_S_x100;   // threshold as a multiple of S, times 100
+    uint32_t tile_rows;
+};
+
+std::mutex g_mu;
+std::map<Key, Choice> g_mem;
+
+uint32_t log2_ceil(uint64_t x) {
+    uint32_t k = 0;
+    while (k < 63 && (1ull << k) < x) k++;
+    return k;
+}
+
+void load_file(const char *path) {
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    unsigned P, SL, lg, rows;
+    unsigned long long d, tx;
+    while (fscanf(f, "%u %llu %u %u %llu %u", &P, &d, &SL, &lg, &tx, &rows) == 6)
+        g_mem[Key{P, d, SL, lg}] = Choice{tx, rows};
+    fclose(f);
+}
+
+void append_file(const char *path, const Key &k, const Choice &c) {
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%u %llu %u %u %llu %u\n", std::get<0>(k), (unsigned long long)std::get<1>(k), std::get<2>(k),
+            std::get<3>(k), (unsigned long long)c.T_over_S_x100, c.tile_rows);
+    fclose(f);
+}
+
+// device time of one sieve of the proxy (best of two), or a negative value
+double time_once(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL, uint64_t L,
+                 const cs_tuning &t, cudaStream_t st) {
+    cs_plan_t plan = nullptr;
+    if (cs_plan(P, d, M_start, M_inc, SL, L, &t, &plan)) return -1;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    double best = -1;
+    for (int rep = 0; rep < 3; rep++) {
+        cudaEventRecord(a, st);
+        if (cs_sieve(plan, st)) break;
+        cudaEventRecord(b, st);
+        if (cudaEventSynchronize(b) != cudaSuccess) break;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        if (rep > 0 && (best < 0 || ms < best)) best = ms;   // first run warms up
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cs_destroy(plan);
+    return best;
+}
+
+}  // namespace
+
+extern "C" cs_status cs_autotune(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL,
+                                 uint64_t L, const char *cache_path, cs_tuning *out) {
+    if (!out) return set_error(CS_EINVAL, "out is NULL");
+    cs_status s = validate_params(P, d, M_start, M_inc, SL, L);
+    if (s) return s;
+    memset(out, 0, sizeof(*out));
+    out->large_mode = 2;
+    const uint64_t S = 2ull * SL + 1;
+    const Key key{P, d, SL, log2_ceil(std::max<uint64_t>(L, 2))};
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (cache_path) load_file(cache_path);
+    auto it = g_mem.find(key);
+    if (it == g_mem.end()) {
+        // proxy: same K and interval, fewer m, lower limit
+        const uint64_t pM = std::min<uint64_t>(M_inc, 100000), pL = std::min<uint64_t>(L, 1000000000ull);
+        const uint64_t mults_x100[] = {300, 500, 800, 1200, 2000};
+        const uint32_t rows[] = {16, 32};
+        cudaStream_t st;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+            return set_error(CS_EDEVICE, "cudaStreamCreate");
+        double best = -1;
+        Choice pick{800, 0};
+        for (uint64_t mx : mults_x100)
+            for (uint32_t tr : rows) {
+                cs_tuning t{};
+                t.large_mode = 2;
+                t.tile_rows = tr;
+                t.threshold = std::max<uint64_t>(S * mx / 100, 2ull * SL);
+                if (t.threshold > (1ull << 30)) continue;
+                double ms = time_once(P, d, M_start, pM, SL, pL, t, st);
+                if (ms >= 0 && (best < 0 || ms < best)) {
+                    best = ms;
+                    pick = Choice{mx, tr};
+                }
+            }
+        cudaStreamDestroy(st);
+        if (best < 0) return set_error(CS_EDEVICE, "autotune: no candidate ran");
+        g_mem[key] = pick;
+        if (cache_path) append_file(cache_path, key, pick);
+        it = g_mem.find(key);
+    }
+    out->threshold = std::min<uint64_t>(std::max<uint64_t>(S * it->second.T_over_S_x100 / 100, 2ull * SL), 1ull << 30);
+    out->tile_rows = it->second.tile_rows;
+    return CS_OK;
+}

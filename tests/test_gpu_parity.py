@@ -194,3 +194,23 @@ def test_search_953_sampled_rows_and_invariants():
     expect = prm.M_inc * (2 * prm.SL + 1) * inv + n_large
     assert abs(st["solves"] - expect) < 0.01 * expect
     assert st["n_large_primes"] == n_large
+
+
+def test_autotune_picks_a_valid_tuning_and_caches_it(tmp_path):
+    prm = workloads.PLAIN_503.with_(L=10**8)
+    path = str(tmp_path / "tune.txt")
+    t = cs.cs_autotune(*prm.as_tuple(), cache_path=path)
+    assert t["threshold"] >= 2 * prm.SL and t["tile_rows"] in (16, 32) and t["large_mode"] == 2
+    assert len(open(path).read().split()) == 6                  # one line: key and choice
+    assert cs.cs_autotune(*prm.as_tuple(), cache_path=path) == t
+    ref = _run(prm.as_tuple())
+    got = _run(prm.as_tuple(), **t)
+    assert (got["F"], got["hash"]) == (ref["F"], ref["hash"])
+
+
+def test_environment_overrides_tuning(monkeypatch):
+    prm = workloads.PLAIN_503
+    monkeypatch.setenv("CS_THRESHOLD", "50000")
+    monkeypatch.setenv("CS_TILE_ROWS", "8")
+    with cs.Plan(*prm.as_tuple()) as p:
+        assert p.info.threshold == 50000 and p.info.tile_rows == 8

@@ -320,8 +320,8 @@ def csrc_sha() -> str:
 # constants for the walk sources whose digest is recorded (csrc_sha); they are
 # ignored when those sources change.
 WALK_COUNTERS = {
-    "search_953": {"csrc_sha": "54c668edd10c13a0", "launches": 16,
-                   "thread_inst": 2.6716e11, "dram_bytes": 1.19406e9 + 1.95712e6},
+    "search_953": {"csrc_sha": "d638fe3684485a53", "threshold": 400010, "tile_rows": 16, "launches": 15,
+                   "thread_inst": 2.11233e11, "dram_bytes": 1.17087e9 + 2.14195e6},
 }
 
 
@@ -346,7 +346,9 @@ def roofline(dom, kern_ms, kern_n, stats, info, params, peaks, peak_src, clk, co
            "peak": peak, "unit": "Tinst/s", "frac": None, "traffic": None,
            "peak_source": f"derived: {n_sm} SMs x 4 schedulers x 32 lanes x {sm_mhz:.0f} MHz (integer issue rate)"}
     ctr = WALK_COUNTERS.get(config)
-    if name == "large_walk" and ctr and ctr["csrc_sha"] == csrc_sha():
+    same_setup = ctr is not None and (ctr.get("threshold"), ctr.get("tile_rows")) == (int(info.threshold),
+                                                                                     int(info.tile_rows))
+    if name == "large_walk" and ctr and ctr["csrc_sha"] == csrc_sha() and same_setup:
         sieves = n_launch / ctr["launches"]
         inst_launch = ctr["thread_inst"] / ctr["launches"]
         out["achieved"] = inst_launch / per_launch_s / 1e12
@@ -357,7 +359,7 @@ def roofline(dom, kern_ms, kern_n, stats, info, params, peaks, peak_src, clk, co
         out["launches_timed"] = n_launch
         del sieves
     else:
-        out["note"] = "ncu instruction counts not recorded for these sources"
+        out["note"] = "ncu instruction counts not recorded for these sources and this threshold / tile height"
     return out
 
 

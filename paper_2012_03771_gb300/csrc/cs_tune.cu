@@ -61,7 +61,8 @@ void append_file(const char *path, const Key &k, const Choice &c) {
     fclose(f);
 }
 
-// device time of one sieve of the proxy (best of two), or a negative value
+// device time of one sieve of the proxy (median of five after one warm-up run),
+// or a negative value
 double time_once(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL, uint64_t L,
                  const cs_tuning &t, cudaStream_t st) {
     cs_plan_t plan = nullptr;
@@ -69,20 +70,22 @@ double time_once(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint3
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    double best = -1;
-    for (int rep = 0; rep < 3; rep++) {
+    std::vector<float> ts;
+    for (int rep = 0; rep < 6; rep++) {
         cudaEventRecord(a, st);
         if (cs_sieve(plan, st)) break;
         cudaEventRecord(b, st);
         if (cudaEventSynchronize(b) != cudaSuccess) break;
         float ms = 0;
         cudaEventElapsedTime(&ms, a, b);
-        if (rep > 0 && (best < 0 || ms < best)) best = ms;   // first run warms up
+        if (rep > 0) ts.push_back(ms);
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     cs_destroy(plan);
-    return best;
+    if (ts.size() < 5) return -1;
+    std::sort(ts.begin(), ts.end());
+    return ts[ts.size() / 2];
 }
 
 }  // namespace
@@ -102,7 +105,7 @@ extern "C" cs_status cs_autotune(uint32_t P, uint64_t d, uint64_t M_start, uint6
     if (it == g_mem.end()) {
         // proxy: same K and interval, fewer m, lower limit
         const uint64_t pM = std::min<uint64_t>(M_inc, 100000), pL = std::min<uint64_t>(L, 1000000000ull);
-        const uint64_t mults_x100[] = {300, 500, 800, 1200, 2000};
+        const uint64_t mults_x100[] = {300, 400, 500, 600, 800, 1000, 1200, 1600};
         const uint32_t rows[] = {16, 32};
         cudaStream_t st;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)

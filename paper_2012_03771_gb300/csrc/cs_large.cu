@@ -87,7 +87,8 @@ __device__ __forceinline__ void record_hit(const DevPlan &pl, uint64_t moff, UT 
     c.F += ok;
 }
 
-template <class UT, class ST, int MODE>
+// One thread per work item, one G solve per hit (the walk of Section 3.2).
+template <class UT, class ST>
 __global__ void __launch_bounds__(LARGE_THREADS) k_large(const LargeArgs a) {
     const DevPlan &pl = a.pl;
     const UT *Pp = reinterpret_cast<const UT *>(a.p);
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_large(const LargeArgs a) {
         UT v = Vp ? Vp[i] : start_v(r, pl.M_start, pl.SL, p);
         if (m_lo) v = advance(v, r, m_lo, p);
         uint32_t it = 0;
-        if (MODE == LARGE_PAPER) {
+        {
             uint64_t m = 0;
             while (true) {
                 if (v <= w) {
@@ -133,65 +134,6 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_large(const LargeArgs a) {
                 if ((uint64_t)t >= Mseg - m) break;
                 m += t;
                 v = (UT)(v + y - p);
-            }
-        } else {
-            // one fused pass of the solver over three windows of the same
-            // (p, r): the first m with r*m mod p in [p - 2SL, p - 1] (step that
-            // lowers v by da), in [1, 2SL] (raises it by ub), and the first hit
-            // from v (skipped, L = 0, when v is already in the window)
-            UT ma, da, mb = 0, ub = 0;
-            uint64_t m = 0;
-            if (w == 0) {
-                ma = p;
-                da = 0;
-                if (v > w) {
-                    UT t, y;
-                    c.solves++;
-                    if (!g_solve<UT, ST>(p, r, (UT)(p - v), w, t, y, it, max_iter)) {
-                        c.err |= ERR_SOLVER_LIMIT;
-                        continue;
-                    }
-                    if ((uint64_t)t >= Mseg) {
-                        c.levels += it;
-                        continue;
-                    }
-                    m = t;
-                    v = (UT)(v + y - p);
-                }
-            } else {
-                const bool first = v > w;
-                const UT L3[3] = {(UT)(p - w), (UT)1, first ? (UT)(p - v) : (UT)0};
-                const UT W3[3] = {(UT)(w - 1), (UT)(w - 1), w};
-                UT m3[3], y3[3];
-                c.solves += 2 + first;
-                if (!g_solve_multi<UT, ST, 3>(p, r, L3, W3, m3, y3, it, max_iter)) {
-                    c.err |= ERR_SOLVER_LIMIT;
-                    continue;
-                }
-                ma = m3[0];
-                da = p - y3[0];
-                mb = m3[1];
-                ub = y3[1];
-                if (first) {
-                    if ((uint64_t)m3[2] >= Mseg) {
-                        c.levels += it;
-                        continue;
-                    }
-                    m = m3[2];
-                    v = (UT)(v + y3[2] - p);
-                }
-            }
-            const uint64_t mab = (uint64_t)ma + mb;
-            while (true) {
-                record_hit<UT>(pl, m_lo + m, v, p, c);
-                // three-distance step, as selects
-                const bool down = v >= da;
-                const bool up = v + ub <= w;
-                const UT vd = v - da, vu = v + ub;
-                v = down ? vd : (up ? vu : (UT)(vu - da));
-                const uint64_t step = down ? (uint64_t)ma : (up ? (uint64_t)mb : mab);
-                if (step >= Mseg - m) break;
-                m += step;
             }
         }
         c.levels += it;
@@ -394,12 +336,12 @@ cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p
     if (grid <= 0) grid = sm_count() * 8;
     if (narrow) {
         if (mode == LARGE_PAPER)
-            k_large<uint32_t, int32_t, LARGE_PAPER><<<grid, LARGE_THREADS, 0, stream>>>(a);
+            k_large<uint32_t, int32_t><<<grid, LARGE_THREADS, 0, stream>>>(a);
         else
             k_large_tg<uint32_t, int32_t, uint32_t><<<grid, LARGE_THREADS, 0, stream>>>(a);
     } else {
         if (mode == LARGE_PAPER)
-            k_large<uint64_t, int64_t, LARGE_PAPER><<<grid, LARGE_THREADS, 0, stream>>>(a);
+            k_large<uint64_t, int64_t><<<grid, LARGE_THREADS, 0, stream>>>(a);
         else
             k_large_tg<uint64_t, int64_t, uint64_t><<<grid, LARGE_THREADS, 0, stream>>>(a);
     }

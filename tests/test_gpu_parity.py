@@ -214,3 +214,22 @@ def test_environment_overrides_tuning(monkeypatch):
     monkeypatch.setenv("CS_TILE_ROWS", "8")
     with cs.Plan(*prm.as_tuple()) as p:
         assert p.info.threshold == 50000 and p.info.tile_rows == 8
+
+
+def test_wide_interval_uses_several_column_chunks():
+    """X = 5e5: one row of raw offsets no longer fits in shared memory, so the
+    tile sieve works on column chunks; rows against the oracle."""
+    prm = workloads.SieveParams(P=37, d=30, M_start=10**9 + 7, M_inc=12, SL=500_000, L=200_000)
+    got = _run(prm.as_tuple())
+    assert got["info"].tile_rows == 1
+    _check_full(prm.as_tuple(), got)
+    got2 = _run(prm.as_tuple(), tile_rows=4)
+    assert (got2["F"], got2["hash"]) == (got["F"], got["hash"])
+
+
+def test_large_divisor_wheel():
+    """d with a prime factor above 64 (the wheel's pattern tables grow with q)."""
+    prm = workloads.SieveParams(P=101, d=2 * 3 * 5 * 7 * 97, M_start=1000, M_inc=500, SL=3000, L=10**6)
+    for no_wheel in (False, True):
+        got = _run(prm.as_tuple(), no_wheel=no_wheel)
+        _check_full(prm.as_tuple(), got, wheel=not no_wheel)

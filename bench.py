@@ -151,7 +151,7 @@ def _config(params, info, name="search_953"):
     if info is not None:
         c.update({"M_c": int(info.M_c), "W": int(info.W), "bitset_bytes": int(info.bitset_bytes),
                   "threshold": int(info.threshold), "large_mode": int(info.large_mode),
-                  "tile_rows": int(info.tile_rows)})
+                  "tile_rows": int(info.tile_rows), "layout": "compact" if info.layout else "x coprime to K"})
     return c
 
 
@@ -182,6 +182,8 @@ def run_cuda(args, params):
         tuning["large_mode"] = args.mode
     if args.threshold:
         tuning["threshold"] = args.threshold
+    if args.layout:
+        tuning["layout"] = args.layout
     plan = cs.Plan(*params.as_tuple(), **tuning)
     info = plan.info
 
@@ -546,6 +548,7 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--layout", type=int, default=0, help="1 = compact rows (no wheel offsets stored)")
     args = ap.parse_args()
     rank, ws = _dist()
     if args.config == "batched_64":

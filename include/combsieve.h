@@ -77,12 +77,19 @@ typedef struct {
     uint32_t large_grid;     /* CTAs of the large-prime kernel; 0 = automatic */
     uint64_t chunk_numbers;  /* width of one large-prime chunk of (T, L]; 0 = automatic */
     uint32_t profile;        /* 1 = time each kernel with CUDA events (cs_kernel_times) */
-    uint32_t reserved[7];
+    uint32_t layout;         /* 0 = columns x coprime to K (the same for every row);
+                                1 = compact: row m keeps only the x with gcd(m K + x, d) = 1
+                                (the x the wheel would clear are not stored), so its columns
+                                depend on m mod d (cs_row_columns).  Needs the wheel, no
+                                N + x small enough to be a prime of d, phi(d) <= 4096 and an
+                                interval whose tile fits in one piece (SL up to about 3.7e5).
+                                F and the per-row counts are the same in both layouts. */
+    uint32_t reserved[6];
 } cs_tuning;
 
 typedef struct {
     uint64_t M_c;              /* rows */
-    uint64_t W;                /* columns */
+    uint64_t W;                /* columns (layout 1: the widest row's) */
     uint64_t words_per_row;    /* ceil(W / 64) */
     uint64_t bitset_bytes;     /* M_c * words_per_row * 8 */
     uint64_t S;                /* 2*SL + 1 */
@@ -97,6 +104,8 @@ typedef struct {
     uint64_t device_bytes;     /* device memory held by the plan */
     uint64_t est_cost;         /* relative device cost estimate (about picoseconds on a
                                   GB300), used to order instances in a batch */
+    uint32_t layout;           /* 0 literal, 1 compact */
+    uint32_t n_classes;        /* compact: residue classes of m mod d (phi(d)), else 1 */
 } cs_info_t;
 
 typedef struct {
@@ -151,6 +160,11 @@ cs_status cs_stats(cs_plan_t plan, cs_stats_t *out);
 /* The plan's row map (m of each row) and column map (x of each column). */
 cs_status cs_rows(cs_plan_t plan, uint64_t *m_of_row, size_t n);
 cs_status cs_columns(cs_plan_t plan, int64_t *x_of_col, size_t n);
+
+/* Columns of one row: the x values of its bits in order (layout 0: the same
+ * for every row, as cs_columns; layout 1: the row's own set).  *n_cols gets
+ * the count (at most W); n is the capacity of x_of_col. */
+cs_status cs_row_columns(cs_plan_t plan, uint64_t row, int64_t *x_of_col, size_t n, uint64_t *n_cols);
 
 /* Borrowed device pointer to the bitset; valid until cs_destroy. */
 const void *cs_device_bitset(cs_plan_t plan);

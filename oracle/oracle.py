@@ -179,6 +179,44 @@ def primes(lo: int, hi: int) -> np.ndarray:
     return out[:n].copy()
 
 
+def compact_layout(P: int, d: int, SL: int, rows_m, bits: np.ndarray):
+    """The compact layout written out from the literal one: row m keeps, in
+    order, the literal columns x with gcd(m*K + x, d) = 1 (the offsets the wheel
+    of d's primes would clear are not stored).  All rows are padded to
+    ceil(W_max / 64) words, W_max the largest such column count over the
+    residues rho of m mod d that are coprime to d.
+    Returns (bits_compact, W_max, per-row column lists)."""
+    xs = columns(P, d, SL)
+    qd = [q for q in _simple_primes(P) if d % q == 0]
+    K = 1
+    for q in _simple_primes(P):
+        if d % q:
+            K *= q
+    kq = {q: K % q for q in qd}
+
+    def keep_mask(rho):
+        keep = np.ones(xs.size, dtype=bool)
+        for q in qd:
+            keep &= ((rho * kq[q] + xs) % q) != 0
+        return keep
+
+    residues = [rho for rho in range(d) if math.gcd(rho, d) == 1]
+    masks = {rho: keep_mask(rho) for rho in residues}
+    W_max = max(int(m.sum()) for m in masks.values())
+    wpr = (W_max + 63) // 64
+    out = np.zeros((len(rows_m), max(wpr, 1)), dtype=np.uint64)
+    cols = []
+    for i, m in enumerate(rows_m):
+        keep = masks[int(m) % d]
+        lit = unpack_row(bits[i], xs.size)
+        sel = lit[keep]
+        packed = np.packbits(np.concatenate([sel, np.zeros(64 * wpr - sel.size, dtype=np.uint8)]).astype(np.uint8),
+                             bitorder="little")
+        out[i, :wpr] = packed.view("<u8")
+        cols.append(xs[keep])
+    return out[:, :wpr], W_max, cols
+
+
 def full_sieve(P, d, M_start, M_inc, SL, L, *, wheel=True, threads=0):
     """Whole bitset of a parameter set: (m_of_row, bits, F_rows)."""
     if validate(P, d, M_start, M_inc, SL, L):

@@ -36,7 +36,7 @@ EXPORTS = ("cs_plan", "cs_sieve", "cs_sync", "cs_info", "cs_fetch_bitset", "cs_c
            "cs_batch_create", "cs_batch_run", "cs_batch_sync", "cs_batch_info", "cs_batch_destroy",
            "cs_server_start", "cs_submit", "cs_poll", "cs_server_plan", "cs_release", "cs_server_usage",
            "cs_server_stop", "cs_fetch_rows", "cs_cache_create", "cs_cache_fill", "cs_cache_info",
-           "cs_cache_destroy", "cs_plan_cached", "cs_autotune")
+           "cs_cache_destroy", "cs_plan_cached", "cs_autotune", "cs_row_columns")
 
 
 class CSError(RuntimeError):
@@ -49,7 +49,7 @@ class cs_tuning(ctypes.Structure):
     _fields_ = [("threshold", ctypes.c_uint64), ("tile_rows", ctypes.c_uint32),
                 ("large_mode", ctypes.c_uint32), ("no_wheel", ctypes.c_uint32),
                 ("large_grid", ctypes.c_uint32), ("chunk_numbers", ctypes.c_uint64),
-                ("profile", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 7)]
+                ("profile", ctypes.c_uint32), ("layout", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 6)]
 
 
 class cs_info_t(ctypes.Structure):
@@ -59,7 +59,7 @@ class cs_info_t(ctypes.Structure):
                 ("narrow", ctypes.c_uint32), ("wheel", ctypes.c_uint32),
                 ("n_large_chunks", ctypes.c_uint64), ("launches_per_sieve", ctypes.c_uint64),
                 ("h2d_bytes", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
-                ("est_cost", ctypes.c_uint64)]
+                ("est_cost", ctypes.c_uint64), ("layout", ctypes.c_uint32), ("n_classes", ctypes.c_uint32)]
 
 
 class cs_stats_t(ctypes.Structure):
@@ -94,6 +94,7 @@ def load(path: Optional[str] = None):
         lib.cs_stats.argtypes = [vp, ctypes.POINTER(cs_stats_t)]
         lib.cs_rows.argtypes = [vp, vp, sz]
         lib.cs_columns.argtypes = [vp, vp, sz]
+        lib.cs_row_columns.argtypes = [vp, u64, vp, sz, P64]
         lib.cs_device_bitset.argtypes = [vp]
         lib.cs_device_bitset.restype = vp
         lib.cs_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), P64]
@@ -149,8 +150,9 @@ def _stream_handle(stream) -> ctypes.c_void_p:
 
 
 def make_tuning(threshold=0, tile_rows=0, large_mode=0, no_wheel=False, large_grid=0,
-                chunk_numbers=0, profile=False) -> cs_tuning:
+                chunk_numbers=0, profile=False, layout=0) -> cs_tuning:
     t = cs_tuning()
+    t.layout = layout
     t.threshold, t.tile_rows, t.large_mode = threshold, tile_rows, large_mode
     t.no_wheel, t.large_grid, t.chunk_numbers = int(no_wheel), large_grid, chunk_numbers
     t.profile = int(profile)
@@ -368,6 +370,13 @@ class Plan:
 
     def columns(self):
         return cs_columns(self.h, self.W)
+
+    def row_columns(self, row):
+        """x values of one row's bits (the compact layout's differ by row)."""
+        out = np.zeros(max(int(self.W), 1), dtype=np.int64)
+        n = ctypes.c_uint64()
+        _check(load().cs_row_columns(self.h, row, _ptr(out), out.size, ctypes.byref(n)))
+        return out[:n.value]
 
     def kernel_times(self):
         return cs_kernel_times(self.h)

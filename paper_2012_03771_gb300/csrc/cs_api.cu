@@ -90,6 +90,10 @@ struct cs_plan_s {
     uint64_t M_c = 0, W = 0, wpr = 0, S = 0, S32 = 0, T = 0, small_hi = 0;
     bool narrow = true, wheel = true;
     int mode = LARGE_THREE_GAP;
+    uint32_t layout = 0;
+    // compact layout, host copies: classes' widths and raw offsets of columns
+    uint32_t n_cls = 1, cls0 = 0, Wc_max = 0;
+    std::vector<uint32_t> cW_h, craw_h;
     std::vector<uint64_t> m_of_row;
     std::vector<int64_t> x_of_col;
     std::vector<std::pair<uint64_t, uint64_t>> chunks;    // large-prime ranges (lo, hi]
@@ -281,7 +285,8 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
         col_prefix[w] = (uint32_t)c;
         c += __builtin_popcount(col_mask[w]);
     }
-    const uint64_t W = raw_of_col.size(), wpr = (W + 63) / 64;
+    const uint64_t W = raw_of_col.size();
+    uint64_t wpr = (W + 63) / 64;
 
     // rows: m coprime to d
     std::vector<uint32_t> moff_of_row;
@@ -324,6 +329,62 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
                 wpat.push_back(b);
             }
         }
+    }
+
+    // compact layout: per residue class rho of m mod d, the literal columns
+    // that the wheel keeps (gcd(rho K + x, d) = 1)
+    pl->layout = pl->tune.layout;
+    std::vector<uint32_t> cmask, cprefix;
+    if (pl->layout > 1) return fail(CS_EINVAL, "layout must be 0 or 1");
+    if (pl->layout == 1) {
+        if (!pl->wheel) return fail(CS_EINVAL, "the compact layout needs the wheel");
+        if (k_fits && (unsigned __int128)M_start * K64 - SL <= (unsigned __int128)P)
+            return fail(CS_EINVAL, "the compact layout needs N + x above the primes of d");
+        uint64_t phi = 1;
+        for (uint32_t q : qd) phi *= (q - 1);
+        if (phi > 4096) return fail(CS_EINVAL, "the compact layout needs phi(d) <= 4096");
+        std::vector<uint64_t> res;
+        for (uint64_t rho = 0; rho < d; rho++) {
+            bool ok = true;
+            for (uint32_t q : qd) ok = ok && rho % q != 0;
+            if (ok) res.push_back(rho);
+        }
+        pl->n_cls = (uint32_t)res.size();
+        cmask.assign((size_t)pl->n_cls * S32, 0);
+        cprefix.assign((size_t)pl->n_cls * S32, 0);
+        pl->cW_h.assign(pl->n_cls, 0);
+        std::vector<std::vector<uint32_t>> lists(pl->n_cls);
+        for (uint32_t k = 0; k < pl->n_cls; k++) {
+            uint32_t *cm = &cmask[(size_t)k * S32];
+            for (uint64_t w = 0; w < S32; w++) cm[w] = col_mask[w];
+            for (size_t qi = 0; qi < qd.size(); qi++) {
+                const uint64_t q = qd[qi], kq = wkmod[qi];
+                // z = x + SL with q | rho K + x:  z = SL - rho K (mod q)
+                uint64_t z = ((SL % q) + q - (res[k] % q) * kq % q) % q;
+                for (; z < S; z += q) cm[z >> 5] &= ~(1u << (z & 31));
+            }
+            uint32_t c = 0;
+            for (uint64_t w = 0; w < S32; w++) {
+                cprefix[(size_t)k * S32 + w] = c;
+                uint32_t bits = cm[w];
+                while (bits) {
+                    uint32_t b = __builtin_ctz(bits);
+                    bits &= bits - 1;
+                    lists[k].push_back((uint32_t)(32 * w + b));
+                }
+                c += __builtin_popcount(cm[w]);
+            }
+            pl->cW_h[k] = c;
+            pl->Wc_max = std::max(pl->Wc_max, c);
+        }
+        pl->craw_h.assign((size_t)pl->n_cls * std::max<uint32_t>(pl->Wc_max, 1), 0);
+        for (uint32_t k = 0; k < pl->n_cls; k++)
+            std::copy(lists[k].begin(), lists[k].end(), pl->craw_h.begin() + (size_t)k * std::max<uint32_t>(pl->Wc_max, 1));
+        if (M_c) {
+            const uint64_t r0 = pl->m_of_row[0] % d;
+            pl->cls0 = (uint32_t)(std::lower_bound(res.begin(), res.end(), r0) - res.begin());
+        }
+        wpr = (pl->Wc_max + 63) / 64;
     }
 
     // small / large threshold and work split
@@ -403,6 +464,8 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
     }
     uint64_t max_words_per_chunk = budget / (TR + 1);
     if (max_words_per_chunk < 64) return fail(CS_EINVAL, "tile_rows too large for shared memory");
+    if (pl->layout == 1 && (uint64_t)(TR + 1) * full_words > budget)
+        return fail(CS_EINVAL, "the compact layout needs the interval's tile in one piece (smaller SL or tile_rows)");
     uint32_t max_words = 1;
     if (W == 0) {
         chunk_tab = {0, 0, 0, 0};
@@ -472,6 +535,18 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
     if ((s = pl->upload(&d_wp, wpat))) return s;
     dp.qd = d_wq; dp.qd_kmod = d_wk; dp.qd_pat_off = d_wo; dp.qd_pat = d_wp;
     dp.n_qd = (uint32_t)wq.size();
+    dp.compact = pl->layout == 1;
+    dp.n_cls = pl->n_cls;
+    dp.cls0 = pl->cls0;
+    dp.Wc_max = pl->Wc_max;
+    if (dp.compact) {
+        uint32_t *d_cm, *d_cp, *d_cr, *d_cw;
+        if ((s = pl->upload(&d_cm, cmask))) return s;
+        if ((s = pl->upload(&d_cp, cprefix))) return s;
+        if ((s = pl->upload(&d_cr, pl->craw_h))) return s;
+        if ((s = pl->upload(&d_cw, pl->cW_h))) return s;
+        dp.cmask = d_cm; dp.cprefix = d_cp; dp.craw = d_cr; dp.cW = d_cw;
+    }
     uint64_t *d_bits; uint32_t *d_cnt; unsigned long long *d_stats;
     if ((s = pl->dalloc(&d_bits, M_c * wpr))) return s;
     if ((s = pl->dalloc(&d_cnt, M_c))) return s;
@@ -700,6 +775,9 @@ cs_status cs_info(cs_plan_t pl, cs_info_t *out) {
     out->h2d_bytes = pl->h2d;
     out->device_bytes = pl->dev_bytes;
     out->est_cost = pl->est_cost;
+    out->layout = pl->layout;
+    out->n_classes = pl->n_cls;
+    if (pl->layout == 1) out->W = pl->Wc_max;
     return CS_OK;
 }
 
@@ -783,6 +861,24 @@ cs_status cs_columns(cs_plan_t pl, int64_t *x_of_col, size_t n) {
     if (!pl) return fail(CS_EINVAL, "plan is NULL");
     if (n < pl->W) return fail(CS_ESIZE, "buffer smaller than W");
     if (pl->W) memcpy(x_of_col, pl->x_of_col.data(), pl->W * 8);
+    return CS_OK;
+}
+
+cs_status cs_row_columns(cs_plan_t pl, uint64_t row, int64_t *x_of_col, size_t n, uint64_t *n_cols) {
+    if (!pl || !n_cols) return fail(CS_EINVAL, "NULL argument");
+    if (row >= pl->M_c) return fail(CS_EINVAL, "row beyond M_c");
+    if (pl->layout == 0) {
+        *n_cols = pl->W;
+        if (n < pl->W) return fail(CS_ESIZE, "buffer smaller than the row's columns");
+        if (pl->W) memcpy(x_of_col, pl->x_of_col.data(), pl->W * 8);
+        return CS_OK;
+    }
+    const uint32_t k = (uint32_t)((pl->cls0 + row) % pl->n_cls);
+    const uint32_t w = pl->cW_h[k];
+    *n_cols = w;
+    if (n < w) return fail(CS_ESIZE, "buffer smaller than the row's columns");
+    const uint32_t *raw = &pl->craw_h[(size_t)k * std::max<uint32_t>(pl->Wc_max, 1)];
+    for (uint32_t j = 0; j < w; j++) x_of_col[j] = (int64_t)raw[j] - pl->SL;
     return CS_OK;
 }
 

@@ -65,6 +65,15 @@ struct DevPlan {
     const uint32_t *qd_kmod;      // K mod q
     const uint32_t *qd_pat_off;   // offset of q's pattern table in qd_pat
     const uint32_t *qd_pat;       // pattern[k]: bits i < 32 with (k + i) % q == 0
+    // compact layout: per residue class of m mod d (ascending), the stored
+    // columns are the literal ones the wheel does not clear
+    int compact;
+    uint32_t n_cls, cls0;         // classes, class of row 0 (row i has class (cls0 + i) % n_cls)
+    const uint32_t *cmask;        // n_cls x S32: stored raw offsets of the class
+    const uint32_t *cprefix;      // n_cls x S32: stored columns before each word
+    const uint32_t *craw;         // n_cls x Wc_max: raw offset of each column of the class
+    const uint32_t *cW;           // n_cls: columns of the class
+    uint32_t Wc_max;
     // outputs
     uint64_t *bits;               // M_c * wpr words
     uint32_t *counts;             // M_c

@@ -146,17 +146,25 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile(const TileArgs a) {
     __syncthreads();
 
     // 3. compress the stored columns [j0, j1) of each row into the output words
+    //    (compact layout: the row's class columns, one chunk covers the row)
     const bool last_chunk = chunk + 1 == a.tc.n_chunks;
     const uint32_t jend = last_chunk ? 64 * pl.wpr : j1;      // pad the row with zeros
     for (uint32_t r = warp; r < nrows; r += TILE_WARPS) {
         uint32_t *out = reinterpret_cast<uint32_t *>(pl.bits + (row0 + r) * pl.wpr);
+        const uint32_t *raw = pl.raw_of_col;
+        uint32_t jlim = min(pl.W, j1);
+        if (pl.compact) {
+            const uint32_t cls = (uint32_t)((pl.cls0 + row0 + r) % pl.n_cls);
+            raw = pl.craw + (size_t)cls * pl.Wc_max;
+            jlim = __ldg(&pl.cW[cls]);
+        }
         uint32_t keep = 0;
         uint32_t k = 0;
         for (uint32_t jb = j0; jb < jend; jb += 32, k++) {
             const uint32_t j = jb + lane;
             uint32_t bit = 0;
-            if (j < pl.W && j < j1) {
-                const uint32_t zz = __ldg(&pl.raw_of_col[j]) - zb;
+            if (j < jlim) {
+                const uint32_t zz = __ldg(&raw[j]) - zb;
                 bit = (tile[r * nw + (zz >> 5)] >> (zz & 31)) & 1u;
             }
             const uint32_t word = __ballot_sync(0xffffffffu, bit);

@@ -233,3 +233,34 @@ def test_large_divisor_wheel():
     for no_wheel in (False, True):
         got = _run(prm.as_tuple(), no_wheel=no_wheel)
         _check_full(prm.as_tuple(), got, wheel=not no_wheel)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_compact_layout_matches_oracle(mode):
+    """Layout 1: per-row columns without the wheel's offsets, bit-exact, with the
+    same F and per-row counts as the literal layout."""
+    for prm in (workloads.PLAIN_503,
+                workloads.SieveParams(P=37, d=30, M_start=10**6, M_inc=300, SL=400, L=10**5),
+                workloads.SieveParams(P=503, d=2310, M_start=10**6, M_inc=3000, SL=3000, L=3 * 10**9)):
+        args = prm.as_tuple()
+        lit = _run(args, large_mode=mode)
+        with cs.Plan(*args, layout=1, large_mode=mode) as p:
+            p.sieve(torch.cuda.current_stream()).sync()
+            bits = p.bitset()
+            counts, F, h = p.counts()
+            m = p.rows()
+            pick = list(range(len(m))) if len(m) <= 300 else [0, 1, len(m) // 2, len(m) - 1]
+            ref_lit, _, _ = O.sieve(prm.P, prm.d, prm.SL, prm.L, [int(m[i]) for i in pick])
+            comp, W_max, cols = O.compact_layout(prm.P, prm.d, prm.SL, [int(m[i]) for i in pick], ref_lit)
+            assert p.info.W == W_max and p.info.words_per_row == comp.shape[1]
+            for k, i in enumerate(pick):
+                assert np.array_equal(bits[i], comp[k]), (prm, i)
+                assert np.array_equal(p.row_columns(i), cols[k])
+        assert F == lit["F"]
+        assert np.array_equal(counts, lit["counts"])
+
+
+def test_compact_layout_size_of_the_search():
+    """search_953 in the compact layout: about 9 MB instead of 37.5 MB."""
+    with cs.Plan(*workloads.SEARCH_953.as_tuple(), layout=1) as p:
+        assert p.info.bitset_bytes < 9.5e6

@@ -315,3 +315,22 @@ def test_hash_properties():
     b3[[0, 1]] = b3[[1, 0]]
     assert O.bitset_hash(b3) != h
     assert list(O.row_counts(bits)) == [sum(bin(int(v)).count("1") for v in r) for r in bits]
+
+
+def test_compact_layout_is_the_wheel_survivor_subset():
+    """Compact rows hold exactly the literal columns with gcd(N + x, d) = 1, in
+    order; their popcount equals the literal row's (the wheel cleared the rest)."""
+    P, d, M_start, M_inc, SL, L = 37, 210, 1000, 60, 300, 4000
+    K = _K(P, d)
+    m, bits, F = O.full_sieve(P, d, M_start, M_inc, SL, L)
+    comp, W_max, cols = O.compact_layout(P, d, SL, m, bits)
+    assert list(O.row_counts(comp)) == list(O.row_counts(bits))
+    xs = O.columns(P, d, SL)
+    for i, mm in enumerate(m):
+        expect = [int(x) for x in xs if math.gcd(int(mm) * K + int(x), d) == 1]
+        assert [int(x) for x in cols[i]] == expect
+        row = O.unpack_row(comp[i], len(expect))
+        lit = dict(zip((int(x) for x in xs), O.unpack_row(bits[i], len(xs))))
+        assert list(row) == [lit[x] for x in expect]
+    assert W_max == max(sum(1 for x in xs if math.gcd(rho * K + int(x), d) == 1)
+                        for rho in range(d) if math.gcd(rho, d) == 1)

@@ -136,23 +136,25 @@ def run_reference(args, params):
     line = {"impl": "reference", "metric": metric_of(params), "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * ts / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-            "data": "synthetic", "config": _config(params, None, args.config),
+            "data": "synthetic", "config": _config(params, args.config),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def _config(params, info, name="search_953"):
-    c = {"workload": f"{name}: K={params.P}#/{params.d}, m in [{params.M_start}, {params.M_start + params.M_inc}) "
-                     f"coprime to {params.d}, X={params.SL}, primes {params.P} < p <= {params.L}",
-         "P": params.P, "d": params.d, "M_start": params.M_start, "M_inc": params.M_inc, "SL": params.SL,
-         "L": params.L, "parallelism": "replicas (independent m-ranges per rank)",
-         "l2": "flushed between steps (256 MB device write)"}
-    if info is not None:
-        c.update({"M_c": int(info.M_c), "W": int(info.W), "bitset_bytes": int(info.bitset_bytes),
-                  "threshold": int(info.threshold), "large_mode": int(info.large_mode),
-                  "tile_rows": int(info.tile_rows), "layout": "compact" if info.layout else "x coprime to K"})
-    return c
+def _config(params, name="search_953"):
+    """The workload, identical for both arms (implementation details go elsewhere)."""
+    return {"workload": f"{name}: K={params.P}#/{params.d}, m in [{params.M_start}, {params.M_start + params.M_inc}) "
+                        f"coprime to {params.d}, X={params.SL}, primes {params.P} < p <= {params.L}",
+            "P": params.P, "d": params.d, "M_start": params.M_start, "M_inc": params.M_inc, "SL": params.SL,
+            "L": params.L, "parallelism": "replicas (independent m-ranges per rank)",
+            "l2": "flushed between steps (256 MB device write)"}
+
+
+def _shape(info, tuned):
+    return {"M_c": int(info.M_c), "W": int(info.W), "bitset_bytes": int(info.bitset_bytes),
+            "threshold": int(info.threshold), "large_mode": int(info.large_mode), "tile_rows": int(info.tile_rows),
+            "layout": "compact" if info.layout else "x coprime to K", "autotuned": tuned is not None}
 
 
 def run_cuda(args, params):
@@ -281,7 +283,8 @@ def run_cuda(args, params):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32" if info.narrow else "u64",
             "data": "synthetic (parameters of the paper-shaped search; primes generated on device)",
-            "config": dict(_config(params, info, args.config), autotuned=tuned is not None),
+            "config": _config(params, args.config),
+            "plan": _shape(info, tuned),
             "intervals_per_s": intervals_s,
             "F_per_step": int(F_ref), "hash": f"{h_ref:#018x}",
             "stats": stats,

@@ -540,7 +540,12 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
     dp.cls0 = pl->cls0;
     dp.Wc_max = pl->Wc_max;
     if (dp.compact) {
-        uint32_t *d_cm, *d_cp, *d_cr, *d_cw;
+        // class of the first row in each 32-m word of the row mask
+        std::vector<uint32_t> cls_word(row_mask.size(), 0);
+        for (size_t w = 0; w < row_mask.size(); w++) cls_word[w] = (uint32_t)((pl->cls0 + row_prefix[w]) % pl->n_cls);
+        uint32_t *d_cm, *d_cp, *d_cr, *d_cw, *d_cls;
+        if ((s = pl->upload(&d_cls, cls_word))) return s;
+        dp.cls_word = d_cls;
         if ((s = pl->upload(&d_cm, cmask))) return s;
         if ((s = pl->upload(&d_cp, cprefix))) return s;
         if ((s = pl->upload(&d_cr, pl->craw_h))) return s;

@@ -73,6 +73,7 @@ struct DevPlan {
     const uint32_t *cprefix;      // n_cls x S32: stored columns before each word
     const uint32_t *craw;         // n_cls x Wc_max: raw offset of each column of the class
     const uint32_t *cW;           // n_cls: columns of the class
+    const uint32_t *cls_word;     // ceil(M_inc/32): class of the first row at or after m = M_start + 32 w
     uint32_t Wc_max;
     // outputs
     uint64_t *bits;               // M_c * wpr words

@@ -82,12 +82,14 @@ __device__ __forceinline__ void record_hit(const DevPlan &pl, uint64_t moff, UT 
     const uint32_t row = rp + __popc(rw & (rb - 1));
     uint32_t col = cp + __popc(cw & (cb - 1));
     bool store = ok;                                     // F counts every stored x coprime to K
-    if (pl.compact) {
-        // the row's class keeps only x with gcd(N + x, d) = 1
-        const uint32_t cls = (pl.cls0 + row) % pl.n_cls;
+    if (pl.compact && ok) {
+        // the row's class keeps only x with gcd(N + x, d) = 1; class of the
+        // first row of this 32-m word, plus the rows before m in the word
+        uint32_t cls = __ldg(&pl.cls_word[moff >> 5]) + __popc(rw & (rb - 1));
+        while (cls >= pl.n_cls) cls -= pl.n_cls;
         const uint32_t ccw = __ldg(&pl.cmask[(size_t)cls * pl.S32 + (z >> 5)]);
         col = __ldg(&pl.cprefix[(size_t)cls * pl.S32 + (z >> 5)]) + __popc(ccw & (cb - 1));
-        store = ok && (ccw & cb);
+        store = (ccw & cb) != 0;
     }
     if (store)
         atomicAnd(reinterpret_cast<unsigned long long *>(pl.bits + (uint64_t)row * pl.wpr + (col >> 6)),

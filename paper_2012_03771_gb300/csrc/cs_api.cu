@@ -527,6 +527,17 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
     if ((s = pl->upload(&d_rmask, row_mask))) return s;
     if ((s = pl->upload(&d_rpref, row_prefix))) return s;
     dp.col_mask = d_mask; dp.col_prefix = d_prefix; dp.raw_of_col = d_raw;
+    {
+        // the same tables interleaved as {mask, prefix} pairs for the walk's lookups
+        std::vector<uint32_t> ct(2 * S32), rt(2 * row_mask.size());
+        for (uint64_t w = 0; w < S32; w++) { ct[2 * w] = col_mask[w]; ct[2 * w + 1] = col_prefix[w]; }
+        for (size_t w = 0; w < row_mask.size(); w++) { rt[2 * w] = row_mask[w]; rt[2 * w + 1] = row_prefix[w]; }
+        uint32_t *d_ct, *d_rt;
+        if ((s = pl->upload(&d_ct, ct))) return s;
+        if ((s = pl->upload(&d_rt, rt))) return s;
+        dp.col_tab = reinterpret_cast<const uint2 *>(d_ct);
+        dp.row_tab = reinterpret_cast<const uint2 *>(d_rt);
+    }
     dp.moff_of_row = d_moff; dp.row_mask = d_rmask; dp.row_prefix = d_rpref;
     uint32_t *d_wq, *d_wk, *d_wo, *d_wp;
     if ((s = pl->upload(&d_wq, wq))) return s;

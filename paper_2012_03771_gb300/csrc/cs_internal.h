@@ -56,6 +56,8 @@ struct DevPlan {
     const uint32_t *col_prefix;   // S32 words: stored columns before word
     const uint32_t *raw_of_col;   // W entries: raw offset of column j
     // rows
+    const uint2 *col_tab;         // S32 pairs {col_mask, col_prefix}: one load per lookup
+    const uint2 *row_tab;         // ceil(M_inc/32) pairs {row_mask, row_prefix}
     const uint32_t *moff_of_row;  // M_c entries: m - M_start
     const uint32_t *row_mask;     // ceil(M_inc/32) words: bit k set iff m = M_start + k is a row
     const uint32_t *row_prefix;   // ceil(M_inc/32) words: rows before word

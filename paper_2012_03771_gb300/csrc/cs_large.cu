@@ -58,46 +58,46 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 }
 
 struct Counters {
-    unsigned long long F = 0, solves = 0, levels = 0, hits = 0, err = 0;
+    // per lane and launch: F and hits stay far below 2^32 (at most a few million)
+    uint32_t F = 0, hits = 0;
+    unsigned long long solves = 0, levels = 0, err = 0;
 };
 
 // One hit of prime p at m = M_start + moff with v = (r m + SL) mod p <= 2SL.
 // Branch-free up to the atomic: the row and column tests are bit lookups in
-// small tables (coprime-m mask, stored-x mask, each with per-word prefix
-// counts) that stay in L1.
+// small tables (coprime-m mask, stored-x mask, each interleaved with its
+// per-word prefix counts) that stay in L1.
 template <class UT>
 __device__ __forceinline__ void record_hit(const DevPlan &pl, uint64_t moff, UT v, UT p, Counters &c) {
     c.hits++;
     const uint32_t z = 2 * pl.SL - (uint32_t)v;          // raw offset x + SL
-    const uint32_t rw = __ldg(&pl.row_mask[moff >> 5]);
-    const uint32_t rp = __ldg(&pl.row_prefix[moff >> 5]);
-    const uint32_t cw = __ldg(&pl.col_mask[z >> 5]);
-    const uint32_t cp = __ldg(&pl.col_prefix[z >> 5]);
+    const uint2 rt = __ldg(&pl.row_tab[moff >> 5]);      // {coprime-m mask, rows before}
+    const uint2 ct = __ldg(&pl.col_tab[z >> 5]);         // {stored-x mask, columns before}
     const uint32_t rb = 1u << (moff & 31), cb = 1u << (z & 31);
-    bool ok = (rw & rb) && (cw & cb);                    // m coprime to d, x coprime to K
+    bool ok = (rt.x & rb) && (ct.x & cb);                // m coprime to d, x coprime to K
     if (pl.small_n) {
         unsigned __int128 n = (unsigned __int128)(pl.M_start + moff) * pl.K64 + z - pl.SL;
         ok = ok && n != (unsigned __int128)p;            // N + x is p itself
     }
-    const uint32_t row = rp + __popc(rw & (rb - 1));
-    uint32_t col = cp + __popc(cw & (cb - 1));
+    const uint32_t row = rt.y + __popc(rt.x & (rb - 1));
+    uint32_t col = ct.y + __popc(ct.x & (cb - 1));
     bool store = ok;                                     // F counts every stored x coprime to K
     if (pl.compact && ok) {
         // the row's class keeps only x with gcd(N + x, d) = 1; class of the
         // first row of this 32-m word, plus the rows before m in the word
-        uint32_t cls = __ldg(&pl.cls_word[moff >> 5]) + __popc(rw & (rb - 1));
+        uint32_t cls = __ldg(&pl.cls_word[moff >> 5]) + __popc(rt.x & (rb - 1));
         while (cls >= pl.n_cls) cls -= pl.n_cls;
         const uint32_t ccw = __ldg(&pl.cmask[(size_t)cls * pl.S32 + (z >> 5)]);
         col = __ldg(&pl.cprefix[(size_t)cls * pl.S32 + (z >> 5)]) + __popc(ccw & (cb - 1));
         store = (ccw & cb) != 0;
     }
+    // 32-bit view of the row's words: column col is bit (col & 31) of word col >> 5
     if (store)
-        atomicAnd(reinterpret_cast<unsigned long long *>(pl.bits + (uint64_t)row * pl.wpr + (col >> 6)),
-                  ~(1ull << (col & 63)));
+        atomicAnd(reinterpret_cast<unsigned int *>(pl.bits) + (uint64_t)row * (2 * pl.wpr) + (col >> 5),
+                  ~(1u << (col & 31)));
     c.F += ok;
 }
 
-// One thread per work item, one G solve per hit (the walk of Section 3.2).
 template <class UT, class ST>
 __global__ void __launch_bounds__(LARGE_THREADS) k_large(const LargeArgs a) {
     const DevPlan &pl = a.pl;
@@ -149,16 +149,15 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_large(const LargeArgs a) {
         c.levels += it;
     }
 
-    c.F = warp_sum(c.F);
+    const unsigned long long F = warp_sum(c.F), hits = warp_sum(c.hits);
     c.solves = warp_sum(c.solves);
     c.levels = warp_sum(c.levels);
-    c.hits = warp_sum(c.hits);
     for (int o = 16; o; o >>= 1) c.err |= __shfl_xor_sync(0xffffffffu, c.err, o);
     if ((threadIdx.x & 31) == 0) {
-        if (c.F) atomicAdd(pl.stats + ST_F_LARGE, c.F);
+        if (F) atomicAdd(pl.stats + ST_F_LARGE, F);
         if (c.solves) atomicAdd(pl.stats + ST_SOLVES, c.solves);
         if (c.levels) atomicAdd(pl.stats + ST_LEVELS, c.levels);
-        if (c.hits) atomicAdd(pl.stats + ST_HITS_ALL, c.hits);
+        if (hits) atomicAdd(pl.stats + ST_HITS_ALL, hits);
         if (c.err) atomicOr(pl.stats + ST_ERROR, c.err);
     }
 }
@@ -181,7 +180,7 @@ constexpr int TG_STEPS = 4;
 constexpr int TG_WARPS = LARGE_THREADS / 32;
 
 template <class UT, class ST, class MT>
-__global__ void __launch_bounds__(LARGE_THREADS) k_large_tg(const LargeArgs a) {
+__global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? 4 : 1) k_large_tg(const LargeArgs a) {
     __shared__ TGItem<UT, ST, MT> queue[TG_WARPS][TG_QCAP];
     const DevPlan &pl = a.pl;
     const UT *Pp = reinterpret_cast<const UT *>(a.p);
@@ -308,16 +307,15 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_large_tg(const LargeArgs a) {
         }
     }
 
-    c.F = warp_sum(c.F);
+    const unsigned long long F = warp_sum(c.F), hits = warp_sum(c.hits);
     c.solves = warp_sum(c.solves);
     c.levels = warp_sum(c.levels);
-    c.hits = warp_sum(c.hits);
     for (int o = 16; o; o >>= 1) c.err |= __shfl_xor_sync(0xffffffffu, c.err, o);
     if (lane == 0) {
-        if (c.F) atomicAdd(pl.stats + ST_F_LARGE, c.F);
+        if (F) atomicAdd(pl.stats + ST_F_LARGE, F);
         if (c.solves) atomicAdd(pl.stats + ST_SOLVES, c.solves);
         if (c.levels) atomicAdd(pl.stats + ST_LEVELS, c.levels);
-        if (c.hits) atomicAdd(pl.stats + ST_HITS_ALL, c.hits);
+        if (hits) atomicAdd(pl.stats + ST_HITS_ALL, hits);
         if (c.err) atomicOr(pl.stats + ST_ERROR, c.err);
     }
 }

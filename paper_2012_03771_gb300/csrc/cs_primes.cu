@@ -151,6 +151,11 @@ __device__ __forceinline__ void emit(const GenArgs &a, uint64_t p, bool valid, u
     }
 }
 
+// n mod q with 32-bit arithmetic when n fits (all segments below 2^32)
+__device__ __forceinline__ uint32_t first_rem(uint64_t n, uint32_t q) {
+    return (n >> 32) == 0 ? (uint32_t)n % q : (uint32_t)(n % q);
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(GEN_THREADS) k_gen(const GenArgs a) {
     __shared__ uint32_t comp[SEG_WORDS];          // bit set = composite (or out of range)
@@ -192,7 +197,7 @@ __global__ void __launch_bounds__(GEN_THREADS) k_gen(const GenArgs a) {
             if (q >= WARP_COOP_Q) break;
             uint64_t start = (uint64_t)q * q;
             if (start < n_first) {
-                uint64_t rem = n_first % q;
+                const uint32_t rem = first_rem(n_first, q);
                 start = rem ? n_first + (q - rem) : n_first;
                 if ((start & 1) == 0) start += q;
             }
@@ -206,7 +211,7 @@ __global__ void __launch_bounds__(GEN_THREADS) k_gen(const GenArgs a) {
                 if ((uint64_t)q * q > n_last) break;
                 uint64_t start = (uint64_t)q * q;
                 if (start < n_first) {
-                    uint64_t rem = n_first % q;
+                    const uint32_t rem = first_rem(n_first, q);
                     start = rem ? n_first + (q - rem) : n_first;
                     if ((start & 1) == 0) start += q;
                 }
@@ -274,7 +279,7 @@ GenArgs make_args(uint64_t lo, uint64_t hi, const uint32_t *base, uint32_t n_bas
     // segment size: enough segments for every SM to get several, within
     // [SEG_MIN, SEG]
     const uint64_t odds = a.i_end > a.i_begin ? a.i_end - a.i_begin : 0;
-    uint64_t want = odds / ((uint64_t)sm_count() * 4);
+    uint64_t want = odds / ((uint64_t)sm_count() * 8);
     uint32_t seg = SEG_MIN;
     while (seg < SEG && seg < want) seg *= 2;
     a.seg = seg;

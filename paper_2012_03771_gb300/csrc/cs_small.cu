@@ -23,7 +23,6 @@ namespace {
 
 constexpr int TILE_THREADS = 1024;
 constexpr int SP_STAGE = 1024;      // small-prime records staged in shared memory at a time
-static_assert(SP_STAGE == TILE_THREADS, "each thread prefetches one record of the next stage");
 constexpr int TILE_WARPS = TILE_THREADS / 32;
 
 struct TileArgs {
@@ -114,21 +113,15 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile(const TileArgs a) {
         unsigned __int128 lowest = 0;
         if (pl.small_n) lowest = (unsigned __int128)(pl.M_start + moff) * pl.K64 - pl.SL;
         const uint32_t two_sl = 2 * pl.SL;
-        // double-buffered staging: the records of the next stage are loaded into
-        // registers while the current stage is processed; one barrier per stage
-        SmallPrime pre = threadIdx.x < n ? a.sp[threadIdx.x] : SmallPrime{0, 0, 0, 0};
-        uint32_t buf = 0;
-        for (uint64_t c0 = 0; c0 < n; c0 += SP_STAGE, buf ^= 1) {
+        for (uint64_t c0 = 0; c0 < n; c0 += SP_STAGE) {
             const uint32_t cn = (uint32_t)min((uint64_t)SP_STAGE, n - c0);
-            SmallPrime *cur = stage + buf * SP_STAGE;
-            if (threadIdx.x < cn) cur[threadIdx.x] = pre;
             __syncthreads();
-            const uint64_t nx = c0 + SP_STAGE + threadIdx.x;
-            if (nx < n) pre = a.sp[nx];
+            for (uint32_t k = threadIdx.x; k < cn; k += TILE_THREADS) stage[k] = a.sp[c0 + k];
+            __syncthreads();
             for (uint32_t base = warp * pp; base < cn; base += TILE_WARPS * pp) {
                 const uint32_t i = base + sub;
                 if (!row_ok || i >= cn) continue;
-                const SmallPrime e = cur[i];
+                const SmallPrime e = stage[i];
                 uint32_t v;
                 if (e.p == 2) {
                     v = (e.v0 + moff) & 1u;
@@ -195,14 +188,14 @@ cudaError_t launch_tile(const DevPlan &pl, const TileConfig &tc, const SmallPrim
     if (pl.M_c == 0 || pl.W == 0) return cudaSuccess;
     const uint64_t row_blocks = (pl.M_c + tc.rows - 1) / tc.rows;
     const uint64_t blocks = row_blocks * tc.n_chunks;
-    const size_t smem = (size_t)(tc.rows + 1) * tc.max_words * sizeof(uint32_t) + 2 * SP_STAGE * sizeof(SmallPrime);
+    const size_t smem = (size_t)(tc.rows + 1) * tc.max_words * sizeof(uint32_t) + SP_STAGE * sizeof(SmallPrime);
     TileArgs a{pl, tc, sp, n_sp, sp_cap};
     if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
     k_tile<<<(unsigned)blocks, TILE_THREADS, smem, stream>>>(a);
     return cudaGetLastError();
 }
 
-size_t tile_stage_bytes() { return 2 * SP_STAGE * sizeof(SmallPrime); }
+size_t tile_stage_bytes() { return SP_STAGE * sizeof(SmallPrime); }
 
 cudaError_t prepare_tile(int max_dynamic_smem) {
     // raise the kernel's dynamic shared-memory limit once, outside any launch

@@ -154,7 +154,9 @@ def _config(params, name="search_953"):
 def _shape(info, tuned):
     return {"M_c": int(info.M_c), "W": int(info.W), "bitset_bytes": int(info.bitset_bytes),
             "threshold": int(info.threshold), "large_mode": int(info.large_mode), "tile_rows": int(info.tile_rows),
-            "layout": "compact" if info.layout else "x coprime to K", "autotuned": tuned is not None}
+            "layout": "compact" if info.layout else "x coprime to K", "autotuned": tuned is not None,
+            "m_classes_walked": f"{int(info.m_walked)} of m mod {int(info.m_mod)}",
+            "chunks_class_walk": f"{int(info.split_chunks)} of {int(info.n_large_chunks)}"}
 
 
 def run_cuda(args, params):

@@ -84,7 +84,11 @@ typedef struct {
                                 N + x small enough to be a prime of d, phi(d) <= 4096 and an
                                 interval whose tile fits in one piece (SL up to about 3.7e5).
                                 F and the per-row counts are the same in both layouts. */
-    uint32_t reserved[6];
+    uint32_t m_classes;      /* three-gap walk over m: 0 = automatic (chunks whose primes have
+                                at least 12 expected hits walk only the m = 1, 5 (mod 6) when
+                                6 | d, the odd m when 2 | d, since the others are never rows);
+                                1 = every m; 2 = the classes in every chunk */
+    uint32_t reserved[5];
 } cs_tuning;
 
 typedef struct {
@@ -106,6 +110,9 @@ typedef struct {
                                   GB300), used to order instances in a batch */
     uint32_t layout;           /* 0 literal, 1 compact */
     uint32_t n_classes;        /* compact: residue classes of m mod d (phi(d)), else 1 */
+    uint32_t m_mod;            /* Q of the walk's m-classes (1: every m is walked) */
+    uint32_t m_walked;         /* classes of m mod Q walked (1 or 2) */
+    uint64_t split_chunks;     /* large-prime chunks that walk only those classes */
 } cs_info_t;
 
 typedef struct {
@@ -114,7 +121,8 @@ typedef struct {
     uint64_t F_large;
     uint64_t solves;           /* G solves of Eq. modeq in the large-prime walk */
     uint64_t levels;           /* passes through G's case analysis */
-    uint64_t hits_all;         /* large-prime hits before the coprime-m / stored-x filters */
+    uint64_t hits_all;         /* large-prime hits the walk visits, before the coprime-m and
+                                  stored-x tests (m outside the walked classes are not visited) */
     uint64_t n_small_primes;
     uint64_t n_large_primes;
     uint64_t survivors;        /* set bits in the bitset */
@@ -189,7 +197,7 @@ const char *cs_last_error(void);
  * appended to that text file and read back by later calls (one line per key).
  * *out receives a complete tuning (large_mode = 2).  Validation errors as for
  * cs_plan.  Tuning fields left at 0 in any plan may also be set from the
- * environment: CS_THRESHOLD, CS_TILE_ROWS, CS_LARGE_MODE, CS_LARGE_GRID. */
+ * environment: CS_THRESHOLD, CS_TILE_ROWS, CS_LARGE_MODE, CS_LARGE_GRID, CS_M_CLASSES. */
 cs_status cs_autotune(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL, uint64_t L,
                       const char *cache_path, cs_tuning *out);
 

@@ -49,7 +49,8 @@ class cs_tuning(ctypes.Structure):
     _fields_ = [("threshold", ctypes.c_uint64), ("tile_rows", ctypes.c_uint32),
                 ("large_mode", ctypes.c_uint32), ("no_wheel", ctypes.c_uint32),
                 ("large_grid", ctypes.c_uint32), ("chunk_numbers", ctypes.c_uint64),
-                ("profile", ctypes.c_uint32), ("layout", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 6)]
+                ("profile", ctypes.c_uint32), ("layout", ctypes.c_uint32), ("m_classes", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 5)]
 
 
 class cs_info_t(ctypes.Structure):
@@ -59,7 +60,8 @@ class cs_info_t(ctypes.Structure):
                 ("narrow", ctypes.c_uint32), ("wheel", ctypes.c_uint32),
                 ("n_large_chunks", ctypes.c_uint64), ("launches_per_sieve", ctypes.c_uint64),
                 ("h2d_bytes", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
-                ("est_cost", ctypes.c_uint64), ("layout", ctypes.c_uint32), ("n_classes", ctypes.c_uint32)]
+                ("est_cost", ctypes.c_uint64), ("layout", ctypes.c_uint32), ("n_classes", ctypes.c_uint32),
+                ("m_mod", ctypes.c_uint32), ("m_walked", ctypes.c_uint32), ("split_chunks", ctypes.c_uint64)]
 
 
 class cs_stats_t(ctypes.Structure):
@@ -150,9 +152,10 @@ def _stream_handle(stream) -> ctypes.c_void_p:
 
 
 def make_tuning(threshold=0, tile_rows=0, large_mode=0, no_wheel=False, large_grid=0,
-                chunk_numbers=0, profile=False, layout=0) -> cs_tuning:
+                chunk_numbers=0, profile=False, layout=0, m_classes=0) -> cs_tuning:
     t = cs_tuning()
     t.layout = layout
+    t.m_classes = m_classes
     t.threshold, t.tile_rows, t.large_mode = threshold, tile_rows, large_mode
     t.no_wheel, t.large_grid, t.chunk_numbers = int(no_wheel), large_grid, chunk_numbers
     t.profile = int(profile)

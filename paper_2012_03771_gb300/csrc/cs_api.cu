@@ -98,6 +98,8 @@ struct cs_plan_s {
     std::vector<int64_t> x_of_col;
     std::vector<std::pair<uint64_t, uint64_t>> chunks;    // large-prime ranges (lo, hi]
     std::vector<uint32_t> chunk_seg;                      // m-segments per prime, per chunk
+    std::vector<uint8_t> chunk_split;                     // walk only the m-classes, per chunk
+    MClasses mcls{1, 1, {0, 0}};                          // m-classes of the walk
     uint64_t large_cap = 0, small_cap = 0, est_cost = 0;
     int large_grid = 0;
     uint64_t h2d = 0, dev_bytes = 0;
@@ -224,6 +226,7 @@ void env_tuning(cs_tuning &t) {
     if (!t.tile_rows) t.tile_rows = (uint32_t)get("CS_TILE_ROWS");
     if (!t.large_mode) t.large_mode = (uint32_t)get("CS_LARGE_MODE");
     if (!t.large_grid) t.large_grid = (uint32_t)get("CS_LARGE_GRID");
+    if (!t.m_classes) t.m_classes = (uint32_t)get("CS_M_CLASSES");
 }
 
 cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc,
@@ -408,9 +411,27 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
     // chunk_numbers wide; a chunk's primes are split into n_seg m-segments of
     // about HITS_PER_ITEM expected hits each
     const uint64_t chunk = pl->tune.chunk_numbers ? pl->tune.chunk_numbers : (1ull << 27);
-    const double HITS_PER_ITEM = 128.0;
+    // m-classes: rows need gcd(m, d) = 1, so with Q = 6 (or 2) dividing d the
+    // walk can skip the m = 0, 2, 3, 4 (mod 6) (or the even m).  Each walked
+    // class costs one more window in the item's fused solve, so a chunk walks
+    // the classes only when its primes have enough hits to repay it.
+    if (pl->tune.m_classes > 2) return fail(CS_EINVAL, "m_classes must be 0, 1 or 2");
+    if (pl->mode == LARGE_THREE_GAP && SL > 0 && pl->tune.m_classes != 1) {
+        const uint32_t Q = d % 6 == 0 ? 6 : (d % 2 == 0 ? 2 : 1);
+        const uint32_t ms = (uint32_t)(M_start % Q);
+        if (Q == 6) pl->mcls = MClasses{6, 2, {(1 + 6 - ms) % 6, (5 + 6 - ms) % 6}};
+        if (Q == 2) pl->mcls = MClasses{2, 1, {(1 + 2 - ms) % 2, 0}};
+    }
+    const double SPLIT_MIN_HITS = 12.0;   // expected hits per prime (all m) at the chunk's low end
+    const double HITS_PER_ITEM = 128.0;   // walked hits per work item
+    auto split_for = [&](uint64_t lo) -> bool {
+        if (pl->mcls.Q == 1) return false;
+        if (pl->tune.m_classes == 2) return true;
+        return (double)M_inc * (double)S / (double)std::max<uint64_t>(lo, 1) >= SPLIT_MIN_HITS;
+    };
     auto segs_for = [&](uint64_t lo) {
         double hits = (double)M_inc * (double)S / (double)std::max<uint64_t>(lo, 1);
+        if (split_for(lo)) hits *= (double)pl->mcls.n / (double)pl->mcls.Q;
         double seg = std::min<double>(std::max(1.0, std::ceil(hits / HITS_PER_ITEM)), (double)std::max<uint64_t>(M_inc, 1));
         return (uint32_t)std::min(seg, 65536.0);
     };
@@ -428,6 +449,7 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
             const uint64_t lo = std::max(ch.lo, T), hi = std::min(ch.hi, L);
             pl->chunks.push_back({lo, hi});
             pl->chunk_seg.push_back(segs_for(lo));
+            pl->chunk_split.push_back(split_for(lo));
             pl->cache_idx.push_back(k);
         }
         pl->large_cap = 0;
@@ -436,6 +458,7 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
             uint64_t hi = std::min<uint64_t>({L, lo + std::max<uint64_t>(lo, 1), lo + chunk});
             pl->chunks.push_back({lo, hi});
             pl->chunk_seg.push_back(segs_for(lo));
+            pl->chunk_split.push_back(split_for(lo));
             widest = std::max(widest, hi - lo);
             lo = hi;
         }
@@ -725,7 +748,8 @@ cs_status cs_sieve(cs_plan_t pl, void *stream) {
             CS_CUDA(cudaStreamWaitEvent(st, ch.ready, 0));
             if ((s = prof.begin(KC_LARGE))) return s;
             CS_CUDA(launch_large(dp, ch.narrow, pl->mode, ch.p, ch.r, nullptr, ch.count, ch.cap,
-                                 pl->chunk_seg[c], pl->large_grid, st, pl->T, pl->L));
+                                 pl->chunk_seg[c], pl->large_grid, st, pl->T, pl->L,
+                                 pl->chunk_split[c] ? pl->mcls : MClasses{1, 1, {0, 0}}));
             if ((s = prof.end())) return s;
         }
     }
@@ -738,7 +762,8 @@ cs_status cs_sieve(cs_plan_t pl, void *stream) {
         if ((s = prof.end())) return s;
         if ((s = prof.begin(KC_LARGE))) return s;
         CS_CUDA(launch_large(dp, pl->narrow, pl->mode, pl->d_lp, pl->d_lr, pl->d_lv, cnt,
-                             pl->large_cap, pl->chunk_seg[c], pl->large_grid, st));
+                             pl->large_cap, pl->chunk_seg[c], pl->large_grid, st, 0, ~0ull,
+                             pl->chunk_split[c] ? pl->mcls : MClasses{1, 1, {0, 0}}));
         if ((s = prof.end())) return s;
     }
     if ((s = prof.begin(KC_FINAL))) return s;
@@ -793,6 +818,10 @@ cs_status cs_info(cs_plan_t pl, cs_info_t *out) {
     out->est_cost = pl->est_cost;
     out->layout = pl->layout;
     out->n_classes = pl->n_cls;
+    out->m_mod = pl->mcls.Q;
+    out->m_walked = pl->mcls.n;
+    out->split_chunks = 0;
+    for (uint8_t f : pl->chunk_split) out->split_chunks += f;
     if (pl->layout == 1) out->W = pl->Wc_max;
     return CS_OK;
 }

@@ -120,6 +120,33 @@ CS_HD uint64_t udiv(uint64_t a, uint64_t b) {
     return a / b;
 }
 
+// Quotients by one divisor d, taken several times (T. Granlund and P. L.
+// Montgomery, "Division by invariant integers using multiplication", PLDI
+// 1994): with v = floor((2^32 - 1) / d), a*v / 2^32 lies in (a/d - 1, a/d], so
+// q = floor(a*v / 2^32) is floor(a/d) or one less, and one comparison of the
+// remainder settles it.  One division per divisor instead of one per quotient.
+template <class UT>
+struct Divisor;
+template <>
+struct Divisor<uint32_t> {
+    uint32_t d, v;
+    CS_HD explicit Divisor(uint32_t d_) : d(d_), v(0xffffffffu / d_) {}
+    CS_HD uint32_t div(uint32_t a) const {
+#if defined(__CUDA_ARCH__)
+        uint32_t q = __umulhi(a, v);
+#else
+        uint32_t q = (uint32_t)(((uint64_t)a * v) >> 32);
+#endif
+        return q + (a - q * d >= d);
+    }
+};
+template <>
+struct Divisor<uint64_t> {
+    uint64_t d;
+    CS_HD explicit Divisor(uint64_t d_) : d(d_) {}
+    CS_HD uint64_t div(uint64_t a) const { return udiv(a, d); }
+};
+
 // ----------------------------------------------------------- G(p, K, L, R)
 //
 // Smallest m >= 0 with L <= m*K mod p <= L + w (Eq. modfunc), for 0 < K < p,
@@ -211,12 +238,13 @@ CS_HD bool g_solve_multi(UT p, UT K, const UT (&L0)[NW], const UT (&w)[NW], UT (
     ST U = 0, u = 1, s = 1;
     for (uint32_t it = 0; it < max_iter && n_open; it++) {
         iters++;
+        const Divisor<UT> byK(K);                                // every quotient of this pass is by K
         UT c[NW];
 #pragma unroll
         for (int i = 0; i < NW; i++) {
             c[i] = 0;
             if (!open[i]) continue;
-            c[i] = udiv((UT)(L[i] + K - 1), K);                 // ceil(L/K)
+            c[i] = byK.div((UT)(L[i] + K - 1));                 // ceil(L/K)
             const UT ck = c[i] * K;
             if (ck <= L[i] + w[i]) {                             // case C
                 y_out[i] = (UT)(A[i] + s * (ST)ck);
@@ -239,7 +267,7 @@ CS_HD bool g_solve_multi(UT p, UT K, const UT (&L0)[NW], const UT (&w)[NW], UT (
             K = p - K;
             continue;
         }
-        const UT q = udiv((UT)(p + K - 1), K);                   // case E: ceil(p/K)
+        const UT q = byK.div((UT)(p + K - 1));                   // case E: ceil(p/K)
 #pragma unroll
         for (int i = 0; i < NW; i++) {
             if (!open[i]) continue;

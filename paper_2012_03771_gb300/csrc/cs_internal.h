@@ -121,6 +121,13 @@ cudaError_t prepare_tile(int max_dynamic_smem);
 size_t tile_stage_bytes();
 
 enum LargeMode { LARGE_PAPER = 1, LARGE_THREE_GAP = 2 };
+// m-classes of the three-gap walk: only m = c (mod Q) for the n classes c with
+// gcd(c, Q) = 1 are walked (Q | d, so the others are never rows).  off[k] is
+// class k's residue of m - M_start mod Q.  Q = 1, n = 1: every m.
+struct MClasses {
+    uint32_t Q, n;
+    uint32_t off[2];
+};
 // n_seg: the m-range of every prime is split into n_seg segments walked by
 // separate threads (each starts with its own solve), to balance primes with
 // many hits against primes with few.
@@ -130,7 +137,7 @@ enum LargeMode { LARGE_PAPER = 1, LARGE_THREE_GAP = 2 };
 cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p, const void *r,
                          const void *v, const unsigned long long *count, uint64_t cap,
                          uint32_t n_seg, int grid, cudaStream_t stream, uint64_t p_lo = 0,
-                         uint64_t p_hi = ~0ull);
+                         uint64_t p_hi = ~0ull, MClasses mc = MClasses{1, 1, {0, 0}});
 cudaError_t launch_final(const DevPlan &pl, cudaStream_t stream);
 
 // batch of G solves (tests of the solver)

@@ -17,7 +17,7 @@
 //                    by one more solve, every further hit costs O(1).
 //
 // Each hit on a coprime m and a stored x clears one bit of the device bitset
-// with a 64-bit atomic AND and counts one enumerated factor.
+// with a 32-bit atomic AND and counts one enumerated factor.
 #include "cs_arith.cuh"
 #include "cs_internal.h"
 
@@ -34,6 +34,7 @@ struct LargeArgs {
     uint64_t cap;
     uint32_t n_seg;      // m-segments per prime (work items = primes x n_seg)
     uint64_t p_lo, p_hi; // walk only p_lo < p <= p_hi (v == NULL: shared cache chunk)
+    MClasses mc;         // three-gap walk: m-classes walked (Q = 1: every m)
 };
 
 // v0 = (r * M_start + SL) mod p, for primes from a shared residue cache
@@ -163,25 +164,44 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_large(const LargeArgs a) {
 }
 
 // Three-gap walk with persistent lanes.  A warp prepares 32 work items at a
-// time (one fused solve each: the two steps and the first hit of the item's
-// m-segment) into a queue in shared memory; every lane then steps its own item
-// and, when the item's segment is exhausted, takes the next prepared item from
-// the queue, so that lanes stay busy although items have different numbers of
-// hits.  The queue is refilled whenever it holds at most 32 items.
+// time (one fused solve each: the two steps and the first hits of the item's
+// m-segment) into a queue in shared memory; every lane then steps its own
+// walker and, when its segment is exhausted, takes the next prepared walker
+// from the queue, so that lanes stay busy although walkers have different
+// numbers of hits.
+//
+// m-classes: rows are the m coprime to d, so when Q | d (Q = 6 or 2) the m that
+// share a factor with Q can never be rows.  An item then walks only the NC
+// classes m = c (mod Q) with gcd(c, Q) = 1, each as its own walker over
+// j in m = m_c + Q j: v steps by r' = Q r mod p per unit of j, the two step
+// windows are solved for r' (steps of Q j' in m), and each class needs its own
+// first hit.  All windows share (p, r'), so one fused solve serves them
+// (Q = 6: 2 + 2 windows), and the walk visits a third of the hits (Q = 6) or
+// half of them (Q = 2).
 template <class UT, class ST, class MT>
 struct TGItem {
     MT moff, end;      // current m - M_start, end of the segment
     UT v, p, da, ub;   // v = (r m + SL) mod p, steps of v
-    MT ma, mb;         // steps of m (clamped to M_inc + 1)
+    MT ma, mb;         // steps of m (clamped to M_inc)
 };
 
-constexpr int TG_QCAP = 64;
 constexpr int TG_STEPS = 4;
 constexpr int TG_WARPS = LARGE_THREADS / 32;
 
-template <class UT, class ST, class MT>
+// v + k r mod p for a small k (v, r < p, 2p fits in UT)
+template <class UT>
+__device__ __forceinline__ UT add_times(UT v, UT r, uint32_t k, UT p) {
+    for (; k; k--) {
+        v += r;
+        if (v >= p) v -= p;
+    }
+    return v;
+}
+
+template <class UT, class ST, class MT, int NC>
 __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? 4 : 1) k_large_tg(const LargeArgs a) {
-    __shared__ TGItem<UT, ST, MT> queue[TG_WARPS][TG_QCAP];
+    constexpr int QCAP = 32 * (NC + 1);   // a refill adds at most 32 NC walkers
+    __shared__ TGItem<UT, ST, MT> queue[TG_WARPS][QCAP];
     const DevPlan &pl = a.pl;
     const UT *Pp = reinterpret_cast<const UT *>(a.p);
     const UT *Rp = reinterpret_cast<const UT *>(a.r);
@@ -189,13 +209,17 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? 4 : 1) k_larg
     const uint64_t n = min((uint64_t)*a.count, a.cap);
     const UT w = (UT)(2 * pl.SL);
     const uint64_t M = pl.M_inc;
+    const uint32_t Q = a.mc.Q;
     const uint32_t max_iter = 4 * 8 * sizeof(UT) + 8;
     const uint32_t n_seg = a.n_seg;
     const unsigned lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1;
     const uint64_t n_items = n * n_seg;
     const uint64_t warp_id = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    const MT cap_step = (MT)(M + 1);
+    // any step >= M ends a walker (its segment is at most M long); two clamped
+    // steps still add up below 2^32
+    const uint64_t cap_step = M;
     TGItem<UT, ST, MT> *q = queue[wib];
     Counters c;
     if (M == 0) return;
@@ -207,84 +231,129 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? 4 : 1) k_larg
     UT v = 0, p = 1, da = 0, ub = 0;
 
     while (true) {
-        // refill: prepare 32 items when the queue can take them
-        if (qcount <= TG_QCAP - 32 && batch * 32 < n_items) {
+        // refill: prepare 32 items when the queue can take their walkers
+        if (qcount + 32 * NC <= QCAP && batch * 32 < n_items) {
             const uint64_t item = batch * 32 + lane;
             batch += n_warps;
-            bool push = false;
+            bool push[NC];
+            MT first_m[NC];
+            UT first_v[NC];
             TGItem<UT, ST, MT> e;
+#pragma unroll
+            for (int k = 0; k < NC; k++) push[k] = false;
             if (item < n_items) {
-                const uint64_t i = item / n_seg;
-                const uint32_t sg = (uint32_t)(item - i * n_seg);
-                const uint64_t m_lo = M * sg / n_seg, m_hi = M * (sg + 1) / n_seg;
+                uint64_t i = item, m_lo = 0, m_hi = M;
+                if (n_seg > 1) {
+                    i = item / n_seg;
+                    const uint32_t sg = (uint32_t)(item - i * n_seg);
+                    m_lo = M * sg / n_seg;
+                    m_hi = M * (sg + 1) / n_seg;
+                }
                 const UT pp = Pp[i], r = Rp[i];
                 bool ok = m_lo < m_hi && (uint64_t)pp > a.p_lo && (uint64_t)pp <= a.p_hi;
                 UT vv = ok ? (Vp ? Vp[i] : start_v(r, pl.M_start, pl.SL, pp)) : (UT)0;
                 if (ok && m_lo) vv = advance(vv, r, m_lo, pp);
                 uint32_t it = 0;
-                UT ma_, da_, mb_ = 0, ub_ = 0;
-                uint64_t first = 0;
+                UT ma_ = 0, da_ = 0, mb_ = 0, ub_ = 0;
+                uint64_t first[NC];
+                UT vk[NC];
+                uint32_t dk[NC];
+#pragma unroll
+                for (int k = 0; k < NC; k++) {
+                    first[k] = 0;
+                    vk[k] = vv;
+                    dk[k] = 0;
+                }
                 if (ok && w == 0) {
+                    // SL = 0 (Q = 1, NC = 1): every p-th m; v stays 0
                     ma_ = pp;
-                    da_ = 0;
                     if (vv > w) {
                         UT t, y;
                         c.solves++;
                         ok = g_solve<UT, ST>(pp, r, (UT)(pp - vv), w, t, y, it, max_iter);
                         if (!ok) c.err |= ERR_SOLVER_LIMIT;
-                        first = t;
-                        vv = (UT)(vv + y - pp);
+                        first[0] = t;
+                        vk[0] = (UT)(vv + y - pp);
                     }
                 } else if (ok) {
-                    const bool need_first = vv > w;
-                    const UT L3[3] = {(UT)(pp - w), (UT)1, need_first ? (UT)(pp - vv) : (UT)0};
-                    const UT W3[3] = {(UT)(w - 1), (UT)(w - 1), w};
-                    UT m3[3], y3[3];
-                    c.solves += 2 + need_first;
-                    ok = g_solve_multi<UT, ST, 3>(pp, r, L3, W3, m3, y3, it, max_iter);
+                    // class k starts at the first m_lo + dk with m = c_k (mod Q)
+                    const uint32_t lo_res = (uint32_t)m_lo % Q;      // m_lo < M_inc < 2^31
+                    UT rq = add_times(r, r, Q - 1, pp);        // r' = Q r mod p
+                    UT Lw[2 + NC], Ww[2 + NC], mw[2 + NC], yw[2 + NC];
+                    Lw[0] = (UT)(pp - w); Ww[0] = (UT)(w - 1);   // r' j mod p in [p - 2SL, p - 1]
+                    Lw[1] = (UT)1;        Ww[1] = (UT)(w - 1);   // r' j mod p in [1, 2SL]
+                    uint32_t n_first = 0;
+#pragma unroll
+                    for (int k = 0; k < NC; k++) {
+                        uint32_t dd = a.mc.off[k] + Q - lo_res;
+                        if (dd >= Q) dd -= Q;
+                        dk[k] = dd;
+                        vk[k] = add_times(vv, r, dd, pp);
+                        const bool need = vk[k] > w;
+                        n_first += need;
+                        Lw[2 + k] = need ? (UT)(pp - vk[k]) : (UT)0;   // L = 0: m = 0 (case a)
+                        Ww[2 + k] = w;
+                    }
+                    c.solves += 2 + n_first;
+                    ok = g_solve_multi<UT, ST, 2 + NC>(pp, rq, Lw, Ww, mw, yw, it, max_iter);
                     if (!ok) c.err |= ERR_SOLVER_LIMIT;
-                    ma_ = m3[0];
-                    da_ = pp - y3[0];
-                    mb_ = m3[1];
-                    ub_ = y3[1];
-                    if (need_first) {
-                        first = m3[2];
-                        vv = (UT)(vv + y3[2] - pp);
+                    ma_ = mw[0];
+                    da_ = pp - yw[0];
+                    mb_ = mw[1];
+                    ub_ = yw[1];
+#pragma unroll
+                    for (int k = 0; k < NC; k++) {
+                        if (vk[k] > w) {
+                            first[k] = (uint64_t)mw[2 + k] * Q;
+                            vk[k] = (UT)(vk[k] + yw[2 + k] - pp);
+                        }
                     }
                 }
                 c.levels += it;
-                if (ok && first < m_hi - m_lo) {
-                    push = true;
-                    e.moff = (MT)(m_lo + first);
+                if (ok) {
+#pragma unroll
+                    for (int k = 0; k < NC; k++) {
+                        const uint64_t mf = m_lo + dk[k] + first[k];
+                        push[k] = mf < m_hi;
+                        first_m[k] = (MT)mf;
+                        first_v[k] = vk[k];
+                    }
+                    const uint64_t sa = (uint64_t)ma_ * Q, sb = (uint64_t)mb_ * Q;
                     e.end = (MT)m_hi;
-                    e.v = vv;
                     e.p = pp;
                     e.da = da_;
                     e.ub = ub_;
-                    e.ma = (uint64_t)ma_ < (uint64_t)cap_step ? (MT)ma_ : cap_step;
-                    e.mb = (uint64_t)mb_ < (uint64_t)cap_step ? (MT)mb_ : cap_step;
+                    e.ma = (MT)(sa < cap_step ? sa : cap_step);
+                    e.mb = (MT)(sb < cap_step ? sb : cap_step);
                 }
             }
-            const unsigned pm = __ballot_sync(0xffffffffu, push);
-            if (push) {
-                const uint32_t slot = (qhead + qcount + __popc(pm & ((1u << lane) - 1))) % TG_QCAP;
-                q[slot] = e;
+            uint32_t tail = qhead + qcount;
+#pragma unroll
+            for (int k = 0; k < NC; k++) {
+                const unsigned pm = __ballot_sync(0xffffffffu, push[k]);
+                if (push[k]) {
+                    TGItem<UT, ST, MT> ek = e;
+                    ek.moff = first_m[k];
+                    ek.v = first_v[k];
+                    q[(tail + __popc(pm & lt_mask)) % QCAP] = ek;
+                }
+                tail += __popc(pm);
             }
-            qcount += __popc(pm);
+            qcount = tail - qhead;
             __syncwarp();
         }
         // hand queued items to idle lanes
         const unsigned idle = __ballot_sync(0xffffffffu, !active);
         if (idle && qcount) {
-            const uint32_t rank = __popc(idle & ((1u << lane) - 1));
+            const uint32_t rank = __popc(idle & lt_mask);
             const uint32_t take = min((uint32_t)__popc(idle), qcount);
             if (!active && rank < take) {
-                const TGItem<UT, ST, MT> e = q[(qhead + rank) % TG_QCAP];
+                const TGItem<UT, ST, MT> e = q[(qhead + rank) % QCAP];
                 moff = e.moff; end = e.end; v = e.v; p = e.p; da = e.da; ub = e.ub;
                 ma = e.ma; mb = e.mb;
                 active = true;
             }
-            qhead = (qhead + take) % TG_QCAP;
+            qhead = (qhead + take) % QCAP;
             qcount -= take;
             __syncwarp();
         }
@@ -339,19 +408,25 @@ __global__ void k_modsolve(const uint64_t *p, const uint64_t *K, const uint64_t 
 
 cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p, const void *r,
                          const void *v, const unsigned long long *count, uint64_t cap, uint32_t n_seg,
-                         int grid, cudaStream_t stream, uint64_t p_lo, uint64_t p_hi) {
-    LargeArgs a{pl, p, r, v, count, cap, n_seg ? n_seg : 1, p_lo, p_hi};
+                         int grid, cudaStream_t stream, uint64_t p_lo, uint64_t p_hi, MClasses mc) {
+    if (mc.Q == 0 || mc.n < 1 || mc.n > 2 || mc.n > mc.Q || pl.SL == 0) mc = MClasses{1, 1, {0, 0}};
+    LargeArgs a{pl, p, r, v, count, cap, n_seg ? n_seg : 1, p_lo, p_hi, mc};
     if (grid <= 0) grid = sm_count() * 8;
+    // m - M_start < M_inc < 2^31: 32-bit m offsets in both widths
     if (narrow) {
         if (mode == LARGE_PAPER)
             k_large<uint32_t, int32_t><<<grid, LARGE_THREADS, 0, stream>>>(a);
+        else if (mc.n == 2)
+            k_large_tg<uint32_t, int32_t, uint32_t, 2><<<grid, LARGE_THREADS, 0, stream>>>(a);
         else
-            k_large_tg<uint32_t, int32_t, uint32_t><<<grid, LARGE_THREADS, 0, stream>>>(a);
+            k_large_tg<uint32_t, int32_t, uint32_t, 1><<<grid, LARGE_THREADS, 0, stream>>>(a);
     } else {
         if (mode == LARGE_PAPER)
             k_large<uint64_t, int64_t><<<grid, LARGE_THREADS, 0, stream>>>(a);
+        else if (mc.n == 2)
+            k_large_tg<uint64_t, int64_t, uint32_t, 2><<<grid, LARGE_THREADS, 0, stream>>>(a);
         else
-            k_large_tg<uint64_t, int64_t, uint64_t><<<grid, LARGE_THREADS, 0, stream>>>(a);
+            k_large_tg<uint64_t, int64_t, uint32_t, 1><<<grid, LARGE_THREADS, 0, stream>>>(a);
     }
     return cudaGetLastError();
 }

@@ -1,12 +1,20 @@
 // Host build of the kernels' integer arithmetic (cs_arith.cuh) for CPU tests:
-// reads "p K L R" lines, prints "m y" from g_solve (32- or 64-bit) and from
-// g_solve_multi with the window placed in each of three slots.
+// reads "p K L R" lines, prints "m y" from g_solve (32- or 64-bit), from
+// g_solve_multi with the window in one of three slots and, 32-bit, in the last
+// of four slots.  Mode "q" reads "a d" lines and prints the 32-bit quotient of
+// the solver's shared-reciprocal division.
 #include <cstdio>
 #include <cstdint>
 #include "../../paper_2012_03771_gb300/csrc/cs_arith.cuh"
 
 int main(int argc, char **argv) {
     const bool narrow = argc > 1 && argv[1][0] == 'n';
+    if (argc > 1 && argv[1][0] == 'q') {
+        unsigned long long a, d;
+        while (scanf("%llu %llu", &a, &d) == 2)
+            printf("%u\n", cs::Divisor<uint32_t>((uint32_t)d).div((uint32_t)a));
+        return 0;
+    }
     unsigned long long p, K, L, R;
     while (scanf("%llu %llu %llu %llu", &p, &K, &L, &R) == 4) {
         uint32_t it = 0;
@@ -18,7 +26,11 @@ int main(int argc, char **argv) {
             const uint32_t Ws[3] = {(uint32_t)(R - L), 0, 0};
             uint32_t ms[3], ys[3];
             bool ok2 = cs::g_solve_multi<uint32_t, int32_t, 3>((uint32_t)p, (uint32_t)(K % p), Ls, Ws, ms, ys, it, 200);
-            printf("%d %u %u %d %u %u\n", ok, m, y, ok2, ms[0], ys[0]);
+            const uint32_t L4[4] = {(uint32_t)(p - 1), 1, 0, (uint32_t)L};
+            const uint32_t W4[4] = {0, 0, 0, (uint32_t)(R - L)};
+            uint32_t m4[4], y4[4];
+            bool ok4 = cs::g_solve_multi<uint32_t, int32_t, 4>((uint32_t)p, (uint32_t)(K % p), L4, W4, m4, y4, it, 200);
+            printf("%d %u %u %d %u %u %d %u %u\n", ok, m, y, ok2, ms[0], ys[0], ok4, m4[3], y4[3]);
         } else {
             uint64_t m = 0, y = 0;
             bool ok = cs::g_solve<uint64_t, int64_t>(p, K % p, L, R - L, m, y, it, 300);

@@ -35,8 +35,32 @@ def test_g_solve_and_multi_match_paper_recursion(exe, narrow):
     out = subprocess.run([exe, "n" if narrow else "w"], input=inp, capture_output=True, text=True,
                          check=True).stdout.split("\n")
     for (p, K, L, R), line in zip(cases, out):
-        ok, m, y, ok2, m2, y2 = (int(v) for v in line.split())
+        vals = [int(v) for v in line.split()]
+        ok, m, y, ok2, m2, y2 = vals[:6]
         g = O.G(p, K, L, R)
         assert ok and ok2
         assert (m, y) == (g, g * K % p), (p, K, L, R)
         assert (m2, y2) == (g, g * K % p), (p, K, L, R)
+        if narrow:
+            ok4, m4, y4 = vals[6:]
+            assert ok4 and (m4, y4) == (g, g * K % p), (p, K, L, R)
+
+
+def test_shared_reciprocal_quotients(exe):
+    """floor(a / d) through one precomputed reciprocal of d, for every size of
+    a and d that the 32-bit solver meets (a < 2^31 + 2^30, d < 2^30), with the
+    edges where the estimate is one short: a = k d - 1, k d, k d + d - 1."""
+    rng = random.Random(11)
+    cases = []
+    for _ in range(20000):
+        d = rng.choice([1, 2, 3, 7, rng.randrange(1, 1 << 16), rng.randrange(1, 1 << 30), (1 << 30) - 35])
+        k = rng.randrange(0, (3 << 30) // d + 1)
+        for a in (k * d - 1, k * d, k * d + d - 1, rng.randrange(0, 3 << 30)):
+            if 0 <= a < (3 << 30):
+                cases.append((a, d))
+    cases += [(0xffffffff, 1), (0xffffffff, 0xffffffff), (0xfffffffe, 0xffffffff), (0x80000000, 3)]
+    inp = "".join(f"{a} {d}\n" for a, d in cases)
+    out = subprocess.run([exe, "q"], input=inp, capture_output=True, text=True, check=True).stdout.split()
+    assert len(out) == len(cases)
+    for (a, d), q in zip(cases, out):
+        assert int(q) == a // d, (a, d)

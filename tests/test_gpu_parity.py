@@ -123,6 +123,29 @@ def test_tiny_cases_bit_exact(mode):
     assert n > 80
 
 
+@pytest.mark.parametrize("m_classes", [1, 2])
+def test_m_class_walk_bit_exact(m_classes):
+    """The three-gap walk over every m (1) and over the m-classes coprime to
+    Q = 6 or 2 in every chunk (2) give the oracle's bitset; d = 6, 70 (Q = 2),
+    2310, and odd d (Q = 1), with M_start in every residue class mod 6."""
+    n = 0
+    for prm in workloads.tiny_cases(150, seed=12):
+        args = prm.as_tuple()
+        if O.validate(*args):
+            continue
+        got = _run(args, large_mode=2, threshold=max(2 * prm.SL, 1), m_classes=m_classes)
+        _check_full(args, got)
+        n += 1
+    assert n > 80
+    for d in (6, 70, 2310, 15):
+        for M_start in range(1000, 1006):
+            args = (101, d, M_start, 200, 500, 10**6)
+            got = _run(args, large_mode=2, threshold=1000, m_classes=m_classes)
+            info = got["info"]
+            assert info.m_mod == ((6 if d % 6 == 0 else 2 if d % 2 == 0 else 1) if m_classes == 2 else 1)
+            _check_full(args, got)
+
+
 def test_k1_survivors_are_primes():
     """K = d = 1 and L >= sqrt(N + SL): survivors are the primes (Section 1 gaps)."""
     SL = 199_999
@@ -194,6 +217,15 @@ def test_search_953_sampled_rows_and_invariants():
     expect = prm.M_inc * (2 * prm.SL + 1) * inv + n_large
     assert abs(st["solves"] - expect) < 0.01 * expect
     assert st["n_large_primes"] == n_large
+    # hits the three-gap walk visits: M S sum 1/p over (T, L] for every m, a third
+    # of that when only m = 1, 5 (mod 6) are walked (6 | d)
+    T = got["info"].threshold
+    _, _, inv = O.prime_stats(T, prm.L)
+    all_hits = prm.M_inc * (2 * prm.SL + 1) * inv
+    for m_classes, frac in ((1, 1.0), (2, 1.0 / 3.0)):
+        alt = _run(prm.as_tuple(), threshold=T, tile_rows=got["info"].tile_rows, m_classes=m_classes)
+        assert alt["hash"] == got["hash"] and alt["F"] == got["F"]
+        assert abs(alt["stats"]["hits_all"] - frac * all_hits) < 0.005 * frac * all_hits
 
 
 def test_autotune_picks_a_valid_tuning_and_caches_it(tmp_path):

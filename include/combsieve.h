@@ -85,10 +85,14 @@ typedef struct {
                                 interval whose tile fits in one piece (SL up to about 3.7e5).
                                 F and the per-row counts are the same in both layouts. */
     uint32_t m_classes;      /* three-gap walk over m: 0 = automatic (chunks whose primes have
-                                at least 12 expected hits walk only the m = 1, 5 (mod 6) when
+                                at least 24 expected hits walk only the m = 1, 5 (mod 6) when
                                 6 | d, the odd m when 2 | d, since the others are never rows);
                                 1 = every m; 2 = the classes in every chunk */
-    uint32_t reserved[5];
+    uint32_t item_hits;      /* three-gap walk: expected walked hits per work item (prime,
+                                m-segment); 0 = automatic (128) */
+    uint32_t class_min_hits; /* m_classes = 0: expected hits per prime (every m) from which a
+                                chunk walks only the m-classes; 0 = automatic (24) */
+    uint32_t reserved[3];
 } cs_tuning;
 
 typedef struct {
@@ -197,7 +201,8 @@ const char *cs_last_error(void);
  * appended to that text file and read back by later calls (one line per key).
  * *out receives a complete tuning (large_mode = 2).  Validation errors as for
  * cs_plan.  Tuning fields left at 0 in any plan may also be set from the
- * environment: CS_THRESHOLD, CS_TILE_ROWS, CS_LARGE_MODE, CS_LARGE_GRID, CS_M_CLASSES. */
+ * environment: CS_THRESHOLD, CS_TILE_ROWS, CS_LARGE_MODE, CS_LARGE_GRID, CS_M_CLASSES,
+ * CS_ITEM_HITS, CS_CLASS_MIN_HITS. */
 cs_status cs_autotune(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL, uint64_t L,
                       const char *cache_path, cs_tuning *out);
 

@@ -50,7 +50,8 @@ class cs_tuning(ctypes.Structure):
                 ("large_mode", ctypes.c_uint32), ("no_wheel", ctypes.c_uint32),
                 ("large_grid", ctypes.c_uint32), ("chunk_numbers", ctypes.c_uint64),
                 ("profile", ctypes.c_uint32), ("layout", ctypes.c_uint32), ("m_classes", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 5)]
+                ("item_hits", ctypes.c_uint32), ("class_min_hits", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 3)]
 
 
 class cs_info_t(ctypes.Structure):
@@ -152,10 +153,11 @@ def _stream_handle(stream) -> ctypes.c_void_p:
 
 
 def make_tuning(threshold=0, tile_rows=0, large_mode=0, no_wheel=False, large_grid=0,
-                chunk_numbers=0, profile=False, layout=0, m_classes=0) -> cs_tuning:
+                chunk_numbers=0, profile=False, layout=0, m_classes=0, item_hits=0,
+                class_min_hits=0) -> cs_tuning:
     t = cs_tuning()
     t.layout = layout
-    t.m_classes = m_classes
+    t.m_classes, t.item_hits, t.class_min_hits = m_classes, item_hits, class_min_hits
     t.threshold, t.tile_rows, t.large_mode = threshold, tile_rows, large_mode
     t.no_wheel, t.large_grid, t.chunk_numbers = int(no_wheel), large_grid, chunk_numbers
     t.profile = int(profile)

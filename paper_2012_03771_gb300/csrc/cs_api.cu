@@ -227,6 +227,8 @@ void env_tuning(cs_tuning &t) {
     if (!t.large_mode) t.large_mode = (uint32_t)get("CS_LARGE_MODE");
     if (!t.large_grid) t.large_grid = (uint32_t)get("CS_LARGE_GRID");
     if (!t.m_classes) t.m_classes = (uint32_t)get("CS_M_CLASSES");
+    if (!t.item_hits) t.item_hits = (uint32_t)get("CS_ITEM_HITS");
+    if (!t.class_min_hits) t.class_min_hits = (uint32_t)get("CS_CLASS_MIN_HITS");
 }
 
 cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc,
@@ -422,8 +424,10 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
         if (Q == 6) pl->mcls = MClasses{6, 2, {(1 + 6 - ms) % 6, (5 + 6 - ms) % 6}};
         if (Q == 2) pl->mcls = MClasses{2, 1, {(1 + 2 - ms) % 2, 0}};
     }
-    const double SPLIT_MIN_HITS = 12.0;   // expected hits per prime (all m) at the chunk's low end
-    const double HITS_PER_ITEM = 128.0;   // walked hits per work item
+    // expected hits per prime (every m) at a chunk's low end from which it walks
+    // the classes, and walked hits per work item
+    const double SPLIT_MIN_HITS = pl->tune.class_min_hits ? (double)pl->tune.class_min_hits : 24.0;
+    const double HITS_PER_ITEM = pl->tune.item_hits ? (double)pl->tune.item_hits : 128.0;
     auto split_for = [&](uint64_t lo) -> bool {
         if (pl->mcls.Q == 1) return false;
         if (pl->tune.m_classes == 2) return true;

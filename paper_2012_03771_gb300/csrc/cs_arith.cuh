@@ -54,6 +54,50 @@ CS_HD uint32_t mont32_r2(uint32_t p) {
     return (uint32_t)((r * r) % p);
 }
 
+// R^2 mod p without a 64-bit division, for odd 2^20 <= p < 2^31 (smaller p
+// take the plain remainder): a Barrett-style reduction (P. Barrett, CRYPTO '86)
+// of n = 2^64 - 1 whose quotients are estimated with the correctly rounded
+// float reciprocal of p.  The first estimate of n / p <= 2^44 is off by less
+// than 2^22; its remainder, taken in wrapping 64-bit arithmetic, is exact as a
+// signed value; two more estimates bring it into (-p, 2p), and two
+// corrections into [0, p).  Then R^2 = n + 1.
+CS_HD float rcp_rn(float x) {
+#if defined(__CUDA_ARCH__)
+    return __frcp_rn(x);
+#else
+    return 1.0f / x;
+#endif
+}
+CS_HD uint32_t mont32_r2_fast(uint32_t p) {
+    if (p < (1u << 20)) return mont32_r2(p);
+    const float fr = rcp_rn((float)p);
+    const uint64_t q0 = (uint64_t)(18446744073709551616.0f * fr);
+    int64_t rem = (int64_t)(~0ull - q0 * (uint64_t)p);
+    for (int pass = 0; pass < 2; pass++) {
+        const int64_t q = (int64_t)((float)rem * fr);
+        rem -= q * (int64_t)p;
+    }
+    if (rem < 0) rem += p;
+    if (rem < 0) rem += p;
+    if (rem >= (int64_t)p) rem -= p;
+    if (rem >= (int64_t)p) rem -= p;
+    const uint32_t r = (uint32_t)rem + 1;
+    return r == p ? 0u : r;
+}
+
+// (r * M + s) mod p for r < p, M < 2^64, s < p, given rt = r R mod p and
+// r2 = R^2 mod p: r * M = r * lo + (r * hi) * 2^32 with M = hi 2^32 + lo, each
+// part one Montgomery product (no 64-bit division).
+CS_HD uint32_t mont32_affine(uint32_t rt, uint64_t M, uint32_t s, uint32_t r2, uint32_t p, uint32_t pinv) {
+    uint32_t v = mont32_mul(rt, (uint32_t)M, p, pinv);
+    if (M >> 32) {
+        uint32_t h = mont32_mul(rt, (uint32_t)(M >> 32), p, pinv);   // r hi mod p
+        h = mont32_mul(h, r2, p, pinv);                               // r hi R mod p
+        v = v + h >= p ? v + h - p : v + h;
+    }
+    return v + s >= p ? v + s - p : v + s;
+}
+
 // R^e mod p given R mod p and R^2 mod p.  Under mont32_mul the residues
 // Y_j = R^(j+1) mod p form a monoid with Y_a * Y_b = Y_(a+b) and identity Y_0 = R,
 // so R^e = Y_1^(e-1) by square-and-multiply.  e >= 1.
@@ -284,6 +328,131 @@ CS_HD bool g_solve_multi(UT p, UT K, const UT (&L0)[NW], const UT (&w)[NW], UT (
         p = np;
     }
     return n_open == 0;
+}
+
+// The two steps of the three-gap walk from one run of Euclid's algorithm.
+//
+// For 0 < r < p with gcd(r, p) = 1 and 1 <= w < p: a = the smallest m > 0 with
+// r m mod p in [p - w, p - 1] (da = p - r a mod p) and b = the smallest with
+// r m mod p in [1, w] (ub = r b mod p), the same answers as the solver G of
+// Section 3.3 gives for those two windows.  Euclid's algorithm on x_0 = p,
+// x_1 = r with m_0 = 0, m_1 = 1, x_(k+1) = x_(k-1) - c_k x_k,
+// m_(k+1) = m_(k-1) + c_k m_k keeps r m_k = (-1)^(k+1) x_k (mod p), so odd k
+// give residues +x_k and even k residues -x_k.  The first m of a given sign
+// whose residue is at most w is a convergent or intermediate fraction
+// (best approximation): with K the first index where x_K <= w, the sign of K
+// is reached at m_(K-2) + t m_(K-1), t = ceil((x_(K-2) - w) / x_(K-1)) (at m_1
+// when K = 1), and the other sign at m_(K-1) + t' m_K,
+// t' = ceil((x_(K-1) - w) / x_K).  One division per step, against the solver's
+// window bookkeeping.  Returns false after max_iter steps (not reached: the
+// x_k fall at least as fast as Fibonacci numbers).
+template <class UT>
+CS_HD bool tg_steps(UT p, UT r, UT w, UT &a, UT &da, UT &b, UT &ub, uint32_t &iters, uint32_t max_iter) {
+    UT x_pp = 0, m_pp = 0, x_prev = p, m_prev = 0, x = r, m = 1;
+    uint32_t k = 1;
+    while (x > w) {
+        if (k > max_iter) return false;
+        const UT c = udiv(x_prev, x);
+        const UT xn = x_prev - c * x, mn = m_prev + c * m;
+        x_pp = x_prev; m_pp = m_prev;
+        x_prev = x; m_prev = m;
+        x = xn; m = mn;
+        k++;
+    }
+    iters += k;
+    UT ms, xs;                                   // first m with the sign of x_K
+    if (k == 1) {
+        ms = 1;
+        xs = r;
+    } else {
+        const UT t = udiv((UT)(x_pp - w + x_prev - 1), x_prev);
+        ms = m_pp + t * m_prev;
+        xs = x_pp - t * x_prev;
+    }
+    const UT t2 = udiv((UT)(x_prev - w + x - 1), x);   // first m with the other sign
+    const UT mo = m_prev + t2 * m, xo = x_prev - t2 * x;
+    if (k & 1) {
+        b = ms; ub = xs; a = mo; da = xo;
+    } else {
+        a = ms; da = xs; b = mo; ub = xo;
+    }
+    return true;
+}
+
+// floor(n / p) for n < 2^62, p < 2^31 and a quotient below 2^32, given
+// fr = rcp_rn(p): a float estimate of the quotient (off by less than 2^10),
+// its exact remainder in 64-bit arithmetic, one refinement (off by at most
+// one) and two corrections each way.
+CS_HD uint64_t udiv64_est(uint64_t n, uint32_t p, float fr, int64_t &rem_out) {
+    uint64_t q = (uint64_t)((float)n * fr);
+    int64_t rem = (int64_t)(n - q * p);
+    const int64_t q1 = (int64_t)((float)rem * fr);
+    rem -= q1 * (int64_t)p;
+    q += (uint64_t)q1;
+    if (rem < 0) { rem += p; q--; }
+    if (rem < 0) { rem += p; q--; }
+    if (rem >= (int64_t)p) { rem -= p; q++; }
+    if (rem >= (int64_t)p) { rem -= p; q++; }
+    rem_out = rem;
+    return q;
+}
+
+// First hit of a walk from the three-gap basis, without a solve.
+//
+// For 0 < r < p and 1 <= w < p let a > 0 be the smallest m with r m mod p in
+// [p - w, p - 1] (r a = -da) and b the smallest with r m mod p in [1, w]
+// (r b = ub).  Then a ub + b da = p, so e1 = (a, -da) and e2 = (b, ub) are a
+// basis of the lattice {(t, y) : y = r t (mod p)}, and the points of
+// (0, v0) + lattice in the strip 0 <= y <= w are (i a + j b, v0 - i da + j ub)
+// for the (i, j) with 0 <= v0 - i da + j ub <= w.  Ordered by t they form one
+// chain whose steps are e1, e2 or e1 + e2, so i and j never decrease along it.
+// With da <= ub the chain runs through blocks of fixed j (i from
+// ceil((Y_j - w)/da) to floor(Y_j/da), Y_j = v0 + j ub); the first block whose
+// last point has t >= 0 is j = -floor(v0 a / p) or the next one (a da / p < 1),
+// and the answer is its first point with t >= 0.  With ub < da the roles of
+// (i, a, da) and (j, b, ub) swap, the first block being i = ceil((v0 - w) b / p)
+// or the next.  Returns the smallest t >= 0 with (v0 + r t) mod p <= w, for
+// w < v0 < p < 2^30 (smaller v0 is a hit at t = 0), and in y_out that residue.
+CS_HD uint32_t first_hit32(uint32_t p, float fr, uint32_t w, uint32_t a, uint32_t da, uint32_t b,
+                           uint32_t ub, uint32_t v0, uint32_t &y_out) {
+    int64_t rem;
+    // steps e (a or b) from the block's first point t_lo to its first point
+    // with t >= 0: ceil(-t_lo / e), so that t = t_lo mod e
+    auto steps_to = [&](int64_t t_lo, uint32_t e) -> int64_t {
+        if (t_lo >= 0) return 0;
+        int64_t rm;
+        const int64_t q = (int64_t)udiv64_est((uint64_t)(-t_lo), e, rcp_rn((float)e), rm);
+        return q + (rm != 0);
+    };
+    if (da <= ub) {
+        int64_t j = -(int64_t)udiv64_est((uint64_t)v0 * a, p, fr, rem);
+        for (int k = 0; k < 2; k++, j++) {
+            const int64_t Y = (int64_t)v0 + j * (int64_t)ub;               // 0 <= Y < 2^31
+            const int64_t ihi = (int64_t)((uint32_t)Y / da);
+            if (ihi * a + j * (int64_t)b < 0) continue;
+            const int64_t x = Y - (int64_t)w;                              // i_lo = ceil(x / da)
+            int64_t i = x >= 0 ? (int64_t)(((uint32_t)x + da - 1) / da) : -(int64_t)((uint32_t)(-x) / da);
+            i += steps_to(i * a + j * (int64_t)b, a);
+            y_out = (uint32_t)(Y - i * da);
+            return (uint32_t)(i * a + j * (int64_t)b);
+        }
+    } else {
+        int64_t i = (int64_t)udiv64_est((uint64_t)(v0 - w) * b, p, fr, rem);
+        if (rem) i++;                                                      // ceil
+        for (int k = 0; k < 2; k++, i++) {
+            const int64_t X = i * (int64_t)da - v0;                        // |X| < 2^31
+            const int64_t xh = X + w;                                      // j_hi = floor(xh / ub)
+            const int64_t jhi = xh >= 0 ? (int64_t)((uint32_t)xh / ub)
+                                        : -(int64_t)(((uint32_t)(-xh) + ub - 1) / ub);
+            if (i * (int64_t)a + jhi * b < 0) continue;
+            int64_t j = X >= 0 ? (int64_t)(((uint32_t)X + ub - 1) / ub) : -(int64_t)((uint32_t)(-X) / ub);
+            j += steps_to(i * (int64_t)a + j * b, b);
+            y_out = (uint32_t)(j * ub - X);
+            return (uint32_t)(i * (int64_t)a + j * b);
+        }
+    }
+    y_out = 0;
+    return 0xffffffffu;   // not reached for valid input
 }
 
 // ------------------------------------------------------------- checksum

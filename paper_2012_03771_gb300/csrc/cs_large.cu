@@ -8,13 +8,13 @@
 //                    (Section 3.3) finds the next m whose v is in the window,
 //                    the hit is recorded, m advances by one and the next solve
 //                    starts there.
-//   LARGE_THREE_GAP  two G solves per prime give the first m with r*m mod p in
-//                    [p - 2SL, p - 1] (a step that lowers v by at most 2SL) and
-//                    in [1, 2SL] (a step that raises it); by the three-distance
-//                    theorem the next hit after any hit is one of those steps or
-//                    their sum (cf. Franke and Kleinjung, "Continued fractions and
-//                    lattice sieving", SHARCS 2005), so after the first hit, found
-//                    by one more solve, every further hit costs O(1).
+//   LARGE_THREE_GAP  the first m with r*m mod p in [p - 2SL, p - 1] (a step
+//                    that lowers v by at most 2SL) and in [1, 2SL] (a step that
+//                    raises it), i.e. G of those two windows; by the
+//                    three-distance theorem the next hit after any hit is one of
+//                    those steps or their sum (cf. Franke and Kleinjung,
+//                    "Continued fractions and lattice sieving", SHARCS 2005), so
+//                    after the first hit every further hit costs O(1).
 //
 // Each hit on a coprime m and a stored x clears one bit of the device bitset
 // with a 32-bit atomic AND and counts one enumerated factor.
@@ -175,9 +175,12 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_large(const LargeArgs a) {
 // classes m = c (mod Q) with gcd(c, Q) = 1, each as its own walker over
 // j in m = m_c + Q j: v steps by r' = Q r mod p per unit of j, the two step
 // windows are solved for r' (steps of Q j' in m), and each class needs its own
-// first hit.  All windows share (p, r'), so one fused solve serves them
-// (Q = 6: 2 + 2 windows), and the walk visits a third of the hits (Q = 6) or
-// half of them (Q = 2).
+// first hit.  The walk visits a third of the hits (Q = 6) or half of them
+// (Q = 2).  The two steps come from one run of Euclid's algorithm on (p, r')
+// (tg_steps, the same answers as G for the two step windows); in the 32-bit
+// walk the first hits follow from the two step vectors, a basis of the lattice
+// of (j, r' j mod p) (first_hit32), and the 64-bit walk solves them as windows
+// of one fused G.
 template <class UT, class ST, class MT>
 struct TGItem {
     MT moff, end;      // current m - M_start, end of the segment
@@ -198,8 +201,14 @@ __device__ __forceinline__ UT add_times(UT v, UT r, uint32_t k, UT p) {
     return v;
 }
 
+// resident CTAs per SM the 32-bit walk is compiled for: three (85 registers)
+// measured 7% faster than four (64 registers, with spills) on a GB300
+#ifndef CS_TG_MIN_BLOCKS
+#define CS_TG_MIN_BLOCKS 3
+#endif
+
 template <class UT, class ST, class MT, int NC>
-__global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? 4 : 1) k_large_tg(const LargeArgs a) {
+__global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLOCKS : 1) k_large_tg(const LargeArgs a) {
     constexpr int QCAP = 32 * (NC + 1);   // a refill adds at most 32 NC walkers
     __shared__ TGItem<UT, ST, MT> queue[TG_WARPS][QCAP];
     const DevPlan &pl = a.pl;
@@ -220,6 +229,7 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? 4 : 1) k_larg
     // any step >= M ends a walker (its segment is at most M long); two clamped
     // steps still add up below 2^32
     const uint64_t cap_step = M;
+    const uint64_t seg_len = (M + n_seg - 1) / n_seg;
     TGItem<UT, ST, MT> *q = queue[wib];
     Counters c;
     if (M == 0) return;
@@ -244,15 +254,25 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? 4 : 1) k_larg
             if (item < n_items) {
                 uint64_t i = item, m_lo = 0, m_hi = M;
                 if (n_seg > 1) {
-                    i = item / n_seg;
+                    // segments of seg_len m (the last one shorter)
+                    i = n_items >> 32 ? item / n_seg : (uint32_t)item / n_seg;
                     const uint32_t sg = (uint32_t)(item - i * n_seg);
-                    m_lo = M * sg / n_seg;
-                    m_hi = M * (sg + 1) / n_seg;
+                    m_lo = (uint64_t)sg * seg_len;
+                    m_hi = min(M, m_lo + seg_len);
                 }
                 const UT pp = Pp[i], r = Rp[i];
                 bool ok = m_lo < m_hi && (uint64_t)pp > a.p_lo && (uint64_t)pp <= a.p_hi;
                 UT vv = ok ? (Vp ? Vp[i] : start_v(r, pl.M_start, pl.SL, pp)) : (UT)0;
-                if (ok && m_lo) vv = advance(vv, r, m_lo, pp);
+                if (ok && m_lo) {
+                    if constexpr (sizeof(UT) == 4) {
+                        // (r m_lo + v) mod p: quotient below m_lo + 1 < 2^31
+                        int64_t rm;
+                        udiv64_est((uint64_t)r * m_lo + vv, pp, rcp_rn((float)pp), rm);
+                        vv = (UT)rm;
+                    } else {
+                        vv = advance(vv, r, m_lo, pp);
+                    }
+                }
                 uint32_t it = 0;
                 UT ma_ = 0, da_ = 0, mb_ = 0, ub_ = 0;
                 uint64_t first[NC];
@@ -277,35 +297,49 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? 4 : 1) k_larg
                     }
                 } else if (ok) {
                     // class k starts at the first m_lo + dk with m = c_k (mod Q)
-                    const uint32_t lo_res = (uint32_t)m_lo % Q;      // m_lo < M_inc < 2^31
+                    const uint32_t lo_res = Q == 1 ? 0u : (uint32_t)m_lo % Q;   // m_lo < M_inc < 2^31
                     UT rq = add_times(r, r, Q - 1, pp);        // r' = Q r mod p
-                    UT Lw[2 + NC], Ww[2 + NC], mw[2 + NC], yw[2 + NC];
-                    Lw[0] = (UT)(pp - w); Ww[0] = (UT)(w - 1);   // r' j mod p in [p - 2SL, p - 1]
-                    Lw[1] = (UT)1;        Ww[1] = (UT)(w - 1);   // r' j mod p in [1, 2SL]
-                    uint32_t n_first = 0;
 #pragma unroll
                     for (int k = 0; k < NC; k++) {
                         uint32_t dd = a.mc.off[k] + Q - lo_res;
                         if (dd >= Q) dd -= Q;
                         dk[k] = dd;
                         vk[k] = add_times(vv, r, dd, pp);
-                        const bool need = vk[k] > w;
-                        n_first += need;
-                        Lw[2 + k] = need ? (UT)(pp - vk[k]) : (UT)0;   // L = 0: m = 0 (case a)
-                        Ww[2 + k] = w;
                     }
-                    c.solves += 2 + n_first;
-                    ok = g_solve_multi<UT, ST, 2 + NC>(pp, rq, Lw, Ww, mw, yw, it, max_iter);
+                    // the two steps from one run of Euclid's algorithm on (p, r')
+                    ok = tg_steps<UT>(pp, rq, w, ma_, da_, mb_, ub_, it, max_iter);
                     if (!ok) c.err |= ERR_SOLVER_LIMIT;
-                    ma_ = mw[0];
-                    da_ = pp - yw[0];
-                    mb_ = mw[1];
-                    ub_ = yw[1];
+                    uint32_t n_first = 0;
 #pragma unroll
-                    for (int k = 0; k < NC; k++) {
-                        if (vk[k] > w) {
-                            first[k] = (uint64_t)mw[2 + k] * Q;
-                            vk[k] = (UT)(vk[k] + yw[2 + k] - pp);
+                    for (int k = 0; k < NC; k++) n_first += vk[k] > w;
+                    c.solves += 2 + n_first;
+                    if constexpr (sizeof(UT) == 4) {
+                        // each walker's first hit from the step basis, without a solve
+                        const float fr = rcp_rn((float)pp);
+#pragma unroll
+                        for (int k = 0; k < NC; k++) {
+                            if (ok && vk[k] > w) {
+                                uint32_t y;
+                                first[k] = (uint64_t)first_hit32(pp, fr, w, ma_, da_, mb_, ub_, vk[k], y) * Q;
+                                vk[k] = y;
+                            }
+                        }
+                    } else if (ok && n_first) {
+                        // 64-bit: the first hits as windows of one fused solve
+                        UT Lw[NC], Ww[NC], mw[NC], yw[NC];
+#pragma unroll
+                        for (int k = 0; k < NC; k++) {
+                            Lw[k] = vk[k] > w ? (UT)(pp - vk[k]) : (UT)0;   // L = 0: m = 0 (case a)
+                            Ww[k] = w;
+                        }
+                        ok = g_solve_multi<UT, ST, NC>(pp, rq, Lw, Ww, mw, yw, it, max_iter);
+                        if (!ok) c.err |= ERR_SOLVER_LIMIT;
+#pragma unroll
+                        for (int k = 0; k < NC; k++) {
+                            if (vk[k] > w) {
+                                first[k] = (uint64_t)mw[k] * Q;
+                                vk[k] = (UT)(vk[k] + yw[k] - pp);
+                            }
                         }
                     }
                 }

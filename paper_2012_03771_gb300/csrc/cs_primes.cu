@@ -5,9 +5,10 @@
 // primes never cross the host boundary.
 //
 // One CTA sieves one segment of SEG odd numbers in shared memory at a time
-// (grid-stride over segments).  Multiples of the base primes q <= sqrt(hi) are
-// marked with shared-memory atomics: small q cooperatively by a warp, large q
-// one per thread.  Each warp then scans its share of the segment, queues the
+// (grid-stride over segments).  The multiples of 3..31 come from tabulated
+// period masks; those of the other base primes q <= sqrt(hi) are marked with
+// shared-memory atomics: small q cooperatively by a warp, large q one per
+// thread.  Each warp then scans its share of the segment, queues the
 // primes it finds in shared memory and, 32 at a time, computes K mod p with
 // Montgomery multiplication over K's prime factors packed into machine words,
 // and appends the entries to the output with one atomic per 32 primes.
@@ -91,12 +92,11 @@ __device__ __forceinline__ void emit(const GenArgs &a, uint64_t p, bool valid, u
         } else if (KIND == KIND_LARGE32) {
             uint32_t p32 = (uint32_t)p;
             uint32_t pinv = mont32_neg_inv(p32);
-            uint32_t r1 = mont32_r1(p32), r2 = mont32_r2(p32);
+            uint32_t r2 = mont32_r2_fast(p32);
+            uint32_t r1 = mont32_mul(r2, 1u, p32, pinv);         // R mod p
             uint32_t r = kmodp32(p32, pinv, r1, r2, a.kch32, a.n_kch32);
             uint32_t rt = mont32_mul(r, r2, p32, pinv);
-            uint32_t ms = (uint32_t)(a.M_start % p32);
-            uint32_t v = mont32_mul(rt, ms, p32, pinv) + a.SL;   // SL < p
-            e0 = p32; e1 = r; e2 = v >= p32 ? v - p32 : v;
+            e0 = p32; e1 = r; e2 = mont32_affine(rt, a.M_start, a.SL, r2, p32, pinv);   // SL < p
         } else if (KIND == KIND_LARGE64) {
             uint64_t pinv = mont64_neg_inv(p);
             uint64_t r1 = mont64_r1(p), r2 = mont64_r2(p);
@@ -108,7 +108,8 @@ __device__ __forceinline__ void emit(const GenArgs &a, uint64_t p, bool valid, u
             uint32_t p32 = (uint32_t)p;
             uint32_t pinv = mont32_neg_inv(p32);
             e0 = p32;
-            e1 = kmodp32(p32, pinv, mont32_r1(p32), mont32_r2(p32), a.kch32, a.n_kch32);
+            const uint32_t r2 = mont32_r2_fast(p32);
+            e1 = kmodp32(p32, pinv, mont32_mul(r2, 1u, p32, pinv), r2, a.kch32, a.n_kch32);
         } else if (KIND == KIND_PR64) {
             uint64_t pinv = mont64_neg_inv(p);
             w0 = p;
@@ -156,11 +157,43 @@ __device__ __forceinline__ uint32_t first_rem(uint64_t n, uint32_t q) {
     return (n >> 32) == 0 ? (uint32_t)n % q : (uint32_t)(n % q);
 }
 
+// Pre-sieve of the odd multiples of 3..31 (half of all marks, and the ones
+// whose lanes collide on the same shared-memory word): the masks of one period
+// of T = 3*5*7, 11*13, 17*19, 23*29 and 31 odd indices are tabulated in shared
+// memory, and word w of a segment, whose first odd index I = i0 + 32 w has
+// I mod T = s, ORs in table entry s.  Bit b of that entry is set when the odd
+// number 2(I + b) + 1 has a factor q | T, i.e. I + b = (q - 1)/2 (mod q).
+constexpr int PRE_N = 5;
+constexpr uint32_t PRE_MAX_Q = 31;
+__device__ __constant__ uint32_t c_pre_T[PRE_N] = {105, 143, 323, 667, 31};
+__device__ __constant__ uint32_t c_pre_off[PRE_N + 1] = {0, 105, 248, 571, 1238, 1269};
+constexpr uint32_t PRE_WORDS = 1269;
+
+__device__ __forceinline__ uint32_t pre_mask(uint32_t T, uint32_t s) {
+    const uint32_t qs[10] = {3, 5, 7, 11, 13, 17, 19, 23, 29, 31};
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < 10; k++) {
+        const uint32_t q = qs[k];
+        if (T % q) continue;
+        const uint32_t h = (q - 1) / 2;
+        for (uint32_t b = (h + q - s % q) % q; b < 32; b += q) m |= 1u << b;
+    }
+    return m;
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(GEN_THREADS) k_gen(const GenArgs a) {
     __shared__ uint32_t comp[SEG_WORDS];          // bit set = composite (or out of range)
     __shared__ uint32_t queue[GEN_WARPS][QCAP];
+    __shared__ uint32_t pre[PRE_WORDS];           // pre-sieve tables
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t e = threadIdx.x; e < PRE_WORDS; e += GEN_THREADS) {
+        int t = 0;
+        while (e >= c_pre_off[t + 1]) t++;
+        pre[e] = pre_mask(c_pre_T[t], e - c_pre_off[t]);
+    }
+    __syncthreads();
 
     if (a.emit_two && blockIdx.x == 0 && warp == 0) emit<KIND>(a, 2, lane == 0, lane);
 
@@ -181,10 +214,27 @@ __global__ void __launch_bounds__(GEN_THREADS) k_gen(const GenArgs a) {
         const uint32_t len = (uint32_t)(i1 - i0);
         const uint64_t n_first = 2 * i0 + 1;
         const uint64_t n_last = 2 * (i1 - 1) + 1;
+        // the tables apply when no q <= 31 lies in the segment itself
+        const bool pre_ok = n_first > PRE_MAX_Q;
+        uint32_t ph[PRE_N], step[PRE_N];
+#pragma unroll
+        for (int t = 0; t < PRE_N; t++) {
+            const uint32_t T = c_pre_T[t];
+            ph[t] = pre_ok ? first_rem(i0 + 32ull * threadIdx.x, T) : 0;
+            step[t] = (32u * GEN_THREADS) % T;
+        }
         for (uint32_t w = threadIdx.x; w < seg_words; w += GEN_THREADS) {
             uint32_t v = 0;
             uint32_t lo = w * 32;
             if (lo + 32 > len) v = lo >= len ? 0xffffffffu : (0xffffffffu << (len - lo));
+            if (pre_ok) {
+#pragma unroll
+                for (int t = 0; t < PRE_N; t++) {
+                    v |= pre[c_pre_off[t] + ph[t]];
+                    ph[t] += step[t];
+                    if (ph[t] >= c_pre_T[t]) ph[t] -= c_pre_T[t];
+                }
+            }
             comp[w] = v;
         }
         __syncthreads();
@@ -195,6 +245,7 @@ __global__ void __launch_bounds__(GEN_THREADS) k_gen(const GenArgs a) {
             const uint32_t q = __ldg(&a.base[b]);
             if ((uint64_t)q * q > n_last) break;
             if (q >= WARP_COOP_Q) break;
+            if (pre_ok && q <= PRE_MAX_Q) continue;          // in the pre-sieve
             uint64_t start = (uint64_t)q * q;
             if (start < n_first) {
                 const uint32_t rem = first_rem(n_first, q);

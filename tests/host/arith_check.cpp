@@ -2,13 +2,56 @@
 // reads "p K L R" lines, prints "m y" from g_solve (32- or 64-bit), from
 // g_solve_multi with the window in one of three slots and, 32-bit, in the last
 // of four slots.  Mode "q" reads "a d" lines and prints the 32-bit quotient of
-// the solver's shared-reciprocal division.
+// the solver's shared-reciprocal division; mode "r" checks the prime
+// generator's division-free R^2 mod p and (r M + s) mod p; mode "f" the walk's
+// first hit from the three-gap basis; mode "s" the walk's two steps from
+// Euclid's algorithm.
 #include <cstdio>
 #include <cstdint>
 #include "../../paper_2012_03771_gb300/csrc/cs_arith.cuh"
 
 int main(int argc, char **argv) {
     const bool narrow = argc > 1 && argv[1][0] == 'n';
+    if (argc > 1 && argv[1][0] == 'r') {
+        // "p M r s" -> R^2 mod p (division-free) and (r M + s) mod p via mont32_affine
+        unsigned long long p, M, r, s;
+        while (scanf("%llu %llu %llu %llu", &p, &M, &r, &s) == 4) {
+            const uint32_t p32 = (uint32_t)p, pinv = cs::mont32_neg_inv(p32);
+            const uint32_t r2 = cs::mont32_r2_fast(p32);
+            const uint32_t rt = cs::mont32_mul((uint32_t)r, r2, p32, pinv);
+            printf("%u %u\n", r2, cs::mont32_affine(rt, M, (uint32_t)s, r2, p32, pinv));
+        }
+        return 0;
+    }
+    if (argc > 1 && argv[1][0] == 's') {
+        // "p r w" -> a da b ub from Euclid's algorithm, 32-bit (p < 2^31) and 64-bit
+        unsigned long long p, r, w;
+        while (scanf("%llu %llu %llu", &p, &r, &w) == 3) {
+            uint32_t it = 0;
+            unsigned long long a64, da64, b64, ub64;
+            uint64_t A, DA, B, UB;
+            bool ok64 = cs::tg_steps<uint64_t>(p, r, w, A, DA, B, UB, it, 200);
+            a64 = A; da64 = DA; b64 = B; ub64 = UB;
+            uint32_t a = 0, da = 0, b = 0, ub = 0;
+            bool ok32 = p < (1ull << 31) && cs::tg_steps<uint32_t>((uint32_t)p, (uint32_t)r, (uint32_t)w, a, da, b, ub, it, 200);
+            printf("%d %llu %llu %llu %llu %d %u %u %u %u\n", ok64, a64, da64, b64, ub64, ok32, a, da, b, ub);
+        }
+        return 0;
+    }
+    if (argc > 1 && argv[1][0] == 'f') {
+        // "p r w v0" -> first t >= 0 with (v0 + r t) mod p <= w from the three-gap basis
+        unsigned long long p, r, w, v0;
+        while (scanf("%llu %llu %llu %llu", &p, &r, &w, &v0) == 4) {
+            const uint32_t Ls[2] = {(uint32_t)(p - w), 1u}, Ws[2] = {(uint32_t)(w - 1), (uint32_t)(w - 1)};
+            uint32_t ms[2], ys[2], it = 0;
+            bool ok = cs::g_solve_multi<uint32_t, int32_t, 2>((uint32_t)p, (uint32_t)r, Ls, Ws, ms, ys, it, 200);
+            uint32_t y = 0;
+            const uint32_t t = cs::first_hit32((uint32_t)p, cs::rcp_rn((float)p), (uint32_t)w, ms[0],
+                                               (uint32_t)(p - ys[0]), ms[1], ys[1], (uint32_t)v0, y);
+            printf("%d %u %u\n", ok, t, y);
+        }
+        return 0;
+    }
     if (argc > 1 && argv[1][0] == 'q') {
         unsigned long long a, d;
         while (scanf("%llu %llu", &a, &d) == 2)

@@ -64,3 +64,68 @@ def test_shared_reciprocal_quotients(exe):
     assert len(out) == len(cases)
     for (a, d), q in zip(cases, out):
         assert int(q) == a // d, (a, d)
+
+
+def test_division_free_montgomery_constants(exe):
+    """R^2 mod p (R = 2^32) from float-reciprocal quotient estimates, and
+    (r M + s) mod p from two Montgomery products, against exact integers, for
+    odd p across [3, 2^31) (the estimate is used from 2^20 up), M up to 2^40."""
+    rng = random.Random(13)
+    ps = [3, 5, (1 << 20) - 3, (1 << 20) + 7, (1 << 20) + 1, (1 << 30) - 35, (1 << 31) - 1, (1 << 31) - 19]
+    ps += [rng.randrange(1 << 20, 1 << 31) | 1 for _ in range(20000)]
+    ps += [rng.randrange(3, 1 << 20) | 1 for _ in range(2000)]
+    cases = []
+    for p in ps:
+        M = rng.choice([0, 1, rng.randrange(1, 1 << 32), rng.randrange(1 << 32, 1 << 40), (1 << 40) - 1])
+        cases.append((p, M, rng.randrange(0, p), rng.randrange(0, p)))
+    inp = "".join(f"{p} {M} {r} {s}\n" for p, M, r, s in cases)
+    out = subprocess.run([exe, "r"], input=inp, capture_output=True, text=True, check=True).stdout.split("\n")
+    for (p, M, r, s), line in zip(cases, out):
+        r2, v = (int(t) for t in line.split())
+        assert r2 == pow(2, 64, p), p
+        assert v == (r * M + s) % p, (p, M, r, s)
+
+
+def test_first_hit_from_three_gap_basis(exe):
+    """The walk's first hit without a solve (chain of strip points in the basis
+    of the two step vectors) equals the paper's G for the window [p - v0, p - v0 + w],
+    including w = 1, v0 = w + 1 and v0 = p - 1, and primes up to 2^30."""
+    rng = random.Random(17)
+    pool = [5, 7, 101, 7919, 104729, 1000003, 999999937, (1 << 30) - 35]
+    cases = []
+    for _ in range(20000):
+        p = rng.choice(pool)
+        r = rng.randrange(1, p)
+        w = min(rng.choice([1, 2, 3, 17, 300, 40000, 50001, rng.randrange(1, p)]), p - 2)
+        v0 = rng.choice([w + 1, p - 1, rng.randrange(w + 1, p)])
+        cases.append((p, r, w, v0))
+    inp = "".join(f"{p} {r} {w} {v0}\n" for p, r, w, v0 in cases)
+    out = subprocess.run([exe, "f"], input=inp, capture_output=True, text=True, check=True).stdout.split("\n")
+    for (p, r, w, v0), line in zip(cases, out):
+        ok, t, y = (int(x) for x in line.split())
+        assert ok and t == O.G(p, r, p - v0, p - v0 + w), (p, r, w, v0)
+        assert y == (v0 + r * t) % p, (p, r, w, v0)
+
+
+def test_three_gap_steps_from_euclid(exe):
+    """The walk's two steps from one run of Euclid's algorithm (32- and 64-bit)
+    equal the paper's G for the windows [p - w, p - 1] and [1, w]."""
+    rng = random.Random(19)
+    pool = [3, 5, 101, 7919, 1000003, 999999937, (1 << 30) - 35, 4294967291, 1099511627689]
+    cases = []
+    for _ in range(20000):
+        p = rng.choice(pool)
+        r = rng.randrange(1, p)
+        w = min(rng.choice([1, 2, 3, 17, 300, 40000, 50001, rng.randrange(1, p)]), p - 2)
+        if w < 1:
+            continue
+        cases.append((p, r, w))
+    inp = "".join(f"{p} {r} {w}\n" for p, r, w in cases)
+    out = subprocess.run([exe, "s"], input=inp, capture_output=True, text=True, check=True).stdout.split("\n")
+    for (p, r, w), line in zip(cases, out):
+        ok64, a, da, b, ub, ok32, a2, da2, b2, ub2 = (int(x) for x in line.split())
+        ga, gb = O.G(p, r, p - w, p - 1), O.G(p, r, 1, w)
+        want = (ga, p - ga * r % p, gb, gb * r % p)
+        assert ok64 and (a, da, b, ub) == want, (p, r, w)
+        if p < (1 << 31):
+            assert ok32 and (a2, da2, b2, ub2) == want, (p, r, w)

@@ -248,7 +248,7 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
     {
         uint64_t acc = 1;
         for (uint32_t q : qK) {
-            if (acc > 0xffffffffull / q) { kch32.push_back((uint32_t)acc); acc = 1; }
+            if (acc > 0x7fffffffull / q) { kch32.push_back((uint32_t)acc); acc = 1; }   // words < 2^31
             acc *= q;
         }
         if (acc > 1) kch32.push_back((uint32_t)acc);
@@ -997,7 +997,7 @@ cs_status cs_k_mod_p(uint32_t P, uint64_t d, const uint64_t *p, uint64_t n, uint
     std::vector<uint64_t> kch64;
     uint64_t acc = 1;
     for (uint32_t q : qK) {
-        if (acc > 0xffffffffull / q) { kch32.push_back((uint32_t)acc); acc = 1; }
+        if (acc > 0x7fffffffull / q) { kch32.push_back((uint32_t)acc); acc = 1; }   // words < 2^31
         acc *= q;
     }
     if (acc > 1) kch32.push_back((uint32_t)acc);

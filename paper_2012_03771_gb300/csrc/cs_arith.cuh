@@ -47,6 +47,17 @@ CS_HD uint32_t mont32_mul(uint32_t a, uint32_t b, uint32_t p, uint32_t pinv) {
     return r >= p ? r - p : r;
 }
 
+// a * b * 2^-32 mod p, reduced only below 2p (P. L. Montgomery's REDC without
+// the final subtraction): for odd p < 2^31, a < 2p and b < 2^31,
+// (a b + m p) / 2^32 < (2p 2^31 + 2^32 p) / 2^32 = 2p and a b + m p < 2^64,
+// so a chain of such products by words below 2^31 needs one subtraction at
+// its end.
+CS_HD uint32_t mont32_mul_lazy(uint32_t a, uint32_t b, uint32_t p, uint32_t pinv) {
+    const uint64_t t = (uint64_t)a * b;
+    const uint32_t m = (uint32_t)t * pinv;
+    return (uint32_t)((t + (uint64_t)m * p) >> 32);
+}
+
 // R mod p and R^2 mod p for R = 2^32.
 CS_HD uint32_t mont32_r1(uint32_t p) { return (0u - p) % p; }
 CS_HD uint32_t mont32_r2(uint32_t p) {
@@ -411,48 +422,44 @@ CS_HD uint64_t udiv64_est(uint64_t n, uint32_t p, float fr, int64_t &rem_out) {
 // last point has t >= 0 is j = -floor(v0 a / p) or the next one (a da / p < 1),
 // and the answer is its first point with t >= 0.  With ub < da the roles of
 // (i, a, da) and (j, b, ub) swap, the first block being i = ceil((v0 - w) b / p)
-// or the next.  Returns the smallest t >= 0 with (v0 + r t) mod p <= w, for
-// w < v0 < p < 2^30 (smaller v0 is a hit at t = 0), and in y_out that residue.
+// or the next; the second case is the first one for the reflected strip
+// y' = w - y and is computed as such.  Returns the smallest t >= 0 with
+// (v0 + r t) mod p <= w, for w < v0 < p < 2^30 (smaller v0 is a hit at t = 0),
+// and in y_out that residue.
 CS_HD uint32_t first_hit32(uint32_t p, float fr, uint32_t w, uint32_t a, uint32_t da, uint32_t b,
                            uint32_t ub, uint32_t v0, uint32_t &y_out) {
-    int64_t rem;
-    // steps e (a or b) from the block's first point t_lo to its first point
-    // with t >= 0: ceil(-t_lo / e), so that t = t_lo mod e
-    auto steps_to = [&](int64_t t_lo, uint32_t e) -> int64_t {
-        if (t_lo >= 0) return 0;
-        int64_t rm;
-        const int64_t q = (int64_t)udiv64_est((uint64_t)(-t_lo), e, rcp_rn((float)e), rm);
-        return q + (rm != 0);
+    // ub < da is the case da <= ub for the reflected strip y' = w - y (start
+    // w - v0, steps e2 down by ub and e1 up by da): swap the roles and reflect,
+    // so that one branch-free path serves both
+    const bool sw = da > ub;
+    const uint32_t A = sw ? b : a, DA = sw ? ub : da, B = sw ? a : b, UB = sw ? da : ub;
+    const int64_t V0 = sw ? (int64_t)w - (int64_t)v0 : (int64_t)v0;      // |V0| < 2^30
+    // floor(x / d) and ceil(x / d) for |x| < 2^31, 0 < d < 2^31
+    auto fdiv = [](int64_t x, uint32_t d) -> int64_t {
+        const uint32_t ax = (uint32_t)(x < 0 ? -x : x), q = ax / d;
+        return x >= 0 ? (int64_t)q : -(int64_t)q - (ax != q * d);
     };
-    if (da <= ub) {
-        int64_t j = -(int64_t)udiv64_est((uint64_t)v0 * a, p, fr, rem);
-        for (int k = 0; k < 2; k++, j++) {
-            const int64_t Y = (int64_t)v0 + j * (int64_t)ub;               // 0 <= Y < 2^31
-            const int64_t ihi = (int64_t)((uint32_t)Y / da);
-            if (ihi * a + j * (int64_t)b < 0) continue;
-            const int64_t x = Y - (int64_t)w;                              // i_lo = ceil(x / da)
-            int64_t i = x >= 0 ? (int64_t)(((uint32_t)x + da - 1) / da) : -(int64_t)((uint32_t)(-x) / da);
-            i += steps_to(i * a + j * (int64_t)b, a);
-            y_out = (uint32_t)(Y - i * da);
-            return (uint32_t)(i * a + j * (int64_t)b);
-        }
-    } else {
-        int64_t i = (int64_t)udiv64_est((uint64_t)(v0 - w) * b, p, fr, rem);
-        if (rem) i++;                                                      // ceil
-        for (int k = 0; k < 2; k++, i++) {
-            const int64_t X = i * (int64_t)da - v0;                        // |X| < 2^31
-            const int64_t xh = X + w;                                      // j_hi = floor(xh / ub)
-            const int64_t jhi = xh >= 0 ? (int64_t)((uint32_t)xh / ub)
-                                        : -(int64_t)(((uint32_t)(-xh) + ub - 1) / ub);
-            if (i * (int64_t)a + jhi * b < 0) continue;
-            int64_t j = X >= 0 ? (int64_t)(((uint32_t)X + ub - 1) / ub) : -(int64_t)((uint32_t)(-X) / ub);
-            j += steps_to(i * (int64_t)a + j * b, b);
-            y_out = (uint32_t)(j * ub - X);
-            return (uint32_t)(i * (int64_t)a + j * b);
-        }
+    // first block: J = -floor(V0 A / p) = ceil(-V0 A / p)
+    int64_t rem;
+    const uint64_t aq = udiv64_est((uint64_t)(V0 < 0 ? -V0 : V0) * A, p, fr, rem);
+    int64_t j = V0 >= 0 ? -(int64_t)aq : (int64_t)aq + (rem != 0);
+    int64_t Y = V0 + j * (int64_t)UB;                                    // |Y| < 2^31
+    // the block's last point must reach t >= 0, else the next block
+    if (fdiv(Y, DA) * A + j * (int64_t)B < 0) {
+        j++;
+        Y += UB;
     }
-    y_out = 0;
-    return 0xffffffffu;   // not reached for valid input
+    int64_t i = -fdiv((int64_t)w - Y, DA);                               // ceil((Y - w) / DA)
+    const int64_t t_lo = i * A + j * (int64_t)B;
+    if (t_lo < 0) {
+        // steps of A to the first point with t >= 0: ceil(-t_lo / A)
+        int64_t rm;
+        const int64_t q = (int64_t)udiv64_est((uint64_t)(-t_lo), A, rcp_rn((float)A), rm);
+        i += q + (rm != 0);
+    }
+    const uint32_t y = (uint32_t)(Y - i * (int64_t)DA);
+    y_out = sw ? w - y : y;
+    return (uint32_t)(i * A + j * (int64_t)B);
 }
 
 // ------------------------------------------------------------- checksum

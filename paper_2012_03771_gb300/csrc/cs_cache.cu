@@ -182,7 +182,7 @@ cs_status cache_new(uint32_t P, uint64_t d, uint64_t L_max, cs_cache_t *out) {
     std::vector<uint64_t> kch64;
     uint64_t acc = 1;
     for (uint32_t q : qK) {
-        if (acc > 0xffffffffull / q) { kch32.push_back((uint32_t)acc); acc = 1; }
+        if (acc > 0x7fffffffull / q) { kch32.push_back((uint32_t)acc); acc = 1; }   // words < 2^31
         acc *= q;
     }
     if (acc > 1) kch32.push_back((uint32_t)acc);

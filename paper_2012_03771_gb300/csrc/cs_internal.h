@@ -46,7 +46,7 @@ struct DevPlan {
     uint64_t P, L, T;             // primorial bound, sieve limit, small/large threshold
     int small_n;                  // N + x may equal a sieving prime or a prime of d
     uint64_t K64;                 // K when it fits in 64 bits (small_n only)
-    // K's prime factors packed into words: products that fit in 32 / 64 bits
+    // K's prime factors packed into words: products below 2^31 / 2^64
     const uint32_t *kch32;
     uint32_t n_kch32;
     const uint64_t *kch64;

@@ -188,7 +188,11 @@ struct TGItem {
     MT ma, mb;         // steps of m (clamped to M_inc)
 };
 
-constexpr int TG_STEPS = 4;
+// three-gap steps per lane between queue checks
+#ifndef CS_TG_STEPS
+#define CS_TG_STEPS 8
+#endif
+constexpr int TG_STEPS = CS_TG_STEPS;
 constexpr int TG_WARPS = LARGE_THREADS / 32;
 
 // v + k r mod p for a small k (v, r < p, 2p fits in UT)

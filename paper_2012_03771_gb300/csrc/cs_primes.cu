@@ -57,8 +57,9 @@ __device__ __forceinline__ uint32_t kmodp32(uint32_t p, uint32_t pinv, uint32_t 
                                             const uint32_t *kch, uint32_t n) {
     if (n == 0) return 1u % p;
     uint32_t acc = mont32_rpow(n, r1, r2, p, pinv);     // R^n: cancels the n factors R^-1
-    for (uint32_t i = 0; i < n; i++) acc = mont32_mul(acc, __ldg(&kch[i]), p, pinv);
-    return acc;
+    // the factor words are below 2^31, so the running product stays below 2p
+    for (uint32_t i = 0; i < n; i++) acc = mont32_mul_lazy(acc, __ldg(&kch[i]), p, pinv);
+    return acc >= p ? acc - p : acc;
 }
 
 __device__ __forceinline__ uint64_t kmodp64(uint64_t p, uint64_t pinv, uint64_t r1, uint64_t r2,

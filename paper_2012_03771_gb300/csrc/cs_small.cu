@@ -63,22 +63,29 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile(const TileArgs a) {
     __syncthreads();
 
     // 1. rows start as the stored columns minus the wheel of d's primes; one
-    //    pass per prime q | d with the pattern phase advanced incrementally
-    for (uint32_t r = warp; r < nrows; r += TILE_WARPS) {
-        const uint64_t m = pl.M_start + __ldg(&pl.moff_of_row[row0 + r]);
-        for (uint32_t w = lane; w < nw; w += 32) tile[r * nw + w] = mask[w];
-        for (uint32_t qi = 0; qi < pl.n_qd; qi++) {
-            const uint32_t q = __ldg(&pl.qd[qi]);
-            const uint32_t *pat = pl.qd_pat + __ldg(&pl.qd_pat_off[qi]);
-            // phase of word w: (N - SL + zb + 32 w) mod q, N = m*K
-            const uint32_t nq = (uint32_t)((m % q) * __ldg(&pl.qd_kmod[qi]) % q);
-            uint32_t k = (uint32_t)(((uint64_t)nq + q - pl.SL % q + (zb + 32 * lane) % q) % q);
-            const uint32_t step = 1024u % q;
-            __syncwarp();
-            for (uint32_t w = lane; w < nw; w += 32) {
-                tile[r * nw + w] &= ~__ldg(&pat[k]);
-                k += step;
-                if (k >= q) k -= q;
+    //    pass per prime q | d with the pattern phase advanced incrementally.
+    //    Rows are split into word ranges so that every warp has work when a
+    //    tile has fewer rows than the CTA has warps.
+    {
+        const uint32_t parts = nrows ? max(1u, TILE_WARPS / nrows) : 1u;
+        const uint32_t span = ((nw + parts - 1) / parts + 31) & ~31u;       // words per part
+        for (uint32_t t = warp; t < nrows * parts; t += TILE_WARPS) {
+            const uint32_t r = t / parts, w0 = (t % parts) * span, w1 = min(nw, w0 + span);
+            const uint64_t m = pl.M_start + __ldg(&pl.moff_of_row[row0 + r]);
+            for (uint32_t w = w0 + lane; w < w1; w += 32) tile[r * nw + w] = mask[w];
+            for (uint32_t qi = 0; qi < pl.n_qd; qi++) {
+                const uint32_t q = __ldg(&pl.qd[qi]);
+                const uint32_t *pat = pl.qd_pat + __ldg(&pl.qd_pat_off[qi]);
+                // phase of word w: (N - SL + zb + 32 w) mod q, N = m*K
+                const uint32_t nq = (uint32_t)((m % q) * __ldg(&pl.qd_kmod[qi]) % q);
+                uint32_t k = (uint32_t)(((uint64_t)nq + q - pl.SL % q + (zb + 32 * (w0 + lane)) % q) % q);
+                const uint32_t step = 1024u % q;
+                __syncwarp();
+                for (uint32_t w = w0 + lane; w < w1; w += 32) {
+                    tile[r * nw + w] &= ~__ldg(&pat[k]);
+                    k += step;
+                    if (k >= q) k -= q;
+                }
             }
         }
     }
@@ -147,9 +154,15 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile(const TileArgs a) {
 
     // 3. compress the stored columns [j0, j1) of each row into the output words
     //    (compact layout: the row's class columns, one chunk covers the row)
+    //    Each row's columns are split into runs of 1024 (32 output words) over
+    //    several warps when the tile has fewer rows than warps.
     const bool last_chunk = chunk + 1 == a.tc.n_chunks;
     const uint32_t jend = last_chunk ? 64 * pl.wpr : j1;      // pad the row with zeros
-    for (uint32_t r = warp; r < nrows; r += TILE_WARPS) {
+    const uint32_t cparts = nrows ? max(1u, TILE_WARPS / nrows) : 1u;
+    const uint32_t cspan = ((jend - j0 + cparts - 1) / cparts + 1023) & ~1023u;   // columns per part
+    for (uint32_t t = warp; t < nrows * cparts; t += TILE_WARPS) {
+        const uint32_t r = t / cparts;
+        const uint32_t ja = j0 + (t % cparts) * cspan, jz = min(jend, ja + cspan);
         uint32_t *out = reinterpret_cast<uint32_t *>(pl.bits + (row0 + r) * pl.wpr);
         const uint32_t *raw = pl.raw_of_col;
         uint32_t jlim = min(pl.W, j1);
@@ -159,8 +172,8 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile(const TileArgs a) {
             jlim = __ldg(&pl.cW[cls]);
         }
         uint32_t keep = 0;
-        uint32_t k = 0;
-        for (uint32_t jb = j0; jb < jend; jb += 32, k++) {
+        uint32_t k = (ja - j0) / 32;
+        for (uint32_t jb = ja; jb < jz; jb += 32, k++) {
             const uint32_t j = jb + lane;
             uint32_t bit = 0;
             if (j < jlim) {
@@ -170,7 +183,7 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile(const TileArgs a) {
             const uint32_t word = __ballot_sync(0xffffffffu, bit);
             const uint32_t kk = k & 31;
             if (lane == kk) keep = word;
-            if (kk == 31 || jb + 32 >= jend) {
+            if (kk == 31 || jb + 32 >= jz) {
                 const uint32_t first = j0 / 32 + (k - kk);
                 if (lane <= kk) out[first + lane] = keep;
             }

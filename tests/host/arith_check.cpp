@@ -5,7 +5,7 @@
 // the solver's shared-reciprocal division; mode "r" checks the prime
 // generator's division-free R^2 mod p and (r M + s) mod p; mode "f" the walk's
 // first hit from the three-gap basis; mode "s" the walk's two steps from
-// Euclid's algorithm.
+// Euclid's algorithm; mode "l" the generator's lazily reduced Montgomery product.
 #include <cstdio>
 #include <cstdint>
 #include "../../paper_2012_03771_gb300/csrc/cs_arith.cuh"
@@ -21,6 +21,13 @@ int main(int argc, char **argv) {
             const uint32_t rt = cs::mont32_mul((uint32_t)r, r2, p32, pinv);
             printf("%u %u\n", r2, cs::mont32_affine(rt, M, (uint32_t)s, r2, p32, pinv));
         }
+        return 0;
+    }
+    if (argc > 1 && argv[1][0] == 'l') {
+        // "p a b" -> a b 2^-32 mod p reduced below 2p (a < 2p, b < 2^31)
+        unsigned long long p, a, b;
+        while (scanf("%llu %llu %llu", &p, &a, &b) == 3)
+            printf("%u\n", cs::mont32_mul_lazy((uint32_t)a, (uint32_t)b, (uint32_t)p, cs::mont32_neg_inv((uint32_t)p)));
         return 0;
     }
     if (argc > 1 && argv[1][0] == 's') {

@@ -129,3 +129,20 @@ def test_three_gap_steps_from_euclid(exe):
         assert ok64 and (a, da, b, ub) == want, (p, r, w)
         if p < (1 << 31):
             assert ok32 and (a2, da2, b2, ub2) == want, (p, r, w)
+
+
+def test_lazy_montgomery_product(exe):
+    """a b 2^-32 mod p kept below 2p for a < 2p, b < 2^31, odd p < 2^31 (the
+    generator's K mod p chain over factor words below 2^31)."""
+    rng = random.Random(23)
+    cases = []
+    for _ in range(20000):
+        p = rng.choice([3, 1009, 999999937, (1 << 31) - 1, rng.randrange(3, 1 << 31) | 1])
+        a = rng.choice([0, 2 * p - 1, rng.randrange(0, 2 * p)])
+        b = rng.choice([0, (1 << 31) - 1, rng.randrange(0, 1 << 31)])
+        cases.append((p, a, b))
+    inp = "".join(f"{p} {a} {b}\n" for p, a, b in cases)
+    out = subprocess.run([exe, "l"], input=inp, capture_output=True, text=True, check=True).stdout.split()
+    for (p, a, b), v in zip(cases, out):
+        v = int(v)
+        assert v < 2 * p and (v - a * b * pow(2, -32, p)) % p == 0, (p, a, b)

@@ -8,6 +8,7 @@
 // * The SplitMix64 finaliser (Steele, Lea and Flood, 2014) for the bitset
 //   checksum.
 #pragma once
+#include <math.h>
 #include <stdint.h>
 
 #if defined(__CUDACC__)
@@ -69,7 +70,7 @@ CS_HD uint32_t mont32_r2(uint32_t p) {
 // take the plain remainder): a Barrett-style reduction (P. Barrett, CRYPTO '86)
 // of n = 2^64 - 1 whose quotients are estimated with the correctly rounded
 // float reciprocal of p.  The first estimate of n / p <= 2^44 is off by less
-// than 2^22; its remainder, taken in wrapping 64-bit arithmetic, is exact as a
+// than 2^23; its remainder, taken in wrapping 64-bit arithmetic, is exact as a
 // signed value; two more estimates bring it into (-p, 2p), and two
 // corrections into [0, p).  Then R^2 = n + 1.
 CS_HD float rcp_rn(float x) {
@@ -79,14 +80,32 @@ CS_HD float rcp_rn(float x) {
     return 1.0f / x;
 #endif
 }
+// Conversions between 64-bit integers and float through 32-bit halves: on
+// this GPU the direct 64-bit conversions issue to the slow FP64 pipe.  The
+// value is rounded at most three times (relative error below 2^-22; the
+// halves of a magnitude are both non-negative, so they never cancel), and
+// f_to_u64 truncates exactly: for x >= 2^32 the part below 2^32 has at most 24
+// significant bits.
+CS_HD float u64_to_f(uint64_t n) {
+    return (float)(uint32_t)(n >> 32) * 4294967296.0f + (float)(uint32_t)n;
+}
+CS_HD float s64_to_f(int64_t n) {   // magnitude and sign: the halves must not cancel
+    const float f = u64_to_f((uint64_t)(n < 0 ? -n : n));
+    return n < 0 ? -f : f;
+}
+CS_HD uint64_t f_to_u64(float x) {   // 0 <= x < 2^64
+    const float hi = floorf(x * 2.3283064365386963e-10f);
+    return ((uint64_t)(uint32_t)hi << 32) + (uint32_t)(x - hi * 4294967296.0f);
+}
+
 CS_HD uint32_t mont32_r2_fast(uint32_t p) {
     if (p < (1u << 20)) return mont32_r2(p);
     const float fr = rcp_rn((float)p);
-    const uint64_t q0 = (uint64_t)(18446744073709551616.0f * fr);
+    const uint64_t q0 = f_to_u64(18446744073709551616.0f * fr);
     int64_t rem = (int64_t)(~0ull - q0 * (uint64_t)p);
     for (int pass = 0; pass < 2; pass++) {
-        const int64_t q = (int64_t)((float)rem * fr);
-        rem -= q * (int64_t)p;
+        const int32_t q = (int32_t)(s64_to_f(rem) * fr);   // |q| < 2^23
+        rem -= (int64_t)q * (int64_t)p;
     }
     if (rem < 0) rem += p;
     if (rem < 0) rem += p;
@@ -391,15 +410,15 @@ CS_HD bool tg_steps(UT p, UT r, UT w, UT &a, UT &da, UT &b, UT &ub, uint32_t &it
 }
 
 // floor(n / p) for n < 2^62, p < 2^31 and a quotient below 2^32, given
-// fr = rcp_rn(p): a float estimate of the quotient (off by less than 2^10),
+// fr = rcp_rn(p): a float estimate of the quotient (off by less than 2^11),
 // its exact remainder in 64-bit arithmetic, one refinement (off by at most
 // one) and two corrections each way.
 CS_HD uint64_t udiv64_est(uint64_t n, uint32_t p, float fr, int64_t &rem_out) {
-    uint64_t q = (uint64_t)((float)n * fr);
+    uint64_t q = f_to_u64(u64_to_f(n) * fr);
     int64_t rem = (int64_t)(n - q * p);
-    const int64_t q1 = (int64_t)((float)rem * fr);
-    rem -= q1 * (int64_t)p;
-    q += (uint64_t)q1;
+    const int32_t q1 = (int32_t)(s64_to_f(rem) * fr);      // |q1| < 2^12
+    rem -= (int64_t)q1 * (int64_t)p;
+    q += (uint64_t)(int64_t)q1;
     if (rem < 0) { rem += p; q--; }
     if (rem < 0) { rem += p; q--; }
     if (rem >= (int64_t)p) { rem -= p; q++; }

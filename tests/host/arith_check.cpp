@@ -5,7 +5,8 @@
 // the solver's shared-reciprocal division; mode "r" checks the prime
 // generator's division-free R^2 mod p and (r M + s) mod p; mode "f" the walk's
 // first hit from the three-gap basis; mode "s" the walk's two steps from
-// Euclid's algorithm; mode "l" the generator's lazily reduced Montgomery product.
+// Euclid's algorithm; mode "l" the generator's lazily reduced Montgomery
+// product; mode "u" the float-estimate division of 64-bit numerators.
 #include <cstdio>
 #include <cstdint>
 #include "../../paper_2012_03771_gb300/csrc/cs_arith.cuh"
@@ -20,6 +21,16 @@ int main(int argc, char **argv) {
             const uint32_t r2 = cs::mont32_r2_fast(p32);
             const uint32_t rt = cs::mont32_mul((uint32_t)r, r2, p32, pinv);
             printf("%u %u\n", r2, cs::mont32_affine(rt, M, (uint32_t)s, r2, p32, pinv));
+        }
+        return 0;
+    }
+    if (argc > 1 && argv[1][0] == 'u') {
+        // "n p" -> floor(n / p) and n mod p from the float-estimate division
+        unsigned long long n, p;
+        while (scanf("%llu %llu", &n, &p) == 2) {
+            int64_t rem = 0;
+            const uint64_t q = cs::udiv64_est(n, (uint32_t)p, cs::rcp_rn((float)p), rem);
+            printf("%llu %lld\n", (unsigned long long)q, (long long)rem);
         }
         return 0;
     }

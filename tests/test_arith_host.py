@@ -146,3 +146,22 @@ def test_lazy_montgomery_product(exe):
     for (p, a, b), v in zip(cases, out):
         v = int(v)
         assert v < 2 * p and (v - a * b * pow(2, -32, p)) % p == 0, (p, a, b)
+
+
+def test_float_estimate_division(exe):
+    """floor(n / p) and n mod p for n < 2^62, p < 2^31 and quotients below 2^32,
+    from a float reciprocal estimate with exact 64-bit correction."""
+    rng = random.Random(29)
+    cases = []
+    for _ in range(30000):
+        p = rng.choice([1, 2, 3, 7, (1 << 31) - 1, rng.randrange(1, 1 << 31), rng.randrange(1, 1 << 16)])
+        qmax = min((1 << 32) - 1, ((1 << 62) - 1) // p)
+        q = rng.choice([0, 1, qmax, rng.randrange(0, qmax + 1)])
+        n = q * p + rng.randrange(0, p)
+        if n < (1 << 62):
+            cases.append((n, p))
+    inp = "".join(f"{n} {p}\n" for n, p in cases)
+    out = subprocess.run([exe, "u"], input=inp, capture_output=True, text=True, check=True).stdout.split("\n")
+    for (n, p), line in zip(cases, out):
+        q, r = (int(x) for x in line.split())
+        assert (q, r) == (n // p, n % p), (n, p)

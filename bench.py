@@ -288,6 +288,10 @@ def run_cuda(args, params):
             "config": _config(params, args.config),
             "plan": _shape(info, tuned),
             "intervals_per_s": intervals_s,
+            # walk work per second: windows solved (two steps and the first hits per
+            # work item in the three-gap walk) and Euclid / solver passes
+            "solves_per_s": stats["solves"] * ws / (total_ms / args.steps / 1e3),
+            "levels_per_s": stats["levels"] * ws / (total_ms / args.steps / 1e3),
             "F_per_step": int(F_ref), "hash": f"{h_ref:#018x}",
             "stats": stats,
             "kernel_ms_per_step": {n: kern_ms[i] / args.steps for i, n in enumerate(KC_NAMES)},

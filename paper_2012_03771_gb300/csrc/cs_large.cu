@@ -192,7 +192,11 @@ struct TGItem {
 #ifndef CS_TG_STEPS
 #define CS_TG_STEPS 8
 #endif
-constexpr int TG_STEPS = CS_TG_STEPS;
+#ifndef CS_TG_STEPS_ALL_M
+#define CS_TG_STEPS_ALL_M CS_TG_STEPS
+#endif
+constexpr int TG_STEPS = CS_TG_STEPS;               // class walks (long walkers)
+constexpr int TG_STEPS_ALL_M = CS_TG_STEPS_ALL_M;   // every-m walks (the light chunks)
 constexpr int TG_WARPS = LARGE_THREADS / 32;
 
 // v + k r mod p for a small k (v, r < p, 2p fits in UT)
@@ -402,7 +406,8 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
         }
         // up to TG_STEPS three-distance steps per active lane between queue
         // checks (each step as selects)
-        for (int u = 0; u < TG_STEPS && active; u++) {
+        constexpr int STEPS = NC == 1 ? TG_STEPS_ALL_M : TG_STEPS;
+        for (int u = 0; u < STEPS && active; u++) {
             record_hit<UT>(pl, (uint64_t)moff, v, p, c);
             const bool down = v >= da;
             const bool up = v + ub <= w;

@@ -19,12 +19,20 @@ namespace cs {
 
 namespace {
 
-constexpr uint32_t SEG = 1u << 17;          // odd numbers per segment (maximum)
+// odd numbers per segment (maximum), and the base primes marked by a whole
+// warp (below) or one thread each (above)
+#ifndef CS_GEN_SEG_LOG
+#define CS_GEN_SEG_LOG 17
+#endif
+#ifndef CS_WARP_COOP_Q
+#define CS_WARP_COOP_Q 4096
+#endif
+constexpr uint32_t SEG = 1u << CS_GEN_SEG_LOG;
 constexpr uint32_t SEG_MIN = 1u << 12;      // smallest segment: 8 warps x 16-word batches
 constexpr uint32_t SEG_WORDS = SEG / 32;
 constexpr uint32_t GEN_THREADS = 256;
 constexpr uint32_t GEN_WARPS = GEN_THREADS / 32;
-constexpr uint32_t WARP_COOP_Q = 4096;      // q below this: marked by a whole warp
+constexpr uint32_t WARP_COOP_Q = CS_WARP_COOP_Q;
 constexpr uint32_t BATCH = 16;              // words scanned per warp step (lanes 0..15)
 constexpr uint32_t QCAP = BATCH * 32 + 32;  // per-warp queue (odd indices within the segment)
 

@@ -84,14 +84,15 @@ typedef struct {
                                 N + x small enough to be a prime of d, phi(d) <= 4096 and an
                                 interval whose tile fits in one piece (SL up to about 3.7e5).
                                 F and the per-row counts are the same in both layouts. */
-    uint32_t m_classes;      /* three-gap walk over m: 0 = automatic (chunks whose primes have
-                                at least 24 expected hits walk only the m = 1, 5 (mod 6) when
-                                6 | d, the odd m when 2 | d, since the others are never rows);
-                                1 = every m; 2 = the classes in every chunk */
+    uint32_t m_classes;      /* three-gap walk over m (the m sharing a factor with d are never
+                                rows): 0 = automatic (chunks whose primes have at least 48
+                                expected hits walk only the m = 1, 5 (mod 6) when 6 | d, the
+                                other chunks the odd m when 2 | d); 1 = every m; 2 = the
+                                widest classes (mod 6, else mod 2) in every chunk */
     uint32_t item_hits;      /* three-gap walk: expected walked hits per work item (prime,
                                 m-segment); 0 = automatic (128) */
     uint32_t class_min_hits; /* m_classes = 0: expected hits per prime (every m) from which a
-                                chunk walks only the m-classes; 0 = automatic (24) */
+                                chunk walks only the m-classes; 0 = automatic (48) */
     uint32_t reserved[3];
 } cs_tuning;
 
@@ -114,9 +115,11 @@ typedef struct {
                                   GB300), used to order instances in a batch */
     uint32_t layout;           /* 0 literal, 1 compact */
     uint32_t n_classes;        /* compact: residue classes of m mod d (phi(d)), else 1 */
-    uint32_t m_mod;            /* Q of the walk's m-classes (1: every m is walked) */
-    uint32_t m_walked;         /* classes of m mod Q walked (1 or 2) */
-    uint64_t split_chunks;     /* large-prime chunks that walk only those classes */
+    uint32_t m_mod;            /* Q of the m-classes of the chunks with many hits per prime
+                                  (1: every m is walked) */
+    uint32_t m_walked;         /* classes of m mod Q those chunks walk (1 or 2) */
+    uint64_t split_chunks;     /* large-prime chunks that walk those classes (the others walk
+                                  the odd m when 2 | d) */
 } cs_info_t;
 
 typedef struct {

@@ -98,8 +98,10 @@ struct cs_plan_s {
     std::vector<int64_t> x_of_col;
     std::vector<std::pair<uint64_t, uint64_t>> chunks;    // large-prime ranges (lo, hi]
     std::vector<uint32_t> chunk_seg;                      // m-segments per prime, per chunk
-    std::vector<uint8_t> chunk_split;                     // walk only the m-classes, per chunk
-    MClasses mcls{1, 1, {0, 0}};                          // m-classes of the walk
+    std::vector<MClasses> chunk_mc;                       // m-classes each chunk walks
+    MClasses mcls{1, 1, {0, 0}};                          // classes of the chunks with many hits
+    MClasses mcls_light{1, 1, {0, 0}};                    // classes of the other chunks
+    uint64_t split_chunks = 0;                            // chunks that walk mcls
     uint64_t large_cap = 0, small_cap = 0, est_cost = 0;
     int large_grid = 0;
     uint64_t h2d = 0, dev_bytes = 0;
@@ -413,29 +415,31 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
     // chunk_numbers wide; a chunk's primes are split into n_seg m-segments of
     // about HITS_PER_ITEM expected hits each
     const uint64_t chunk = pl->tune.chunk_numbers ? pl->tune.chunk_numbers : (1ull << 27);
-    // m-classes: rows need gcd(m, d) = 1, so with Q = 6 (or 2) dividing d the
-    // walk can skip the m = 0, 2, 3, 4 (mod 6) (or the even m).  Each walked
-    // class costs one more window in the item's fused solve, so a chunk walks
-    // the classes only when its primes have enough hits to repay it.
+    // m-classes: rows need gcd(m, d) = 1, so with 2 | d the walk can skip the
+    // even m, and with 6 | d the m = 0, 2, 3, 4 (mod 6).  The odd m are one
+    // walker per work item (half the hits for the same setup); m = 1, 5 (mod 6)
+    // are two walkers (a third of the hits, one more first hit and queue entry),
+    // taken only by chunks whose primes have enough hits to repay the second.
     if (pl->tune.m_classes > 2) return fail(CS_EINVAL, "m_classes must be 0, 1 or 2");
     if (pl->mode == LARGE_THREE_GAP && SL > 0 && pl->tune.m_classes != 1) {
-        const uint32_t Q = d % 6 == 0 ? 6 : (d % 2 == 0 ? 2 : 1);
-        const uint32_t ms = (uint32_t)(M_start % Q);
-        if (Q == 6) pl->mcls = MClasses{6, 2, {(1 + 6 - ms) % 6, (5 + 6 - ms) % 6}};
-        if (Q == 2) pl->mcls = MClasses{2, 1, {(1 + 2 - ms) % 2, 0}};
+        const uint32_t m6 = (uint32_t)(M_start % 6), m2 = (uint32_t)(M_start % 2);
+        if (d % 2 == 0) pl->mcls_light = pl->mcls = MClasses{2, 1, {(1 + 2 - m2) % 2, 0}};
+        if (d % 6 == 0) pl->mcls = MClasses{6, 2, {(1 + 6 - m6) % 6, (5 + 6 - m6) % 6}};
     }
     // expected hits per prime (every m) at a chunk's low end from which it walks
     // the classes, and walked hits per work item
-    const double SPLIT_MIN_HITS = pl->tune.class_min_hits ? (double)pl->tune.class_min_hits : 24.0;
+    const double SPLIT_MIN_HITS = pl->tune.class_min_hits ? (double)pl->tune.class_min_hits : 48.0;
     const double HITS_PER_ITEM = pl->tune.item_hits ? (double)pl->tune.item_hits : 128.0;
     auto split_for = [&](uint64_t lo) -> bool {
         if (pl->mcls.Q == 1) return false;
         if (pl->tune.m_classes == 2) return true;
         return (double)M_inc * (double)S / (double)std::max<uint64_t>(lo, 1) >= SPLIT_MIN_HITS;
     };
+    auto classes_for = [&](uint64_t lo) -> MClasses { return split_for(lo) ? pl->mcls : pl->mcls_light; };
     auto segs_for = [&](uint64_t lo) {
         double hits = (double)M_inc * (double)S / (double)std::max<uint64_t>(lo, 1);
-        if (split_for(lo)) hits *= (double)pl->mcls.n / (double)pl->mcls.Q;
+        const MClasses mc = classes_for(lo);
+        hits *= (double)mc.n / (double)mc.Q;
         double seg = std::min<double>(std::max(1.0, std::ceil(hits / HITS_PER_ITEM)), (double)std::max<uint64_t>(M_inc, 1));
         return (uint32_t)std::min(seg, 65536.0);
     };
@@ -453,7 +457,8 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
             const uint64_t lo = std::max(ch.lo, T), hi = std::min(ch.hi, L);
             pl->chunks.push_back({lo, hi});
             pl->chunk_seg.push_back(segs_for(lo));
-            pl->chunk_split.push_back(split_for(lo));
+            pl->chunk_mc.push_back(classes_for(lo));
+            pl->split_chunks += split_for(lo);
             pl->cache_idx.push_back(k);
         }
         pl->large_cap = 0;
@@ -462,14 +467,15 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
             uint64_t hi = std::min<uint64_t>({L, lo + std::max<uint64_t>(lo, 1), lo + chunk});
             pl->chunks.push_back({lo, hi});
             pl->chunk_seg.push_back(segs_for(lo));
-            pl->chunk_split.push_back(split_for(lo));
+            pl->chunk_mc.push_back(classes_for(lo));
+            pl->split_chunks += split_for(lo);
             widest = std::max(widest, hi - lo);
             lo = hi;
         }
         pl->large_cap = pl->chunks.empty() ? 0 : primes_in_interval_bound(widest);
     }
     pl->small_cap = pl->small_hi > P ? prime_count_bound(pl->small_hi) : 0;
-    pl->large_grid = pl->tune.large_grid ? (int)pl->tune.large_grid : sm_count() * 8;
+    pl->large_grid = (int)pl->tune.large_grid;   // 0: the launcher picks (one wave of resident CTAs)
 
     // tile shape: up to 32 rows of raw offsets in shared memory
     int dev = 0, optin = 0;
@@ -752,8 +758,7 @@ cs_status cs_sieve(cs_plan_t pl, void *stream) {
             CS_CUDA(cudaStreamWaitEvent(st, ch.ready, 0));
             if ((s = prof.begin(KC_LARGE))) return s;
             CS_CUDA(launch_large(dp, ch.narrow, pl->mode, ch.p, ch.r, nullptr, ch.count, ch.cap,
-                                 pl->chunk_seg[c], pl->large_grid, st, pl->T, pl->L,
-                                 pl->chunk_split[c] ? pl->mcls : MClasses{1, 1, {0, 0}}));
+                                 pl->chunk_seg[c], pl->large_grid, st, pl->T, pl->L, pl->chunk_mc[c]));
             if ((s = prof.end())) return s;
         }
     }
@@ -767,7 +772,7 @@ cs_status cs_sieve(cs_plan_t pl, void *stream) {
         if ((s = prof.begin(KC_LARGE))) return s;
         CS_CUDA(launch_large(dp, pl->narrow, pl->mode, pl->d_lp, pl->d_lr, pl->d_lv, cnt,
                              pl->large_cap, pl->chunk_seg[c], pl->large_grid, st, 0, ~0ull,
-                             pl->chunk_split[c] ? pl->mcls : MClasses{1, 1, {0, 0}}));
+                             pl->chunk_mc[c]));
         if ((s = prof.end())) return s;
     }
     if ((s = prof.begin(KC_FINAL))) return s;
@@ -824,8 +829,7 @@ cs_status cs_info(cs_plan_t pl, cs_info_t *out) {
     out->n_classes = pl->n_cls;
     out->m_mod = pl->mcls.Q;
     out->m_walked = pl->mcls.n;
-    out->split_chunks = 0;
-    for (uint8_t f : pl->chunk_split) out->split_chunks += f;
+    out->split_chunks = pl->split_chunks;
     if (pl->layout == 1) out->W = pl->Wc_max;
     return CS_OK;
 }

@@ -194,33 +194,6 @@ CS_HD uint64_t udiv(uint64_t a, uint64_t b) {
     return a / b;
 }
 
-// Quotients by one divisor d, taken several times (T. Granlund and P. L.
-// Montgomery, "Division by invariant integers using multiplication", PLDI
-// 1994): with v = floor((2^32 - 1) / d), a*v / 2^32 lies in (a/d - 1, a/d], so
-// q = floor(a*v / 2^32) is floor(a/d) or one less, and one comparison of the
-// remainder settles it.  One division per divisor instead of one per quotient.
-template <class UT>
-struct Divisor;
-template <>
-struct Divisor<uint32_t> {
-    uint32_t d, v;
-    CS_HD explicit Divisor(uint32_t d_) : d(d_), v(0xffffffffu / d_) {}
-    CS_HD uint32_t div(uint32_t a) const {
-#if defined(__CUDA_ARCH__)
-        uint32_t q = __umulhi(a, v);
-#else
-        uint32_t q = (uint32_t)(((uint64_t)a * v) >> 32);
-#endif
-        return q + (a - q * d >= d);
-    }
-};
-template <>
-struct Divisor<uint64_t> {
-    uint64_t d;
-    CS_HD explicit Divisor(uint64_t d_) : d(d_) {}
-    CS_HD uint64_t div(uint64_t a) const { return udiv(a, d); }
-};
-
 // ----------------------------------------------------------- G(p, K, L, R)
 //
 // Smallest m >= 0 with L <= m*K mod p <= L + w (Eq. modfunc), for 0 < K < p,
@@ -284,80 +257,6 @@ CS_HD bool g_solve(UT p, UT K, UT L, UT w, UT &m_out, UT &y_out, uint32_t &iters
         L = L - f * np;                                // L mod K
     }
     return false;
-}
-
-// Several windows [L_i, L_i + w_i] for the same (p, K) in one pass.  Cases D
-// and E, and so the chain of sub-problems (p_k, K_k), the lattice vectors
-// (U, u) and the sign s, depend only on (p, K); the windows differ only in
-// where case C stops them and in their own A, B and L.  Running them together
-// shares the chain's division per pass.  Returns false if max_iter passes were
-// not enough.  Windows with L_i = 0 are answered by case a (m = 0).
-template <class UT, class ST, int NW>
-CS_HD bool g_solve_multi(UT p, UT K, const UT (&L0)[NW], const UT (&w)[NW], UT (&m_out)[NW],
-                         UT (&y_out)[NW], uint32_t &iters, uint32_t max_iter) {
-    UT L[NW];
-    ST A[NW], B[NW];
-    bool open[NW];
-    int n_open = 0;
-#pragma unroll
-    for (int i = 0; i < NW; i++) {
-        L[i] = L0[i];
-        A[i] = 0;
-        B[i] = 0;
-        open[i] = L0[i] != 0;
-        m_out[i] = 0;
-        y_out[i] = 0;
-        n_open += open[i];
-    }
-    ST U = 0, u = 1, s = 1;
-    for (uint32_t it = 0; it < max_iter && n_open; it++) {
-        iters++;
-        const Divisor<UT> byK(K);                                // every quotient of this pass is by K
-        UT c[NW];
-#pragma unroll
-        for (int i = 0; i < NW; i++) {
-            c[i] = 0;
-            if (!open[i]) continue;
-            c[i] = byK.div((UT)(L[i] + K - 1));                 // ceil(L/K)
-            const UT ck = c[i] * K;
-            if (ck <= L[i] + w[i]) {                             // case C
-                y_out[i] = (UT)(A[i] + s * (ST)ck);
-                m_out[i] = (UT)(B[i] + s * (ST)c[i] * u);
-                open[i] = false;
-                n_open--;
-            }
-        }
-        if (!n_open) return true;
-        if (2 * K >= p) {                                        // case D
-#pragma unroll
-            for (int i = 0; i < NW; i++) {
-                if (!open[i]) continue;
-                A[i] += s * (ST)p;
-                B[i] += s * U;
-                L[i] = p - (L[i] + w[i]);
-            }
-            s = -s;
-            u = U - u;
-            K = p - K;
-            continue;
-        }
-        const UT q = byK.div((UT)(p + K - 1));                   // case E: ceil(p/K)
-#pragma unroll
-        for (int i = 0; i < NW; i++) {
-            if (!open[i]) continue;
-            const UT f = c[i] - 1;                               // floor(L/K)
-            A[i] += s * (ST)(f * K);
-            B[i] += s * (ST)f * u;
-            L[i] = L[i] - f * K;                                 // L mod K
-        }
-        const ST nu = (ST)q * u - U;
-        U = u;
-        u = nu;
-        const UT np = K;
-        K = q * K - p;
-        p = np;
-    }
-    return n_open == 0;
 }
 
 // The two steps of the three-gap walk from one run of Euclid's algorithm.
@@ -479,6 +378,60 @@ CS_HD uint32_t first_hit32(uint32_t p, float fr, uint32_t w, uint32_t a, uint32_
     const uint32_t y = (uint32_t)(Y - i * (int64_t)DA);
     y_out = sw ? w - y : y;
     return (uint32_t)(i * A + j * (int64_t)B);
+}
+
+// floor(n / d) for |n / d| < 2^42, 0 < d < 2^41 (n, d as below), given
+// fr = rcp_rn(d): a float estimate of the quotient (off by less than 2^19),
+// the exact remainder (128-bit, then below 2^61 in magnitude), two refinements
+// and two corrections each way.
+CS_HD float s128_to_f(__int128 n) {
+    const unsigned __int128 m = (unsigned __int128)(n < 0 ? -n : n);
+    const float f = u64_to_f((uint64_t)(m >> 64)) * 18446744073709551616.0f + u64_to_f((uint64_t)m);
+    return n < 0 ? -f : f;
+}
+CS_HD int64_t f_to_s64(float x) {   // |x| < 2^63, truncated toward zero
+    const uint64_t m = f_to_u64(x < 0 ? -x : x);
+    return x < 0 ? -(int64_t)m : (int64_t)m;
+}
+CS_HD int64_t floor_div_est(__int128 n, uint64_t d, float fr) {
+    int64_t q = f_to_s64(s128_to_f(n) * fr);
+    int64_t rem = (int64_t)(n - (__int128)q * (__int128)d);
+    for (int pass = 0; pass < 2; pass++) {
+        const int64_t q1 = f_to_s64(s64_to_f(rem) * fr);
+        q += q1;
+        rem -= q1 * (int64_t)d;
+    }
+    if (rem < 0) { rem += d; q--; }
+    if (rem < 0) { rem += d; q--; }
+    if (rem >= (int64_t)d) { rem -= d; q++; }
+    if (rem >= (int64_t)d) { rem -= d; q++; }
+    return q;
+}
+
+// first_hit32 for 64-bit primes: p < 2^40, w <= 2^21 (SL <= 2^20).  Bounds:
+// |V0| < 2^40 and A < 2^40, so V0 A < 2^80 (128-bit) with quotient J below
+// 2^40; |Y| < 2^41 (quotients by DA below 2^41); products i A, j B below 2^81
+// (128-bit); the block's last point is at most (w / DA + 1) A < 2^61 past its
+// first, so the steps to t >= 0 fit in 64 bits.
+CS_HD uint64_t first_hit64(uint64_t p, uint64_t w, uint64_t a, uint64_t da, uint64_t b, uint64_t ub,
+                           uint64_t v0, uint64_t &y_out) {
+    const bool sw = da > ub;
+    const uint64_t A = sw ? b : a, DA = sw ? ub : da, B = sw ? a : b, UB = sw ? da : ub;
+    const int64_t V0 = sw ? (int64_t)w - (int64_t)v0 : (int64_t)v0;
+    const float fp = rcp_rn((float)p), fda = rcp_rn((float)DA);
+    // first block: J = -floor(V0 A / p)
+    int64_t j = -floor_div_est((__int128)V0 * (__int128)A, p, fp);
+    int64_t Y = V0 + j * (int64_t)UB;
+    if ((__int128)floor_div_est(Y, DA, fda) * A + (__int128)j * B < 0) {
+        j++;
+        Y += (int64_t)UB;
+    }
+    int64_t i = -floor_div_est((int64_t)w - Y, DA, fda);                 // ceil((Y - w) / DA)
+    const __int128 t_lo = (__int128)i * A + (__int128)j * B;
+    if (t_lo < 0) i += -floor_div_est(t_lo, A, rcp_rn((float)A));     // ceil(-t_lo / A) steps
+    const uint64_t y = (uint64_t)(Y - i * (int64_t)DA);
+    y_out = sw ? w - y : y;
+    return (uint64_t)((__int128)i * A + (__int128)j * B);
 }
 
 // ------------------------------------------------------------- checksum

@@ -18,6 +18,8 @@
 //
 // Each hit on a coprime m and a stored x clears one bit of the device bitset
 // with a 32-bit atomic AND and counts one enumerated factor.
+#include <atomic>
+
 #include "cs_arith.cuh"
 #include "cs_internal.h"
 
@@ -70,7 +72,6 @@ struct Counters {
 // per-word prefix counts) that stay in L1.
 template <class UT>
 __device__ __forceinline__ void record_hit(const DevPlan &pl, uint64_t moff, UT v, UT p, Counters &c) {
-    c.hits++;
     const uint32_t z = 2 * pl.SL - (uint32_t)v;          // raw offset x + SL
     const uint2 rt = __ldg(&pl.row_tab[moff >> 5]);      // {coprime-m mask, rows before}
     const uint2 ct = __ldg(&pl.col_tab[z >> 5]);         // {stored-x mask, columns before}
@@ -130,6 +131,7 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_large(const LargeArgs a) {
             uint64_t m = 0;
             while (true) {
                 if (v <= w) {
+                    c.hits++;
                     record_hit<UT>(pl, m_lo + m, v, p, c);
                     if (++m >= Mseg) break;
                     v += r;
@@ -179,8 +181,7 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_large(const LargeArgs a) {
 // (Q = 2).  The two steps come from one run of Euclid's algorithm on (p, r')
 // (tg_steps, the same answers as G for the two step windows); in the 32-bit
 // walk the first hits follow from the two step vectors, a basis of the lattice
-// of (j, r' j mod p) (first_hit32), and the 64-bit walk solves them as windows
-// of one fused G.
+// of (j, r' j mod p) (first_hit32; first_hit64 in the 64-bit walk).
 template <class UT, class ST, class MT>
 struct TGItem {
     MT moff, end;      // current m - M_start, end of the segment
@@ -250,8 +251,11 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
     uint64_t batch = warp_id;          // next batch of 32 items to prepare
     uint32_t qhead = 0, qcount = 0;    // warp-uniform ring state
     bool active = false;
-    MT moff = 0, end = 0, ma = 0, mb = 0;
-    UT v = 0, p = 1, da = 0, ub = 0;
+    // walker: m offset, segment end, residue v, and the three steps precomputed:
+    // down (v >= d_a): m += a, v -= d_a; up (v <= 2SL - u_b): m += b, v += u_b;
+    // else m += a + b, v += u_b - d_a
+    MT moff = 0, end = 0, ma = 0, mb = 0, mab = 0;
+    UT v = 0, p = 1, da = 0, ub = 0, nda = 0, ubd = 0, wmub = 0;
 
     while (true) {
         // refill: prepare 32 items when the queue can take their walkers
@@ -338,20 +342,13 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
                             }
                         }
                     } else if (ok && n_first) {
-                        // 64-bit: the first hits as windows of one fused solve
-                        UT Lw[NC], Ww[NC], mw[NC], yw[NC];
-#pragma unroll
-                        for (int k = 0; k < NC; k++) {
-                            Lw[k] = vk[k] > w ? (UT)(pp - vk[k]) : (UT)0;   // L = 0: m = 0 (case a)
-                            Ww[k] = w;
-                        }
-                        ok = g_solve_multi<UT, ST, NC>(pp, rq, Lw, Ww, mw, yw, it, max_iter);
-                        if (!ok) c.err |= ERR_SOLVER_LIMIT;
+                        // 64-bit (p < 2^40, 2SL <= 2^21): the same from first_hit64
 #pragma unroll
                         for (int k = 0; k < NC; k++) {
                             if (vk[k] > w) {
-                                first[k] = (uint64_t)mw[k] * Q;
-                                vk[k] = (UT)(vk[k] + yw[k] - pp);
+                                uint64_t y;
+                                first[k] = first_hit64(pp, w, ma_, da_, mb_, ub_, vk[k], y) * Q;
+                                vk[k] = (UT)y;
                             }
                         }
                     }
@@ -398,6 +395,10 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
                 const TGItem<UT, ST, MT> e = q[(qhead + rank) % QCAP];
                 moff = e.moff; end = e.end; v = e.v; p = e.p; da = e.da; ub = e.ub;
                 ma = e.ma; mb = e.mb;
+                mab = ma + mb;                       // ma, mb <= M_inc < 2^31
+                nda = (UT)0 - da;
+                ubd = ub - da;                       // both wrap; v ends in [0, 2SL]
+                wmub = w - ub;
                 active = true;
             }
             qhead = (qhead + take) % QCAP;
@@ -412,16 +413,17 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
         // up to TG_STEPS three-distance steps per active lane between queue
         // checks (each step as selects)
         constexpr int STEPS = NC == 1 ? TG_STEPS_ALL_M : TG_STEPS;
-        for (int u = 0; u < STEPS && active; u++) {
+        int u = 0;
+        for (; u < STEPS && active; u++) {
             record_hit<UT>(pl, (uint64_t)moff, v, p, c);
             const bool down = v >= da;
-            const bool up = v + ub <= w;
-            const UT vd = v - da, vu = v + ub;
-            v = down ? vd : (up ? vu : (UT)(vu - da));
-            const MT step = down ? ma : (up ? mb : (MT)(ma + mb));
+            const bool up = v <= wmub;
+            v += down ? nda : (up ? ub : ubd);
+            const MT step = down ? ma : (up ? mb : mab);
             active = step < end - moff;
             moff += step;
         }
+        c.hits += u;                                 // one hit per step taken
     }
 
     const unsigned long long F = warp_sum(c.F), hits = warp_sum(c.hits);
@@ -459,7 +461,29 @@ cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p
                          int grid, cudaStream_t stream, uint64_t p_lo, uint64_t p_hi, MClasses mc) {
     if (mc.Q == 0 || mc.n < 1 || mc.n > 2 || mc.n > mc.Q || pl.SL == 0) mc = MClasses{1, 1, {0, 0}};
     LargeArgs a{pl, p, r, v, count, cap, n_seg ? n_seg : 1, p_lo, p_hi, mc};
-    if (grid <= 0) grid = sm_count() * 8;
+    // the three-gap walk's lanes are persistent: by default one wave of
+    // resident CTAs (a partial last wave left SMs idle: 3% slower measured);
+    // the paper's walk takes eight CTAs per SM
+    if (grid <= 0) {
+        grid = sm_count() * 8;
+        if (mode != LARGE_PAPER) {
+            static std::atomic<int> resident[2][2];   // [narrow][NC - 1], looked up once
+            std::atomic<int> &cached = resident[narrow ? 1 : 0][mc.n == 2 ? 1 : 0];
+            int per_sm = cached.load(std::memory_order_relaxed);
+            if (per_sm == 0) {
+                cudaError_t e;
+                if (narrow)
+                    e = mc.n == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_large_tg<uint32_t, int32_t, uint32_t, 2>, LARGE_THREADS, 0)
+                                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_large_tg<uint32_t, int32_t, uint32_t, 1>, LARGE_THREADS, 0);
+                else
+                    e = mc.n == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_large_tg<uint64_t, int64_t, uint32_t, 2>, LARGE_THREADS, 0)
+                                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_large_tg<uint64_t, int64_t, uint32_t, 1>, LARGE_THREADS, 0);
+                if (e != cudaSuccess || per_sm <= 0) per_sm = -1;
+                cached.store(per_sm, std::memory_order_relaxed);
+            }
+            if (per_sm > 0) grid = sm_count() * per_sm;
+        }
+    }
     // m - M_start < M_inc < 2^31: 32-bit m offsets in both widths
     if (narrow) {
         if (mode == LARGE_PAPER)

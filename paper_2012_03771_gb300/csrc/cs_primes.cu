@@ -29,6 +29,13 @@ namespace {
 #ifndef CS_WARP_COOP_Q
 #define CS_WARP_COOP_Q 1024
 #endif
+// grid of the generator: CTAs per SM, and segments per CTA it is sized for
+#ifndef CS_GEN_GRID_PER_SM
+#define CS_GEN_GRID_PER_SM 8
+#endif
+#ifndef CS_GEN_SEGS_PER_CTA
+#define CS_GEN_SEGS_PER_CTA 1
+#endif
 constexpr uint32_t SEG = 1u << CS_GEN_SEG_LOG;
 constexpr uint32_t SEG_MIN = 1u << 12;      // smallest segment: 8 warps x 16-word batches
 constexpr uint32_t SEG_WORDS = SEG / 32;
@@ -350,10 +357,10 @@ GenArgs make_args(uint64_t lo, uint64_t hi, const uint32_t *base, uint32_t n_bas
     }
     a.i_begin = (lo + 1) / 2;
     a.i_end = (hi + 1) / 2;
-    // segment size: enough segments for every SM to get several, within
-    // [SEG_MIN, SEG]
+    // segment size: enough segments for every CTA of the grid to get
+    // CS_GEN_SEGS_PER_CTA of them, within [SEG_MIN, SEG]
     const uint64_t odds = a.i_end > a.i_begin ? a.i_end - a.i_begin : 0;
-    uint64_t want = odds / ((uint64_t)sm_count() * 8);
+    uint64_t want = odds / ((uint64_t)sm_count() * CS_GEN_GRID_PER_SM * CS_GEN_SEGS_PER_CTA);
     uint32_t seg = SEG_MIN;
     while (seg < SEG && seg < want) seg *= 2;
     a.seg = seg;
@@ -363,7 +370,7 @@ GenArgs make_args(uint64_t lo, uint64_t hi, const uint32_t *base, uint32_t n_bas
 }
 
 int gen_grid(uint64_t n_seg) {
-    uint64_t g = (uint64_t)sm_count() * 8;
+    uint64_t g = (uint64_t)sm_count() * CS_GEN_GRID_PER_SM;
     if (n_seg < g) g = n_seg;
     return (int)(g ? g : 1);
 }

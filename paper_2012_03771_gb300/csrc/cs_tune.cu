@@ -106,7 +106,7 @@ extern "C" cs_status cs_autotune(uint32_t P, uint64_t d, uint64_t M_start, uint6
         // proxy: same K and interval, fewer m, lower limit
         const uint64_t pM = std::min<uint64_t>(M_inc, 100000), pL = std::min<uint64_t>(L, 1000000000ull);
         const uint64_t mults_x100[] = {200, 250, 300, 400, 500, 600, 800, 1000, 1200, 1600};
-        const uint32_t rows[] = {16, 32};
+        const uint32_t rows[] = {8, 16, 32};
         cudaStream_t st;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
             return set_error(CS_EDEVICE, "cudaStreamCreate");

@@ -1,12 +1,11 @@
 // Host build of the kernels' integer arithmetic (cs_arith.cuh) for CPU tests:
-// reads "p K L R" lines, prints "m y" from g_solve (32- or 64-bit), from
-// g_solve_multi with the window in one of three slots and, 32-bit, in the last
-// of four slots.  Mode "q" reads "a d" lines and prints the 32-bit quotient of
-// the solver's shared-reciprocal division; mode "r" checks the prime
-// generator's division-free R^2 mod p and (r M + s) mod p; mode "f" the walk's
+// reads "p K L R" lines, prints "m y" from g_solve (32- or 64-bit).  Mode "r"
+// checks the prime generator's division-free R^2 mod p and (r M + s) mod p;
+// mode "f" the walk's
 // first hit from the three-gap basis; mode "s" the walk's two steps from
 // Euclid's algorithm; mode "l" the generator's lazily reduced Montgomery
-// product; mode "u" the float-estimate division of 64-bit numerators.
+// product; mode "u" the float-estimate division of 64-bit numerators; mode "F"
+// the first hit for 64-bit primes.
 #include <cstdio>
 #include <cstdint>
 #include "../../paper_2012_03771_gb300/csrc/cs_arith.cuh"
@@ -21,6 +20,19 @@ int main(int argc, char **argv) {
             const uint32_t r2 = cs::mont32_r2_fast(p32);
             const uint32_t rt = cs::mont32_mul((uint32_t)r, r2, p32, pinv);
             printf("%u %u\n", r2, cs::mont32_affine(rt, M, (uint32_t)s, r2, p32, pinv));
+        }
+        return 0;
+    }
+    if (argc > 1 && argv[1][0] == 'F') {
+        // "p r w v0" -> first hit from the three-gap basis, 64-bit (p < 2^40)
+        unsigned long long p, r, w, v0;
+        while (scanf("%llu %llu %llu %llu", &p, &r, &w, &v0) == 4) {
+            uint64_t a, da, b, ub;
+            uint32_t it = 0;
+            bool ok = cs::tg_steps<uint64_t>(p, r, w, a, da, b, ub, it, 400);
+            uint64_t y = 0;
+            const uint64_t t = cs::first_hit64(p, w, a, da, b, ub, v0, y);
+            printf("%d %llu %llu\n", ok, (unsigned long long)t, (unsigned long long)y);
         }
         return 0;
     }
@@ -60,20 +72,13 @@ int main(int argc, char **argv) {
         // "p r w v0" -> first t >= 0 with (v0 + r t) mod p <= w from the three-gap basis
         unsigned long long p, r, w, v0;
         while (scanf("%llu %llu %llu %llu", &p, &r, &w, &v0) == 4) {
-            const uint32_t Ls[2] = {(uint32_t)(p - w), 1u}, Ws[2] = {(uint32_t)(w - 1), (uint32_t)(w - 1)};
-            uint32_t ms[2], ys[2], it = 0;
-            bool ok = cs::g_solve_multi<uint32_t, int32_t, 2>((uint32_t)p, (uint32_t)r, Ls, Ws, ms, ys, it, 200);
+            uint32_t a, da, b, ub, it = 0;
+            bool ok = cs::tg_steps<uint32_t>((uint32_t)p, (uint32_t)r, (uint32_t)w, a, da, b, ub, it, 200);
             uint32_t y = 0;
-            const uint32_t t = cs::first_hit32((uint32_t)p, cs::rcp_rn((float)p), (uint32_t)w, ms[0],
-                                               (uint32_t)(p - ys[0]), ms[1], ys[1], (uint32_t)v0, y);
+            const uint32_t t = cs::first_hit32((uint32_t)p, cs::rcp_rn((float)p), (uint32_t)w, a, da, b, ub,
+                                               (uint32_t)v0, y);
             printf("%d %u %u\n", ok, t, y);
         }
-        return 0;
-    }
-    if (argc > 1 && argv[1][0] == 'q') {
-        unsigned long long a, d;
-        while (scanf("%llu %llu", &a, &d) == 2)
-            printf("%u\n", cs::Divisor<uint32_t>((uint32_t)d).div((uint32_t)a));
         return 0;
     }
     unsigned long long p, K, L, R;
@@ -83,24 +88,11 @@ int main(int argc, char **argv) {
             uint32_t m = 0, y = 0;
             bool ok = cs::g_solve<uint32_t, int32_t>((uint32_t)p, (uint32_t)(K % p), (uint32_t)L,
                                                      (uint32_t)(R - L), m, y, it, 200);
-            const uint32_t Ls[3] = {(uint32_t)L, 1, (uint32_t)(p - 1)};
-            const uint32_t Ws[3] = {(uint32_t)(R - L), 0, 0};
-            uint32_t ms[3], ys[3];
-            bool ok2 = cs::g_solve_multi<uint32_t, int32_t, 3>((uint32_t)p, (uint32_t)(K % p), Ls, Ws, ms, ys, it, 200);
-            const uint32_t L4[4] = {(uint32_t)(p - 1), 1, 0, (uint32_t)L};
-            const uint32_t W4[4] = {0, 0, 0, (uint32_t)(R - L)};
-            uint32_t m4[4], y4[4];
-            bool ok4 = cs::g_solve_multi<uint32_t, int32_t, 4>((uint32_t)p, (uint32_t)(K % p), L4, W4, m4, y4, it, 200);
-            printf("%d %u %u %d %u %u %d %u %u\n", ok, m, y, ok2, ms[0], ys[0], ok4, m4[3], y4[3]);
+            printf("%d %u %u\n", ok, m, y);
         } else {
             uint64_t m = 0, y = 0;
             bool ok = cs::g_solve<uint64_t, int64_t>(p, K % p, L, R - L, m, y, it, 300);
-            const uint64_t Ls[3] = {1, L, p - 1};
-            const uint64_t Ws[3] = {0, R - L, 0};
-            uint64_t ms[3], ys[3];
-            bool ok2 = cs::g_solve_multi<uint64_t, int64_t, 3>(p, K % p, Ls, Ws, ms, ys, it, 300);
-            printf("%d %llu %llu %d %llu %llu\n", ok, (unsigned long long)m, (unsigned long long)y, ok2,
-                   (unsigned long long)ms[1], (unsigned long long)ys[1]);
+            printf("%d %llu %llu\n", ok, (unsigned long long)m, (unsigned long long)y);
         }
     }
     return 0;

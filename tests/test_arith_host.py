@@ -20,7 +20,7 @@ def exe(tmp_path_factory):
 
 
 @pytest.mark.parametrize("narrow", [True, False])
-def test_g_solve_and_multi_match_paper_recursion(exe, narrow):
+def test_g_solve_matches_paper_recursion(exe, narrow):
     rng = random.Random(7 + narrow)
     pool = [7, 101, 7919, 1000003, 999999937, (1 << 30) - 35] if narrow else \
            [7, 1000003, 4294967291, 68719476731, 1099511627689]
@@ -35,35 +35,9 @@ def test_g_solve_and_multi_match_paper_recursion(exe, narrow):
     out = subprocess.run([exe, "n" if narrow else "w"], input=inp, capture_output=True, text=True,
                          check=True).stdout.split("\n")
     for (p, K, L, R), line in zip(cases, out):
-        vals = [int(v) for v in line.split()]
-        ok, m, y, ok2, m2, y2 = vals[:6]
+        ok, m, y = (int(v) for v in line.split())
         g = O.G(p, K, L, R)
-        assert ok and ok2
-        assert (m, y) == (g, g * K % p), (p, K, L, R)
-        assert (m2, y2) == (g, g * K % p), (p, K, L, R)
-        if narrow:
-            ok4, m4, y4 = vals[6:]
-            assert ok4 and (m4, y4) == (g, g * K % p), (p, K, L, R)
-
-
-def test_shared_reciprocal_quotients(exe):
-    """floor(a / d) through one precomputed reciprocal of d, for every size of
-    a and d that the 32-bit solver meets (a < 2^31 + 2^30, d < 2^30), with the
-    edges where the estimate is one short: a = k d - 1, k d, k d + d - 1."""
-    rng = random.Random(11)
-    cases = []
-    for _ in range(20000):
-        d = rng.choice([1, 2, 3, 7, rng.randrange(1, 1 << 16), rng.randrange(1, 1 << 30), (1 << 30) - 35])
-        k = rng.randrange(0, (3 << 30) // d + 1)
-        for a in (k * d - 1, k * d, k * d + d - 1, rng.randrange(0, 3 << 30)):
-            if 0 <= a < (3 << 30):
-                cases.append((a, d))
-    cases += [(0xffffffff, 1), (0xffffffff, 0xffffffff), (0xfffffffe, 0xffffffff), (0x80000000, 3)]
-    inp = "".join(f"{a} {d}\n" for a, d in cases)
-    out = subprocess.run([exe, "q"], input=inp, capture_output=True, text=True, check=True).stdout.split()
-    assert len(out) == len(cases)
-    for (a, d), q in zip(cases, out):
-        assert int(q) == a // d, (a, d)
+        assert ok and (m, y) == (g, g * K % p), (p, K, L, R)
 
 
 def test_division_free_montgomery_constants(exe):
@@ -165,3 +139,23 @@ def test_float_estimate_division(exe):
     for (n, p), line in zip(cases, out):
         q, r = (int(x) for x in line.split())
         assert (q, r) == (n // p, n % p), (n, p)
+
+
+def test_first_hit_64bit(exe):
+    """The first hit from the three-gap basis for primes up to 2^40 (the 64-bit
+    walk) equals the paper's G for the window [p - v0, p - v0 + w]."""
+    rng = random.Random(31)
+    pool = [7, 1000003, 999999937, (1 << 30) + 3, 4294967291, 68719476731, 99999999977, 1099511627689]
+    cases = []
+    for _ in range(20000):
+        p = rng.choice(pool)
+        r = rng.randrange(1, p)
+        w = min(rng.choice([1, 2, 17, 40000, 50000, 1 << 21]), p - 2)
+        v0 = rng.choice([w + 1, p - 1, rng.randrange(w + 1, p)])
+        cases.append((p, r, w, v0))
+    inp = "".join(f"{p} {r} {w} {v0}\n" for p, r, w, v0 in cases)
+    out = subprocess.run([exe, "F"], input=inp, capture_output=True, text=True, check=True).stdout.split("\n")
+    for (p, r, w, v0), line in zip(cases, out):
+        ok, t, y = (int(x) for x in line.split())
+        assert ok and t == O.G(p, r, p - v0, p - v0 + w), (p, r, w, v0)
+        assert y == (v0 + r * t) % p, (p, r, w, v0)

@@ -12,6 +12,8 @@
 // primes it finds in shared memory and, 32 at a time, computes K mod p with
 // Montgomery multiplication over K's prime factors packed into machine words,
 // and appends the entries to the output with one atomic per 32 primes.
+#include <atomic>
+
 #include "cs_arith.cuh"
 #include "cs_internal.h"
 
@@ -35,6 +37,10 @@ namespace {
 #endif
 #ifndef CS_GEN_SEGS_PER_CTA
 #define CS_GEN_SEGS_PER_CTA 1
+#endif
+// 1: grid of the resident CTAs and segments sized for whole waves of them
+#ifndef CS_GEN_ONE_WAVE
+#define CS_GEN_ONE_WAVE 1
 #endif
 constexpr uint32_t SEG = 1u << CS_GEN_SEG_LOG;
 constexpr uint32_t SEG_MIN = 1u << 12;      // smallest segment: 8 warps x 16-word batches
@@ -347,7 +353,23 @@ __global__ void __launch_bounds__(GEN_THREADS) k_gen(const GenArgs a) {
     }
 }
 
-GenArgs make_args(uint64_t lo, uint64_t hi, const uint32_t *base, uint32_t n_base) {
+// CTAs of k_gen<KIND> resident at once on the device (occupancy API, once per kind)
+template <int KIND>
+int gen_resident() {
+    static std::atomic<int> cached{0};
+    int n = cached.load(std::memory_order_relaxed);
+    if (n == 0) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gen<KIND>, GEN_THREADS, 0) != cudaSuccess ||
+            per_sm <= 0)
+            per_sm = CS_GEN_GRID_PER_SM;
+        n = sm_count() * per_sm;
+        cached.store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
+
+GenArgs make_args(uint64_t lo, uint64_t hi, const uint32_t *base, uint32_t n_base, int resident) {
     GenArgs a{};
     a.base = base;
     a.n_base = n_base;
@@ -357,20 +379,39 @@ GenArgs make_args(uint64_t lo, uint64_t hi, const uint32_t *base, uint32_t n_bas
     }
     a.i_begin = (lo + 1) / 2;
     a.i_end = (hi + 1) / 2;
+    const uint64_t odds = a.i_end > a.i_begin ? a.i_end - a.i_begin : 0;
+    uint32_t seg = SEG_MIN;
+#if CS_GEN_ONE_WAVE
+    // segment size: the range split evenly over whole waves of the resident
+    // CTAs (k segments each), in multiples of SEG_MIN within [SEG_MIN, SEG], so
+    // that no CTA waits on a partly filled last wave
+    {
+        const uint64_t res = (uint64_t)(resident > 0 ? resident : 1);
+        const uint64_t k = (odds + res * SEG - 1) / (res * SEG);               // segments per CTA
+        const uint64_t per = k ? (odds + res * k - 1) / (res * k) : 0;          // odds per segment
+        const uint64_t sz = (per + SEG_MIN - 1) / SEG_MIN * SEG_MIN;
+        seg = (uint32_t)(sz < SEG_MIN ? SEG_MIN : (sz > SEG ? SEG : sz));
+    }
+#else
     // segment size: enough segments for every CTA of the grid to get
     // CS_GEN_SEGS_PER_CTA of them, within [SEG_MIN, SEG]
-    const uint64_t odds = a.i_end > a.i_begin ? a.i_end - a.i_begin : 0;
     uint64_t want = odds / ((uint64_t)sm_count() * CS_GEN_GRID_PER_SM * CS_GEN_SEGS_PER_CTA);
-    uint32_t seg = SEG_MIN;
     while (seg < SEG && seg < want) seg *= 2;
+    (void)resident;
+#endif
     a.seg = seg;
     a.n_seg = odds ? (odds + seg - 1) / seg : 0;
     a.emit_two = lo < 2 && hi >= 2;
     return a;
 }
 
-int gen_grid(uint64_t n_seg) {
+int gen_grid(uint64_t n_seg, int resident) {
+#if CS_GEN_ONE_WAVE
+    uint64_t g = (uint64_t)(resident > 0 ? resident : 1);
+#else
     uint64_t g = (uint64_t)sm_count() * CS_GEN_GRID_PER_SM;
+    (void)resident;
+#endif
     if (n_seg < g) g = n_seg;
     return (int)(g ? g : 1);
 }
@@ -391,12 +432,13 @@ int sm_count() {
 cudaError_t launch_gen_small(const DevPlan &pl, uint64_t lo, uint64_t hi, const uint32_t *base,
                              uint32_t n_base, SmallPrime *out, uint64_t cap,
                              unsigned long long *count, cudaStream_t stream) {
-    GenArgs a = make_args(lo, hi, base, n_base);
+    const int res = gen_resident<KIND_SMALL>();
+    GenArgs a = make_args(lo, hi, base, n_base, res);
     if (a.n_seg == 0 && !a.emit_two) return cudaSuccess;
     a.kch32 = pl.kch32; a.n_kch32 = pl.n_kch32;
     a.M_start = pl.M_start; a.SL = pl.SL;
     a.o0 = out; a.cap = cap; a.count = count; a.err = pl.stats + ST_ERROR;
-    k_gen<KIND_SMALL><<<gen_grid(a.n_seg), GEN_THREADS, 0, stream>>>(a);
+    k_gen<KIND_SMALL><<<gen_grid(a.n_seg, res), GEN_THREADS, 0, stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -404,7 +446,8 @@ cudaError_t launch_gen_large(const DevPlan &pl, bool narrow, uint64_t lo, uint64
                              const uint32_t *base, uint32_t n_base, void *p_out, void *r_out,
                              void *v_out, uint64_t cap, unsigned long long *count,
                              cudaStream_t stream) {
-    GenArgs a = make_args(lo, hi, base, n_base);
+    const int res = narrow ? gen_resident<KIND_LARGE32>() : gen_resident<KIND_LARGE64>();
+    GenArgs a = make_args(lo, hi, base, n_base, res);
     if (a.n_seg == 0 && !a.emit_two) return cudaSuccess;
     a.kch32 = pl.kch32; a.n_kch32 = pl.n_kch32;
     a.kch64 = pl.kch64; a.n_kch64 = pl.n_kch64;
@@ -412,35 +455,37 @@ cudaError_t launch_gen_large(const DevPlan &pl, bool narrow, uint64_t lo, uint64
     a.o0 = p_out; a.o1 = r_out; a.o2 = v_out;
     a.cap = cap; a.count = count; a.err = pl.stats + ST_ERROR;
     if (narrow)
-        k_gen<KIND_LARGE32><<<gen_grid(a.n_seg), GEN_THREADS, 0, stream>>>(a);
+        k_gen<KIND_LARGE32><<<gen_grid(a.n_seg, res), GEN_THREADS, 0, stream>>>(a);
     else
-        k_gen<KIND_LARGE64><<<gen_grid(a.n_seg), GEN_THREADS, 0, stream>>>(a);
+        k_gen<KIND_LARGE64><<<gen_grid(a.n_seg, res), GEN_THREADS, 0, stream>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gen_pr(const DevPlan &kp, bool narrow, uint64_t lo, uint64_t hi, const uint32_t *base,
                           uint32_t n_base, void *p_out, void *r_out, uint64_t cap,
                           unsigned long long *count, unsigned long long *err, cudaStream_t stream) {
-    GenArgs a = make_args(lo, hi, base, n_base);
+    const int res = narrow ? gen_resident<KIND_PR32>() : gen_resident<KIND_PR64>();
+    GenArgs a = make_args(lo, hi, base, n_base, res);
     if (a.n_seg == 0 && !a.emit_two) return cudaSuccess;
     a.kch32 = kp.kch32; a.n_kch32 = kp.n_kch32;
     a.kch64 = kp.kch64; a.n_kch64 = kp.n_kch64;
     a.o0 = p_out; a.o1 = r_out;
     a.cap = cap; a.count = count; a.err = err;
     if (narrow)
-        k_gen<KIND_PR32><<<gen_grid(a.n_seg), GEN_THREADS, 0, stream>>>(a);
+        k_gen<KIND_PR32><<<gen_grid(a.n_seg, res), GEN_THREADS, 0, stream>>>(a);
     else
-        k_gen<KIND_PR64><<<gen_grid(a.n_seg), GEN_THREADS, 0, stream>>>(a);
+        k_gen<KIND_PR64><<<gen_grid(a.n_seg, res), GEN_THREADS, 0, stream>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gen_list(uint64_t lo, uint64_t hi, const uint32_t *base, uint32_t n_base,
                             uint64_t *out, uint64_t cap, unsigned long long *count,
                             unsigned long long *err, cudaStream_t stream) {
-    GenArgs a = make_args(lo, hi, base, n_base);
+    const int res = gen_resident<KIND_LIST>();
+    GenArgs a = make_args(lo, hi, base, n_base, res);
     if (a.n_seg == 0 && !a.emit_two) return cudaSuccess;
     a.o0 = out; a.cap = cap; a.count = count; a.err = err;
-    k_gen<KIND_LIST><<<gen_grid(a.n_seg), GEN_THREADS, 0, stream>>>(a);
+    k_gen<KIND_LIST><<<gen_grid(a.n_seg, res), GEN_THREADS, 0, stream>>>(a);
     return cudaGetLastError();
 }
 

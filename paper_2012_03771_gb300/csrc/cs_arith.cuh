@@ -342,8 +342,8 @@ CS_HD uint64_t udiv64_est(uint64_t n, uint32_t p, float fr, int64_t &rem_out) {
 // (i, a, da) and (j, b, ub) swap, the first block being i = ceil((v0 - w) b / p)
 // or the next; the second case is the first one for the reflected strip
 // y' = w - y and is computed as such.  Returns the smallest t >= 0 with
-// (v0 + r t) mod p <= w, for w < v0 < p < 2^30 (smaller v0 is a hit at t = 0),
-// and in y_out that residue.
+// (v0 + r t) mod p <= w, for w < v0 < p < 2^30 and w <= 2^21 (2SL with
+// SL <= 2^20; smaller v0 is a hit at t = 0), and in y_out that residue.
 CS_HD uint32_t first_hit32(uint32_t p, float fr, uint32_t w, uint32_t a, uint32_t da, uint32_t b,
                            uint32_t ub, uint32_t v0, uint32_t &y_out) {
     // ub < da is the case da <= ub for the reflected strip y' = w - y (start
@@ -370,10 +370,17 @@ CS_HD uint32_t first_hit32(uint32_t p, float fr, uint32_t w, uint32_t a, uint32_
     int64_t i = -fdiv((int64_t)w - Y, DA);                               // ceil((Y - w) / DA)
     const int64_t t_lo = i * A + j * (int64_t)B;
     if (t_lo < 0) {
-        // steps of A to the first point with t >= 0: ceil(-t_lo / A)
-        int64_t rm;
-        const int64_t q = (int64_t)udiv64_est((uint64_t)(-t_lo), A, rcp_rn((float)A), rm);
-        i += q + (rm != 0);
+        // steps of A to the first point with t >= 0: ceil(-t_lo / A), a quotient
+        // below w / DA + 2 <= 2^21 + 2, so one float estimate is off by less
+        // than 2 and two corrections each way make it exact
+        const int64_t n = -t_lo;                                         // < 2^52
+        int64_t q = (int64_t)(uint32_t)(u64_to_f((uint64_t)n) * rcp_rn((float)A));
+        int64_t rem = n - q * (int64_t)A;
+        if (rem < 0) { rem += A; q--; }
+        if (rem < 0) { rem += A; q--; }
+        if (rem >= (int64_t)A) { rem -= A; q++; }
+        if (rem >= (int64_t)A) { rem -= A; q++; }
+        i += q + (rem != 0);
     }
     const uint32_t y = (uint32_t)(Y - i * (int64_t)DA);
     y_out = sw ? w - y : y;

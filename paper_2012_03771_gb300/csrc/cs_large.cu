@@ -193,11 +193,13 @@ struct TGItem {
 #ifndef CS_TG_STEPS
 #define CS_TG_STEPS 8
 #endif
+// one-walker items (odd m or every m; the light chunks, a few hits per walker):
+// four steps measured best of 2, 3, 4, 8
 #ifndef CS_TG_STEPS_ALL_M
-#define CS_TG_STEPS_ALL_M CS_TG_STEPS
+#define CS_TG_STEPS_ALL_M 4
 #endif
 constexpr int TG_STEPS = CS_TG_STEPS;               // class walks (long walkers)
-constexpr int TG_STEPS_ALL_M = CS_TG_STEPS_ALL_M;   // every-m walks (the light chunks)
+constexpr int TG_STEPS_ALL_M = CS_TG_STEPS_ALL_M;   // one-walker items (the light chunks)
 constexpr int TG_WARPS = LARGE_THREADS / 32;
 
 // v + k r mod p for a small k (v, r < p, 2p fits in UT)

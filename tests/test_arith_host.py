@@ -63,16 +63,22 @@ def test_division_free_montgomery_constants(exe):
 def test_first_hit_from_three_gap_basis(exe):
     """The walk's first hit without a solve (chain of strip points in the basis
     of the two step vectors) equals the paper's G for the window [p - v0, p - v0 + w],
-    including w = 1, v0 = w + 1 and v0 = p - 1, and primes up to 2^30."""
+    including w = 1 and w = 2^21 (the largest 2SL), v0 = w + 1 and v0 = p - 1,
+    steps of one residue, and primes up to 2^30."""
     rng = random.Random(17)
     pool = [5, 7, 101, 7919, 104729, 1000003, 999999937, (1 << 30) - 35]
     cases = []
     for _ in range(20000):
         p = rng.choice(pool)
         r = rng.randrange(1, p)
-        w = min(rng.choice([1, 2, 3, 17, 300, 40000, 50001, rng.randrange(1, p)]), p - 2)
+        w = min(rng.choice([1, 2, 3, 17, 300, 40000, 50001, 1 << 21, rng.randrange(1, 1 << 21)]), p - 2)
         v0 = rng.choice([w + 1, p - 1, rng.randrange(w + 1, p)])
         cases.append((p, r, w, v0))
+    # a step of 1 in the residue (r = 1 or r = p - 1): blocks of up to w + 1 points
+    for p in ((1 << 30) - 35, 999999937):
+        for r in (1, p - 1, 2, p - 2):
+            for w in (1 << 21, 40000):
+                cases += [(p, r, w, w + 1), (p, r, w, p - 1), (p, r, w, p // 2)]
     inp = "".join(f"{p} {r} {w} {v0}\n" for p, r, w, v0 in cases)
     out = subprocess.run([exe, "f"], input=inp, capture_output=True, text=True, check=True).stdout.split("\n")
     for (p, r, w, v0), line in zip(cases, out):

@@ -250,13 +250,21 @@ def run_cuda(args, params):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h2d = 0
+    split = {"plan_ms": 0.0, "sieve_and_fetch_ms": 0.0, "destroy_ms": 0.0}
     for _ in range(e2e_steps):
+        ta = time.perf_counter()
         p2 = cs.Plan(*params.as_tuple(), **{k: v for k, v in tuning.items() if k != "profile"})
         h2d = int(p2.info.h2d_bytes)
+        tb = time.perf_counter()
         p2.sieve(stream)
         cs.cs_fetch_bitset(p2.h, host_bits.numpy().view(np.uint64))
         cs.cs_counts(p2.h, host_cnt.numpy().view(np.uint32))
+        tc = time.perf_counter()
         p2.close()
+        td = time.perf_counter()
+        split["plan_ms"] += (tb - ta) * 1e3 / e2e_steps
+        split["sieve_and_fetch_ms"] += (tc - tb) * 1e3 / e2e_steps
+        split["destroy_ms"] += (td - tc) * 1e3 / e2e_steps
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_value = F_all / e2e_s if ws == 1 else F_all / e2e_s
@@ -299,7 +307,8 @@ def run_cuda(args, params):
             "cpu_baseline": cpu,
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "includes": "cs_plan (host tables, H2D, allocation) + cs_sieve + bitset/counts D2H + cs_destroy"},
+                    "includes": "cs_plan (host tables, H2D, allocation) + cs_sieve + bitset/counts D2H + cs_destroy",
+                    "per_step_split": split},
             "gpu_launches": int(info.launches_per_sieve) * args.steps,
         }
         print(json.dumps(line), flush=True)
@@ -331,8 +340,8 @@ def csrc_sha() -> str:
 # constants for the walk sources whose digest is recorded (csrc_sha); they are
 # ignored when those sources change.
 WALK_COUNTERS = {
-    "search_953": {"csrc_sha": "85b90aaa7bf88fba", "threshold": 80002, "tile_rows": 16, "launches": 18,
-                   "thread_inst": 1.10206470648e11, "dram_bytes": 1.26959744e9 + 2.222592e6},
+    "search_953": {"csrc_sha": "d58068be6ed1b0cf", "threshold": 120003, "tile_rows": 16, "launches": 17,
+                   "thread_inst": 9.819000e+10, "dram_bytes": 1.243268e+09 + 9.287680e+05},
 }
 
 

@@ -58,6 +58,39 @@ def test_bad_tuning_rejected(lib):
     assert cs.cs_plan_status(503, 210, 1, 10, 1000, 10**6, t) in (cs.CS_EINVAL, cs.CS_EDEVICE)
 
 
+def test_bad_walk_and_layout_knobs_rejected(lib):
+    for kw in (dict(m_classes=3), dict(layout=2)):
+        t = cs.make_tuning(**kw)
+        assert cs.cs_plan_status(503, 210, 1, 10, 1000, 10**6, t) == cs.CS_EINVAL, kw
+
+
+def _header_struct(name):
+    """(type, field) pairs of `typedef struct { ... } name;` in the header, arrays as (type, field[n])."""
+    text = open(os.path.join(ROOT, "include", "combsieve.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", text)
+    assert m, name
+    return re.findall(r"(uint\d+_t)\s+(\w+(?:\[\d+\])?)\s*;", m.group(1))
+
+
+@pytest.mark.parametrize("name, cls", [("cs_tuning", "cs_tuning"), ("cs_info_t", "cs_info_t"),
+                                       ("cs_stats_t", "cs_stats_t")])
+def test_binding_structs_match_header(name, cls):
+    """The ctypes mirrors of the ABI structs have the header's fields, in order and with the
+    same widths, so that the library and the binding agree on every offset."""
+    import ctypes
+    import paper_2012_03771_gb300._binding as b
+    want = _header_struct(name)
+    got = getattr(b, cls)._fields_
+    assert len(got) == len(want), (name, got, want)
+    width = {"uint32_t": 4, "uint64_t": 8}
+    for (ctype, field), (gname, gtype) in zip(want, got):
+        base = field.split("[")[0]
+        n = int(field.split("[")[1][:-1]) if "[" in field else 1
+        assert gname == base, (name, gname, base)
+        assert ctypes.sizeof(gtype) == width[ctype] * n, (name, base)
+
+
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     import paper_2012_03771_gb300._binding as b
     monkeypatch.setattr(b, "_lib", None)

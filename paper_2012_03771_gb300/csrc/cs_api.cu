@@ -803,6 +803,7 @@ cs_status cs_sync(cs_plan_t pl) {
     }
     if (err & ERR_PRIME_OVERFLOW) return fail(CS_EOVERFLOW, "prime buffer overflow");
     if (err & ERR_SOLVER_LIMIT) return fail(CS_EDEVICE, "modular solver exceeded its pass bound");
+    if (err & ERR_STAGE_TIMEOUT) return fail(CS_ETIMEOUT, "tile sieve: a staging copy did not complete");
     return CS_OK;
 }
 

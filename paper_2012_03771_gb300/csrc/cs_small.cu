@@ -38,8 +38,45 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
     return v;
 }
 
+// Bulk asynchronous copies global -> shared (the 1-D form of the tensor memory
+// accelerator), whose completion is counted in bytes on an mbarrier.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// the one arrival of this phase, announcing `bytes` to come, then the copy
+// (16-byte aligned addresses, a multiple of 16 bytes)
+__device__ __forceinline__ void bulk_to_shared(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"((unsigned long long)__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// waits for the phase with the given parity; false after max_tries polls
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t max_tries) {
+    for (uint32_t t = 0; t < max_tries; t++) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n selp.u32 %0, 1, 0, q;\n}"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+constexpr uint32_t STAGE_WAIT_TRIES = 1u << 20;
+constexpr int SP_HALF = SP_STAGE / 2;   // records per staging buffer (two buffers)
+
 __global__ void __launch_bounds__(TILE_THREADS) k_tile(const TileArgs a) {
-    extern __shared__ uint32_t smem[];
+    extern __shared__ __align__(128) uint32_t smem[];
     const DevPlan &pl = a.pl;
     const uint32_t TR = a.tc.rows;
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -107,12 +144,31 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile(const TileArgs a) {
     __syncthreads();
 
     // 2. small primes: lane -> row (lane % TR), prime (lane / TR) of this warp's
-    //    group; the prime records are staged through shared memory so that the
-    //    inner loop reads them with shared-memory latency
+    //    group; the prime records come into two shared-memory buffers by bulk
+    //    asynchronous copies, the next one loading while the current one is
+    //    used, so that the inner loop reads them with shared-memory latency
     unsigned long long F = 0;
     {
-        SmallPrime *stage = reinterpret_cast<SmallPrime *>(smem + (TR + 1) * a.tc.max_words);
+        const uint32_t stage_off = ((TR + 1) * a.tc.max_words + 3) & ~3u;      // 16-byte aligned
+        SmallPrime *stage = reinterpret_cast<SmallPrime *>(smem + stage_off);
+        uint64_t *bars = reinterpret_cast<uint64_t *>(stage + 2 * SP_HALF);
         const uint64_t n = min((uint64_t)*a.n_sp, a.sp_cap);
+        const uint32_t n_st = (uint32_t)((n + SP_HALF - 1) / SP_HALF);
+        auto issue = [&](uint32_t st) {             // one thread
+            const uint32_t cnt = (uint32_t)min((uint64_t)SP_HALF, n - (uint64_t)st * SP_HALF);
+            bulk_to_shared(stage + (st & 1) * SP_HALF, a.sp + (uint64_t)st * SP_HALF, cnt * sizeof(SmallPrime),
+                           &bars[st & 1]);
+        };
+        if (threadIdx.x == 0) {
+            mbar_init(&bars[0]);
+            mbar_init(&bars[1]);
+            mbar_init_fence();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (n_st > 0) issue(0);
+            if (n_st > 1) issue(1);
+        }
         const uint32_t pp = 32 / TR;
         const uint32_t r = lane % TR, sub = lane / TR;
         const bool row_ok = r < nrows;
@@ -120,15 +176,17 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile(const TileArgs a) {
         unsigned __int128 lowest = 0;
         if (pl.small_n) lowest = (unsigned __int128)(pl.M_start + moff) * pl.K64 - pl.SL;
         const uint32_t two_sl = 2 * pl.SL;
-        for (uint64_t c0 = 0; c0 < n; c0 += SP_STAGE) {
-            const uint32_t cn = (uint32_t)min((uint64_t)SP_STAGE, n - c0);
-            __syncthreads();
-            for (uint32_t k = threadIdx.x; k < cn; k += TILE_THREADS) stage[k] = a.sp[c0 + k];
-            __syncthreads();
-            for (uint32_t base = warp * pp; base < cn; base += TILE_WARPS * pp) {
+        bool failed = false;                       // a wait gave up: no more copies, no more waits
+        uint32_t issued = n_st < 2 ? n_st : 2;     // stages whose copies were issued
+        uint32_t fail_st = n_st;                   // first stage whose wait gave up
+        for (uint32_t st = 0; st < n_st; st++) {
+            const uint32_t cn = (uint32_t)min((uint64_t)SP_HALF, n - (uint64_t)st * SP_HALF);
+            const SmallPrime *buf = stage + (st & 1) * SP_HALF;
+            const bool ok = !failed && mbar_wait(&bars[st & 1], (st >> 1) & 1, STAGE_WAIT_TRIES);
+            for (uint32_t base = warp * pp; ok && base < cn; base += TILE_WARPS * pp) {
                 const uint32_t i = base + sub;
                 if (!row_ok || i >= cn) continue;
-                const SmallPrime e = stage[i];
+                const SmallPrime e = buf[i];
                 uint32_t v;
                 if (e.p == 2) {
                     v = (e.v0 + moff) & 1u;
@@ -147,6 +205,22 @@ __global__ void __launch_bounds__(TILE_THREADS) k_tile(const TileArgs a) {
                     atomicAnd(&tile[r * nw + (zz >> 5)], ~bit);
                     F++;
                 }
+            }
+            // every thread is done with this buffer before it is loaded again
+            const bool was_failed = failed;
+            failed = __syncthreads_or(!ok) != 0;
+            if (failed && !was_failed) fail_st = st;
+            if (!failed && st + 2 < n_st) {
+                if (threadIdx.x == 0) issue(st + 2);
+                issued = st + 3;
+            }
+        }
+        if (failed) {
+            // let the copies still in flight (stages fail_st .. issued - 1, at
+            // most two) land, with the same bound, before the CTA exits
+            if (threadIdx.x == 0) {
+                for (uint32_t st = fail_st; st < issued; st++) mbar_wait(&bars[st & 1], (st >> 1) & 1, STAGE_WAIT_TRIES);
+                atomicOr(pl.stats + ST_ERROR, (unsigned long long)ERR_STAGE_TIMEOUT);
             }
         }
     }
@@ -201,14 +275,15 @@ cudaError_t launch_tile(const DevPlan &pl, const TileConfig &tc, const SmallPrim
     if (pl.M_c == 0 || pl.W == 0) return cudaSuccess;
     const uint64_t row_blocks = (pl.M_c + tc.rows - 1) / tc.rows;
     const uint64_t blocks = row_blocks * tc.n_chunks;
-    const size_t smem = (size_t)(tc.rows + 1) * tc.max_words * sizeof(uint32_t) + SP_STAGE * sizeof(SmallPrime);
+    const size_t smem = (size_t)(tc.rows + 1) * tc.max_words * sizeof(uint32_t) + tile_stage_bytes();
     TileArgs a{pl, tc, sp, n_sp, sp_cap};
     if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
     k_tile<<<(unsigned)blocks, TILE_THREADS, smem, stream>>>(a);
     return cudaGetLastError();
 }
 
-size_t tile_stage_bytes() { return SP_STAGE * sizeof(SmallPrime); }
+// two staging buffers, their two mbarriers, and up to 12 bytes of alignment
+size_t tile_stage_bytes() { return SP_STAGE * sizeof(SmallPrime) + 2 * sizeof(uint64_t) + 16; }
 
 cudaError_t prepare_tile(int max_dynamic_smem) {
     // raise the kernel's dynamic shared-memory limit once, outside any launch

@@ -16,6 +16,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import tempfile
 import statistics
 import subprocess
 import sys
@@ -203,8 +204,10 @@ def run_cuda(args, params):
         F_ref, h_ref = cs.cs_counts(plan.h)
         stats = plan.stats()
 
-        clocks = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_bench_r{rank}.csv")
-                        if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_{os.getpid()}.csv")
+        # raw clock samples: CS_CLOCKS_DIR if set (kept for inspection), else a temp file
+        clk_dir = os.environ.get("CS_CLOCKS_DIR")
+        clocks = Clocks(os.path.join(clk_dir, f"clocks_bench_r{rank}.csv") if clk_dir and os.path.isdir(clk_dir)
+                        else os.path.join(tempfile.gettempdir(), f"clocks_{os.getpid()}.csv"))
         clocks.start()
         barrier()
         torch.cuda.synchronize()

@@ -259,6 +259,38 @@ CS_HD bool g_solve(UT p, UT K, UT L, UT w, UT &m_out, UT &y_out, uint32_t &iters
     return false;
 }
 
+// Approximate float reciprocal (one MUFU op; relative error at most 2^-23) for
+// quotient estimates that are corrected afterwards.
+CS_HD float rcp_approx(float x) {
+#if defined(__CUDA_ARCH__)
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+#else
+    return 1.0f / x;
+#endif
+}
+
+// floor(a / b) and a mod b for a < 2^31, 1 <= b, when the quotient is below
+// 2^21 + 2, given rb = a reciprocal of b within a relative 2^-23: the float
+// estimate a * rb is then within 1/2 of a / b, its truncation within 1 of the
+// quotient, and one correction either way makes it exact (the remainder, in
+// [-b, 2b), fits 32 signed bits as b < 2^30).  Replaces a full division in the
+// Euclid steps, whose partial quotients are small.
+CS_HD uint32_t udiv_q21(uint32_t a, uint32_t b, float rb, uint32_t &rem) {
+    uint32_t q = (uint32_t)((float)a * rb);
+    int32_t r = (int32_t)(a - q * b);
+    if (r < 0) {
+        q--;
+        r += (int32_t)b;
+    } else if (r >= (int32_t)b) {
+        q++;
+        r -= (int32_t)b;
+    }
+    rem = (uint32_t)r;
+    return q;
+}
+
 // The two steps of the three-gap walk from one run of Euclid's algorithm.
 //
 // For 0 < r < p with gcd(r, p) = 1 and 1 <= w < p: a = the smallest m > 0 with
@@ -279,10 +311,21 @@ template <class UT>
 CS_HD bool tg_steps(UT p, UT r, UT w, UT &a, UT &da, UT &b, UT &ub, uint32_t &iters, uint32_t max_iter) {
     UT x_pp = 0, m_pp = 0, x_prev = p, m_prev = 0, x = r, m = 1;
     uint32_t k = 1;
+    // 32-bit, p < 2^30 and w >= 512: every partial quotient below x_prev / x <
+    // 2^30 / 512 = 2^21, so the float estimate with one correction is exact
+    const bool small_q = sizeof(UT) == 4 && w >= 512 && p < (UT)(1u << 30);
     while (x > w) {
         if (k > max_iter) return false;
-        const UT c = udiv(x_prev, x);
-        const UT xn = x_prev - c * x, mn = m_prev + c * m;
+        UT c, xn;
+        if (small_q) {
+            uint32_t rem;
+            c = (UT)udiv_q21((uint32_t)x_prev, (uint32_t)x, rcp_approx((float)x), rem);
+            xn = (UT)rem;
+        } else {
+            c = udiv(x_prev, x);
+            xn = x_prev - c * x;
+        }
+        const UT mn = m_prev + c * m;
         x_pp = x_prev; m_pp = m_prev;
         x_prev = x; m_prev = m;
         x = xn; m = mn;
@@ -294,7 +337,14 @@ CS_HD bool tg_steps(UT p, UT r, UT w, UT &a, UT &da, UT &b, UT &ub, uint32_t &it
         ms = 1;
         xs = r;
     } else {
-        const UT t = udiv((UT)(x_pp - w + x_prev - 1), x_prev);
+        // quotient below x_pp / x_prev + 1 (x_prev > w)
+        UT t;
+        if (small_q) {
+            uint32_t rem;
+            t = (UT)udiv_q21((uint32_t)(x_pp - w + x_prev - 1), (uint32_t)x_prev, rcp_approx((float)x_prev), rem);
+        } else {
+            t = udiv((UT)(x_pp - w + x_prev - 1), x_prev);
+        }
         ms = m_pp + t * m_prev;
         xs = x_pp - t * x_prev;
     }

@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
                     }
                 } else if (ok) {
                     // class k starts at the first m_lo + dk with m = c_k (mod Q)
-                    const uint32_t lo_res = Q == 1 ? 0u : (uint32_t)m_lo % Q;   // m_lo < M_inc < 2^31
+                    const uint32_t lo_res = (Q == 1 || m_lo == 0) ? 0u : (uint32_t)m_lo % Q;   // m_lo < M_inc < 2^31
                     UT rq = add_times(r, r, Q - 1, pp);        // r' = Q r mod p
 #pragma unroll
                     for (int k = 0; k < NC; k++) {

@@ -5,7 +5,8 @@
 // first hit from the three-gap basis; mode "s" the walk's two steps from
 // Euclid's algorithm; mode "l" the generator's lazily reduced Montgomery
 // product; mode "u" the float-estimate division of 64-bit numerators; mode "F"
-// the first hit for 64-bit primes.
+// the first hit for 64-bit primes; mode "e" the Euclid steps' small-quotient
+// division.
 #include <cstdio>
 #include <cstdint>
 #include "../../paper_2012_03771_gb300/csrc/cs_arith.cuh"
@@ -33,6 +34,21 @@ int main(int argc, char **argv) {
             uint64_t y = 0;
             const uint64_t t = cs::first_hit64(p, w, a, da, b, ub, v0, y);
             printf("%d %llu %llu\n", ok, (unsigned long long)t, (unsigned long long)y);
+        }
+        return 0;
+    }
+    if (argc > 1 && argv[1][0] == 'e') {
+        // "a b" -> floor(a / b) and a mod b from udiv_q21, with the reciprocal
+        // exact and off by a relative -2^-23 and +2^-23 (the device's approximate one)
+        unsigned long long a, b;
+        while (scanf("%llu %llu", &a, &b) == 2) {
+            const float rb = 1.0f / (float)b;
+            const float lo = rb * (1.0f - 1.1920929e-07f), hi = rb * (1.0f + 1.1920929e-07f);
+            uint32_t r0, r1, r2;
+            const uint32_t q0 = cs::udiv_q21((uint32_t)a, (uint32_t)b, rb, r0);
+            const uint32_t q1 = cs::udiv_q21((uint32_t)a, (uint32_t)b, lo, r1);
+            const uint32_t q2 = cs::udiv_q21((uint32_t)a, (uint32_t)b, hi, r2);
+            printf("%u %u %u %u %u %u\n", q0, r0, q1, r1, q2, r2);
         }
         return 0;
     }

@@ -165,3 +165,24 @@ def test_first_hit_64bit(exe):
         ok, t, y = (int(x) for x in line.split())
         assert ok and t == O.G(p, r, p - v0, p - v0 + w), (p, r, w, v0)
         assert y == (v0 + r * t) % p, (p, r, w, v0)
+
+
+def test_small_quotient_division(exe):
+    """floor(a / b) for a < 2^31 and quotients up to 2^21 + 2 from a float estimate and one
+    correction, with the reciprocal exact and perturbed by the relative 2^-23 that the
+    device's approximate reciprocal may be off (the Euclid steps' division)."""
+    rng = random.Random(37)
+    cases = []
+    for _ in range(60000):
+        b = rng.choice([1, 2, 3, 512, 513, rng.randrange(1, 1 << 10), rng.randrange(1, 1 << 20),
+                        rng.randrange(1, 1 << 30)])
+        qmax = min((1 << 21) + 2, ((1 << 31) - 1) // b)
+        q = rng.choice([0, 1, qmax, qmax - 1, rng.randrange(0, qmax + 1)])
+        a = min(q * b + rng.choice([0, b - 1, rng.randrange(0, b)]), (1 << 31) - 1)
+        cases.append((a, b))
+    inp = "".join(f"{a} {b}\n" for a, b in cases)
+    out = subprocess.run([exe, "e"], input=inp, capture_output=True, text=True, check=True).stdout.split("\n")
+    for (a, b), line in zip(cases, out):
+        v = [int(x) for x in line.split()]
+        for k in range(3):
+            assert (v[2 * k], v[2 * k + 1]) == (a // b, a % b), (a, b, k)

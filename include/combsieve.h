@@ -139,7 +139,9 @@ typedef struct {
 /* Builds a sieve instance: validates the parameters, computes the row and
  * column maps and K's factor words on the host, allocates the device bitset and
  * work buffers (owned by the plan) and uploads the tables.  tune may be NULL.
- * On success *out is a new plan; on error *out is NULL. */
+ * On success *out is a new plan; on error *out is NULL.  The device memory
+ * comes from a stream-ordered memory pool the library keeps per device (plans
+ * built by a request server use the server's). */
 cs_status cs_plan(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL,
                   uint64_t L, const cs_tuning *tune, cs_plan_t *out);
 
@@ -190,7 +192,10 @@ const void *cs_device_bitset(cs_plan_t plan);
  * of that class.  Waits. */
 cs_status cs_kernel_times(cs_plan_t plan, double ms[5], uint64_t launches[5]);
 
-/* Frees the plan and its device memory (waits for its work first). */
+/* Frees the plan and its device memory (waits for its work first).  The memory
+ * goes back to the library's pool, which keeps up to 1 GiB of it for later
+ * plans on the device (returned to the device beyond that) until the process
+ * exits. */
 cs_status cs_destroy(cs_plan_t plan);
 
 /* Message for the last error on the calling thread ("" if none). */

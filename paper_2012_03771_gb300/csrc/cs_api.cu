@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -78,6 +79,46 @@ uint64_t prime_count_bound(uint64_t x) {
 
 enum KernelClass { KC_GEN_SMALL = 0, KC_TILE, KC_GEN_LARGE, KC_LARGE, KC_FINAL, KC_N };
 
+// Device memory of plain plans: a library-owned stream-ordered pool per device
+// that keeps up to POOL_KEEP bytes of freed plan memory for the next plan
+// (cudaMalloc / cudaFree of a plan's ~100 MB took about a millisecond per
+// plan), and a stream on which plans return their buffers.
+constexpr uint64_t POOL_KEEP = 1ull << 30;
+struct PlanPool {
+    cudaMemPool_t pool = nullptr;
+    cudaStream_t free_stream = nullptr;
+};
+std::mutex g_pool_mu;
+PlanPool g_plan_pools[64];
+
+cudaError_t plan_pool(PlanPool **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    PlanPool &pp = g_plan_pools[dev];
+    if (!pp.pool) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
+        uint64_t keep = POOL_KEEP;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        cudaStream_t fs = nullptr;
+        if ((e = cudaStreamCreateWithFlags(&fs, cudaStreamNonBlocking)) != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        pp.pool = pool;
+        pp.free_stream = fs;
+    }
+    *out = &pp;
+    return cudaSuccess;
+}
+
 }  // namespace
 
 struct cs_plan_s {
@@ -124,6 +165,7 @@ struct cs_plan_s {
     cudaStream_t alloc_stream = nullptr;
     bool async_alloc = false;
     cudaStream_t own_upload = nullptr;    // private upload stream of a plain plan
+    PlanPool *pool = nullptr;             // plain plans: the device's plan pool
     cudaStream_t upload_stream() {
         if (async_alloc) return alloc_stream;
         if (!own_upload) cudaStreamCreateWithFlags(&own_upload, cudaStreamNonBlocking);
@@ -137,7 +179,12 @@ struct cs_plan_s {
     size_t prof_used[KC_N] = {0, 0, 0, 0, 0};
 
     ~cs_plan_s() {
-        if (own_upload) cudaStreamDestroy(own_upload);
+        if (own_upload) {
+            // a plan that failed while being built: its allocations and uploads
+            // are ordered on this stream, so let them finish before the frees
+            cudaStreamSynchronize(own_upload);
+            cudaStreamDestroy(own_upload);
+        }
         if (done) cudaEventDestroy(done);
         for (int k = 0; k < KC_N; k++)
             for (auto &e : prof_ev[k]) {
@@ -147,16 +194,25 @@ struct cs_plan_s {
         for (void *p : allocs) {
             if (async_alloc)
                 cudaFreeAsync(p, alloc_stream);
+            else if (pool)
+                cudaFreeAsync(p, pool->free_stream);   // back to the pool: the plan's work is done
             else
                 cudaFree(p);
         }
+        // the pool can hand the memory to the next plan once the frees ran
+        if (pool && !allocs.empty() && !async_alloc) cudaStreamSynchronize(pool->free_stream);
     }
 
     template <class T>
     cs_status dalloc(T **p, size_t count) {
         size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-        cudaError_t e = async_alloc ? cudaMallocAsync((void **)p, bytes, alloc_stream)
-                                    : cudaMalloc((void **)p, bytes);
+        cudaError_t e;
+        if (async_alloc) {
+            e = cudaMallocAsync((void **)p, bytes, alloc_stream);
+        } else {
+            if (!pool && (e = plan_pool(&pool)) != cudaSuccess) return cuda_fail(e, "memory pool");
+            e = cudaMallocFromPoolAsync((void **)p, bytes, pool->pool, upload_stream());
+        }
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
         allocs.push_back(*p);
         dev_bytes += bytes;

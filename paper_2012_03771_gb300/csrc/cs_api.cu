@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <mutex>
 #include <new>
 #include <string>
@@ -87,6 +88,7 @@ constexpr uint64_t POOL_KEEP = 1ull << 30;
 struct PlanPool {
     cudaMemPool_t pool = nullptr;
     cudaStream_t free_stream = nullptr;
+    cudaStream_t upload_stream = nullptr;   // plans' allocations and table uploads
 };
 std::mutex g_pool_mu;
 PlanPool g_plan_pools[64];
@@ -107,13 +109,16 @@ cudaError_t plan_pool(PlanPool **out) {
         if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
         uint64_t keep = POOL_KEEP;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
-        cudaStream_t fs = nullptr;
-        if ((e = cudaStreamCreateWithFlags(&fs, cudaStreamNonBlocking)) != cudaSuccess) {
+        cudaStream_t fs = nullptr, us = nullptr;
+        if ((e = cudaStreamCreateWithFlags(&fs, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&us, cudaStreamNonBlocking)) != cudaSuccess) {
+            if (fs) cudaStreamDestroy(fs);
             cudaMemPoolDestroy(pool);
             return e;
         }
         pp.pool = pool;
         pp.free_stream = fs;
+        pp.upload_stream = us;
     }
     *out = &pp;
     return cudaSuccess;
@@ -164,13 +169,16 @@ struct cs_plan_s {
     // cudaFreeAsync, so building or freeing a plan does not wait for other work
     cudaStream_t alloc_stream = nullptr;
     bool async_alloc = false;
-    cudaStream_t own_upload = nullptr;    // private upload stream of a plain plan
     PlanPool *pool = nullptr;             // plain plans: the device's plan pool
-    cudaStream_t upload_stream() {
-        if (async_alloc) return alloc_stream;
-        if (!own_upload) cudaStreamCreateWithFlags(&own_upload, cudaStreamNonBlocking);
-        return own_upload;
-    }
+    bool built = false;                   // build_plan finished
+    // stream of the plan's allocations and uploads: the server's, else the
+    // device pool's (set up by the first dalloc)
+    cudaStream_t upload_stream() { return async_alloc ? alloc_stream : pool->upload_stream; }
+    // tables to upload, staged in one host arena (256-byte aligned parts) and
+    // sent with one allocation and one copy by flush_uploads, which then sets
+    // each destination pointer
+    std::vector<uint8_t> staging;
+    std::vector<std::function<void(uint8_t *)>> pending;
     // residue cache: large primes come from these cache chunks (indices)
     cs_cache_t cache = nullptr;
     std::vector<size_t> cache_idx;
@@ -179,12 +187,9 @@ struct cs_plan_s {
     size_t prof_used[KC_N] = {0, 0, 0, 0, 0};
 
     ~cs_plan_s() {
-        if (own_upload) {
-            // a plan that failed while being built: its allocations and uploads
-            // are ordered on this stream, so let them finish before the frees
-            cudaStreamSynchronize(own_upload);
-            cudaStreamDestroy(own_upload);
-        }
+        // a plan that failed while being built: its allocations and upload are
+        // ordered on the upload stream, so let them finish before the frees
+        if (!built && !allocs.empty()) cudaStreamSynchronize(upload_stream());
         if (done) cudaEventDestroy(done);
         for (int k = 0; k < KC_N; k++)
             for (auto &e : prof_ev[k]) {
@@ -218,20 +223,28 @@ struct cs_plan_s {
         dev_bytes += bytes;
         return CS_OK;
     }
-    template <class T>
-    cs_status upload(T **p, const std::vector<T> &v) {
-        cs_status s = dalloc(p, v.size());
+    template <class D, class T>
+    void stage(D **dst, const std::vector<T> &v) {
+        const size_t off = (staging.size() + 255) & ~(size_t)255;
+        staging.resize(off + std::max<size_t>(v.size(), 1) * sizeof(T));
+        if (!v.empty()) memcpy(staging.data() + off, v.data(), v.size() * sizeof(T));
+        pending.push_back([dst, off](uint8_t *base) { *dst = reinterpret_cast<D *>(base + off); });
+        h2d += v.size() * sizeof(T);
+    }
+    cs_status flush_uploads() {
+        if (pending.empty()) return CS_OK;
+        uint8_t *base = nullptr;
+        cs_status s = dalloc(&base, staging.size());
         if (s) return s;
-        if (!v.empty()) {
-            // every upload goes on one stream that the plan builder synchronises
-            // before the host vectors go out of scope and before any kernel can
-            // read the tables (a plain cudaMemcpy from pageable memory may return
-            // before its DMA lands and is ordered only on the legacy stream)
-            cudaError_t e = cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice,
-                                            upload_stream());
-            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy H2D");
-            h2d += v.size() * sizeof(T);
-        }
+        // one copy on the upload stream, which the plan builder synchronises
+        // before the arena goes away and before any kernel reads the tables (a
+        // plain cudaMemcpy from pageable memory may return before its DMA lands
+        // and is ordered only on the legacy stream)
+        cudaError_t e = cudaMemcpyAsync(base, staging.data(), staging.size(), cudaMemcpyHostToDevice,
+                                        upload_stream());
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy H2D");
+        for (auto &f : pending) f(base);
+        pending.clear();
         return CS_OK;
     }
 };
@@ -603,37 +616,29 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
     dp.P = P; dp.L = L; dp.T = T;
     dp.small_n = small_n; dp.K64 = K64;
     cs_status s;
-    uint32_t *d_kch32; uint64_t *d_kch64;
-    if ((s = pl->upload(&d_kch32, kch32))) return s;
-    if ((s = pl->upload(&d_kch64, kch64))) return s;
-    dp.kch32 = d_kch32; dp.n_kch32 = (uint32_t)kch32.size();
-    dp.kch64 = d_kch64; dp.n_kch64 = (uint32_t)kch64.size();
-    uint32_t *d_mask, *d_prefix, *d_raw, *d_moff, *d_rmask, *d_rpref;
-    if ((s = pl->upload(&d_mask, col_mask))) return s;
-    if ((s = pl->upload(&d_prefix, col_prefix))) return s;
-    if ((s = pl->upload(&d_raw, raw_of_col))) return s;
-    if ((s = pl->upload(&d_moff, moff_of_row))) return s;
-    if ((s = pl->upload(&d_rmask, row_mask))) return s;
-    if ((s = pl->upload(&d_rpref, row_prefix))) return s;
-    dp.col_mask = d_mask; dp.col_prefix = d_prefix; dp.raw_of_col = d_raw;
+    // the read-only tables go up together (one allocation, one copy)
+    pl->stage(&dp.kch32, kch32);
+    pl->stage(&dp.kch64, kch64);
+    dp.n_kch32 = (uint32_t)kch32.size();
+    dp.n_kch64 = (uint32_t)kch64.size();
+    pl->stage(&dp.col_mask, col_mask);
+    pl->stage(&dp.col_prefix, col_prefix);
+    pl->stage(&dp.raw_of_col, raw_of_col);
+    pl->stage(&dp.moff_of_row, moff_of_row);
+    pl->stage(&dp.row_mask, row_mask);
+    pl->stage(&dp.row_prefix, row_prefix);
     {
         // the same tables interleaved as {mask, prefix} pairs for the walk's lookups
-        std::vector<uint32_t> ct(2 * S32), rt(2 * row_mask.size());
-        for (uint64_t w = 0; w < S32; w++) { ct[2 * w] = col_mask[w]; ct[2 * w + 1] = col_prefix[w]; }
-        for (size_t w = 0; w < row_mask.size(); w++) { rt[2 * w] = row_mask[w]; rt[2 * w + 1] = row_prefix[w]; }
-        uint32_t *d_ct, *d_rt;
-        if ((s = pl->upload(&d_ct, ct))) return s;
-        if ((s = pl->upload(&d_rt, rt))) return s;
-        dp.col_tab = reinterpret_cast<const uint2 *>(d_ct);
-        dp.row_tab = reinterpret_cast<const uint2 *>(d_rt);
+        std::vector<uint2> ct(S32), rt(row_mask.size());
+        for (uint64_t w = 0; w < S32; w++) ct[w] = make_uint2(col_mask[w], col_prefix[w]);
+        for (size_t w = 0; w < row_mask.size(); w++) rt[w] = make_uint2(row_mask[w], row_prefix[w]);
+        pl->stage(&dp.col_tab, ct);
+        pl->stage(&dp.row_tab, rt);
     }
-    dp.moff_of_row = d_moff; dp.row_mask = d_rmask; dp.row_prefix = d_rpref;
-    uint32_t *d_wq, *d_wk, *d_wo, *d_wp;
-    if ((s = pl->upload(&d_wq, wq))) return s;
-    if ((s = pl->upload(&d_wk, wkmod))) return s;
-    if ((s = pl->upload(&d_wo, woff))) return s;
-    if ((s = pl->upload(&d_wp, wpat))) return s;
-    dp.qd = d_wq; dp.qd_kmod = d_wk; dp.qd_pat_off = d_wo; dp.qd_pat = d_wp;
+    pl->stage(&dp.qd, wq);
+    pl->stage(&dp.qd_kmod, wkmod);
+    pl->stage(&dp.qd_pat_off, woff);
+    pl->stage(&dp.qd_pat, wpat);
     dp.n_qd = (uint32_t)wq.size();
     dp.compact = pl->layout == 1;
     dp.n_cls = pl->n_cls;
@@ -643,14 +648,11 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
         // class of the first row in each 32-m word of the row mask
         std::vector<uint32_t> cls_word(row_mask.size(), 0);
         for (size_t w = 0; w < row_mask.size(); w++) cls_word[w] = (uint32_t)((pl->cls0 + row_prefix[w]) % pl->n_cls);
-        uint32_t *d_cm, *d_cp, *d_cr, *d_cw, *d_cls;
-        if ((s = pl->upload(&d_cls, cls_word))) return s;
-        dp.cls_word = d_cls;
-        if ((s = pl->upload(&d_cm, cmask))) return s;
-        if ((s = pl->upload(&d_cp, cprefix))) return s;
-        if ((s = pl->upload(&d_cr, pl->craw_h))) return s;
-        if ((s = pl->upload(&d_cw, pl->cW_h))) return s;
-        dp.cmask = d_cm; dp.cprefix = d_cp; dp.craw = d_cr; dp.cW = d_cw;
+        pl->stage(&dp.cls_word, cls_word);
+        pl->stage(&dp.cmask, cmask);
+        pl->stage(&dp.cprefix, cprefix);
+        pl->stage(&dp.craw, pl->craw_h);
+        pl->stage(&dp.cW, pl->cW_h);
     }
     uint64_t *d_bits; uint32_t *d_cnt; unsigned long long *d_stats;
     if ((s = pl->dalloc(&d_bits, M_c * wpr))) return s;
@@ -662,15 +664,14 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
     std::vector<uint32_t> base;
     for (uint32_t q : primes_upto(isqrt_u64(std::max<uint64_t>(L, T)) + 1))
         if (q != 2) base.push_back(q);
-    if ((s = pl->upload(&pl->d_base, base))) return s;
+    pl->stage(&pl->d_base, base);
     pl->n_base = (uint32_t)base.size();
 
-    uint32_t *d_chunk;
-    if ((s = pl->upload(&d_chunk, chunk_tab))) return s;
+    pl->stage(&pl->tc.chunk, chunk_tab);
     pl->tc.rows = TR;
     pl->tc.n_chunks = (uint32_t)(chunk_tab.size() / 4);
-    pl->tc.chunk = d_chunk;
     pl->tc.max_words = max_words;
+    if ((s = pl->flush_uploads())) return s;
 
     if ((s = pl->dalloc(&pl->d_small, pl->small_cap))) return s;
     if ((s = pl->dalloc(&pl->d_counts, 1 + pl->chunks.size()))) return s;
@@ -684,10 +685,8 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
     }
     CS_CUDA(cudaEventCreateWithFlags(&pl->done, cudaEventDisableTiming));
     CS_CUDA(cudaStreamSynchronize(pl->upload_stream()));
-    if (pl->own_upload) {
-        cudaStreamDestroy(pl->own_upload);
-        pl->own_upload = nullptr;
-    }
+    std::vector<uint8_t>().swap(pl->staging);   // the copy has landed
+    pl->built = true;
     return CS_OK;
 }
 

@@ -157,7 +157,9 @@ def _shape(info, tuned):
             "threshold": int(info.threshold), "large_mode": int(info.large_mode), "tile_rows": int(info.tile_rows),
             "layout": "compact" if info.layout else "x coprime to K", "autotuned": tuned is not None,
             "m_classes_walked": f"{int(info.m_walked)} of m mod {int(info.m_mod)}",
-            "chunks_class_walk": f"{int(info.split_chunks)} of {int(info.n_large_chunks)}"}
+            "chunks_class_walk": f"{int(info.split_chunks)} of {int(info.n_large_chunks)}",
+            "class_items": (f"{int(info.item_chunks)} chunks, finest {int(info.item_classes)} classes of "
+                            f"m mod {int(info.item_mod)}" if info.item_chunks else "none")}
 
 
 def run_cuda(args, params):

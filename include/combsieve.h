@@ -85,15 +85,23 @@ typedef struct {
                                 interval whose tile fits in one piece (SL up to about 3.7e5).
                                 F and the per-row counts are the same in both layouts. */
     uint32_t m_classes;      /* three-gap walk over m (the m sharing a factor with d are never
-                                rows): 0 = automatic (chunks whose primes have at least 48
+                                rows): 0 = automatic (chunks whose primes have at least
+                                class_item_hits expected hits per class of m mod 210, else mod 30,
+                                walk the m coprime to that modulus, one work item per class,
+                                when it divides d; chunks whose primes have at least 48
                                 expected hits walk only the m = 1, 5 (mod 6) when 6 | d, the
                                 other chunks the odd m when 2 | d); 1 = every m; 2 = the
-                                widest classes (mod 6, else mod 2) in every chunk */
+                                classes mod 6 (else mod 2) in every chunk; 3 = class items
+                                mod 210 (else 30, 6, 2: the largest that divides d) in every
+                                chunk */
     uint32_t item_hits;      /* three-gap walk: expected walked hits per work item (prime,
                                 m-segment); 0 = automatic (128) */
     uint32_t class_min_hits; /* m_classes = 0: expected hits per prime (every m) from which a
                                 chunk walks only the m-classes; 0 = automatic (48) */
-    uint32_t reserved[3];
+    uint32_t class_item_hits;/* m_classes = 0: expected hits of one class of m mod Q (Q = 210
+                                or 30) per prime from which a chunk walks class items mod Q;
+                                0 = automatic (64) */
+    uint32_t reserved[2];
 } cs_tuning;
 
 typedef struct {
@@ -120,6 +128,9 @@ typedef struct {
     uint32_t m_walked;         /* classes of m mod Q those chunks walk (1 or 2) */
     uint64_t split_chunks;     /* large-prime chunks that walk those classes (the others walk
                                   the odd m when 2 | d) */
+    uint32_t item_mod;         /* finest Q of the chunks that walk class items (0: none) */
+    uint32_t item_classes;     /* classes of m mod item_mod they walk (phi(item_mod)) */
+    uint64_t item_chunks;      /* large-prime chunks that walk class items */
 } cs_info_t;
 
 typedef struct {

@@ -51,7 +51,7 @@ class cs_tuning(ctypes.Structure):
                 ("large_grid", ctypes.c_uint32), ("chunk_numbers", ctypes.c_uint64),
                 ("profile", ctypes.c_uint32), ("layout", ctypes.c_uint32), ("m_classes", ctypes.c_uint32),
                 ("item_hits", ctypes.c_uint32), ("class_min_hits", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 3)]
+                ("class_item_hits", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 2)]
 
 
 class cs_info_t(ctypes.Structure):
@@ -62,7 +62,9 @@ class cs_info_t(ctypes.Structure):
                 ("n_large_chunks", ctypes.c_uint64), ("launches_per_sieve", ctypes.c_uint64),
                 ("h2d_bytes", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
                 ("est_cost", ctypes.c_uint64), ("layout", ctypes.c_uint32), ("n_classes", ctypes.c_uint32),
-                ("m_mod", ctypes.c_uint32), ("m_walked", ctypes.c_uint32), ("split_chunks", ctypes.c_uint64)]
+                ("m_mod", ctypes.c_uint32), ("m_walked", ctypes.c_uint32), ("split_chunks", ctypes.c_uint64),
+                ("item_mod", ctypes.c_uint32), ("item_classes", ctypes.c_uint32),
+                ("item_chunks", ctypes.c_uint64)]
 
 
 class cs_stats_t(ctypes.Structure):
@@ -154,10 +156,11 @@ def _stream_handle(stream) -> ctypes.c_void_p:
 
 def make_tuning(threshold=0, tile_rows=0, large_mode=0, no_wheel=False, large_grid=0,
                 chunk_numbers=0, profile=False, layout=0, m_classes=0, item_hits=0,
-                class_min_hits=0) -> cs_tuning:
+                class_min_hits=0, class_item_hits=0) -> cs_tuning:
     t = cs_tuning()
     t.layout = layout
     t.m_classes, t.item_hits, t.class_min_hits = m_classes, item_hits, class_min_hits
+    t.class_item_hits = class_item_hits
     t.threshold, t.tile_rows, t.large_mode = threshold, tile_rows, large_mode
     t.no_wheel, t.large_grid, t.chunk_numbers = int(no_wheel), large_grid, chunk_numbers
     t.profile = int(profile)

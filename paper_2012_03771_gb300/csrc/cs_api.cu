@@ -9,6 +9,7 @@
 #include <functional>
 #include <mutex>
 #include <new>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -145,9 +146,11 @@ struct cs_plan_s {
     std::vector<std::pair<uint64_t, uint64_t>> chunks;    // large-prime ranges (lo, hi]
     std::vector<uint32_t> chunk_seg;                      // m-segments per prime, per chunk
     std::vector<MClasses> chunk_mc;                       // m-classes each chunk walks
-    MClasses mcls{1, 1, {0, 0}};                          // classes of the chunks with many hits
-    MClasses mcls_light{1, 1, {0, 0}};                    // classes of the other chunks
+    MClasses mcls = EVERY_M;                              // classes of the chunks with many hits
+    MClasses mcls_light = EVERY_M;                        // classes of the other chunks
     uint64_t split_chunks = 0;                            // chunks that walk mcls
+    uint32_t item_mod = 0, item_classes = 0;              // finest class items walked
+    uint64_t item_chunks = 0;                             // chunks that walk class items
     uint64_t large_cap = 0, small_cap = 0, est_cost = 0;
     int large_grid = 0;
     uint64_t h2d = 0, dev_bytes = 0;
@@ -300,6 +303,7 @@ void env_tuning(cs_tuning &t) {
     if (!t.m_classes) t.m_classes = (uint32_t)get("CS_M_CLASSES");
     if (!t.item_hits) t.item_hits = (uint32_t)get("CS_ITEM_HITS");
     if (!t.class_min_hits) t.class_min_hits = (uint32_t)get("CS_CLASS_MIN_HITS");
+    if (!t.class_item_hits) t.class_item_hits = (uint32_t)get("CS_CLASS_ITEM_HITS");
 }
 
 cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc,
@@ -489,12 +493,32 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
     // walker per work item (half the hits for the same setup); m = 1, 5 (mod 6)
     // are two walkers (a third of the hits, one more first hit and queue entry),
     // taken only by chunks whose primes have enough hits to repay the second.
-    if (pl->tune.m_classes > 2) return fail(CS_EINVAL, "m_classes must be 0, 1 or 2");
+    // Class items: with 30 | d (210 | d) the primes with the most hits walk only
+    // the m coprime to 30 (210), 4/15 (8/35) of the hits, each class of m mod Q
+    // as a work item of its own.  Those primes are split into m-segments of
+    // about HITS_PER_ITEM hits anyway, so splitting them by class instead costs
+    // about as many walker set-ups as the mod-6 walk.
+    if (pl->tune.m_classes > 3) return fail(CS_EINVAL, "m_classes must be 0, 1, 2 or 3");
+    auto class_items = [&](uint32_t Q) {
+        MClasses mc = EVERY_M;
+        mc.Q = Q;
+        mc.n = 0;
+        const uint32_t ms = (uint32_t)(M_start % Q);
+        for (uint32_t c = 1; c < Q; c++)        // c: residue of m mod Q
+            if (std::gcd(c, Q) == 1) mc.item_off[mc.n++] = (uint8_t)((c + Q - ms) % Q);
+        mc.items = mc.n;
+        mc.off[0] = mc.item_off[0];
+        return mc;
+    };
+    std::vector<MClasses> fine;                 // class-item candidates, finest first
     if (pl->mode == LARGE_THREE_GAP && SL > 0 && pl->tune.m_classes != 1) {
         const uint32_t m6 = (uint32_t)(M_start % 6), m2 = (uint32_t)(M_start % 2);
-        if (d % 2 == 0) pl->mcls_light = pl->mcls = MClasses{2, 1, {(1 + 2 - m2) % 2, 0}};
-        if (d % 6 == 0) pl->mcls = MClasses{6, 2, {(1 + 6 - m6) % 6, (5 + 6 - m6) % 6}};
+        if (d % 2 == 0) pl->mcls_light = pl->mcls = MClasses{2, 1, {(1 + 2 - m2) % 2, 0}, 0, {}};
+        if (d % 6 == 0) pl->mcls = MClasses{6, 2, {(1 + 6 - m6) % 6, (5 + 6 - m6) % 6}, 0, {}};
+        for (uint32_t Q : {210u, 30u, 6u, 2u})
+            if (d % Q == 0 && (Q > 6 || pl->tune.m_classes == 3)) fine.push_back(class_items(Q));
     }
+    const double CLASS_ITEM_HITS = pl->tune.class_item_hits ? (double)pl->tune.class_item_hits : 64.0;
     // expected hits per prime (every m) at a chunk's low end from which it walks
     // the classes, and walked hits per work item
     const double SPLIT_MIN_HITS = pl->tune.class_min_hits ? (double)pl->tune.class_min_hits : 48.0;
@@ -504,13 +528,36 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
         if (pl->tune.m_classes == 2) return true;
         return (double)M_inc * (double)S / (double)std::max<uint64_t>(lo, 1) >= SPLIT_MIN_HITS;
     };
-    auto classes_for = [&](uint64_t lo) -> MClasses { return split_for(lo) ? pl->mcls : pl->mcls_light; };
+    auto classes_for = [&](uint64_t lo) -> MClasses {
+        if (pl->tune.m_classes == 3) return fine.empty() ? EVERY_M : fine[0];
+        if (pl->tune.m_classes == 0)
+            for (const MClasses &mc : fine)
+                if ((double)M_inc * (double)S / ((double)std::max<uint64_t>(lo, 1) * mc.Q) >= CLASS_ITEM_HITS)
+                    return mc;
+        return split_for(lo) ? pl->mcls : pl->mcls_light;
+    };
+    // walked hits per item: a class (class items) or the item's n classes
     auto segs_for = [&](uint64_t lo) {
         double hits = (double)M_inc * (double)S / (double)std::max<uint64_t>(lo, 1);
         const MClasses mc = classes_for(lo);
-        hits *= (double)mc.n / (double)mc.Q;
+        hits *= (double)(mc.items ? 1 : mc.n) / (double)mc.Q;
         double seg = std::min<double>(std::max(1.0, std::ceil(hits / HITS_PER_ITEM)), (double)std::max<uint64_t>(M_inc, 1));
         return (uint32_t)std::min(seg, 65536.0);
+    };
+    auto add_chunk = [&](uint64_t lo, uint64_t hi) {
+        const MClasses mc = classes_for(lo);
+        pl->chunks.push_back({lo, hi});
+        pl->chunk_seg.push_back(segs_for(lo));
+        pl->chunk_mc.push_back(mc);
+        if (mc.items) {
+            pl->item_chunks++;
+            if (mc.Q > pl->item_mod) {
+                pl->item_mod = mc.Q;
+                pl->item_classes = mc.items;
+            }
+        } else {
+            pl->split_chunks += mc.Q == pl->mcls.Q && mc.n == pl->mcls.n && pl->mcls.Q > 1;
+        }
     };
     uint64_t widest = 0;
     if (cache) {
@@ -524,25 +571,25 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
             const CacheChunk &ch = cv.chunks[k];
             if (ch.hi <= T || ch.lo >= L) continue;
             const uint64_t lo = std::max(ch.lo, T), hi = std::min(ch.hi, L);
-            pl->chunks.push_back({lo, hi});
-            pl->chunk_seg.push_back(segs_for(lo));
-            pl->chunk_mc.push_back(classes_for(lo));
-            pl->split_chunks += split_for(lo);
+            add_chunk(lo, hi);
             pl->cache_idx.push_back(k);
         }
         pl->large_cap = 0;
     } else {
         for (uint64_t lo = T; lo < L;) {
             uint64_t hi = std::min<uint64_t>({L, lo + std::max<uint64_t>(lo, 1), lo + chunk});
-            pl->chunks.push_back({lo, hi});
-            pl->chunk_seg.push_back(segs_for(lo));
-            pl->chunk_mc.push_back(classes_for(lo));
-            pl->split_chunks += split_for(lo);
+            add_chunk(lo, hi);
             widest = std::max(widest, hi - lo);
             lo = hi;
         }
         pl->large_cap = pl->chunks.empty() ? 0 : primes_in_interval_bound(widest);
     }
+    // one segment count and one class choice per chunk (and one cache index
+    // for cached plans): cs_sieve indexes all of them by chunk
+    const size_t n_chunks = pl->chunks.size();
+    if (pl->chunk_seg.size() != n_chunks || pl->chunk_mc.size() != n_chunks ||
+        (pl->cache && pl->cache_idx.size() != n_chunks))
+        return fail(CS_EDEVICE, "internal: large-prime chunk tables disagree");
     pl->small_cap = pl->small_hi > P ? prime_count_bound(pl->small_hi) : 0;
     pl->large_grid = (int)pl->tune.large_grid;   // 0: the launcher picks (one wave of resident CTAs)
 
@@ -886,6 +933,9 @@ cs_status cs_info(cs_plan_t pl, cs_info_t *out) {
     out->m_mod = pl->mcls.Q;
     out->m_walked = pl->mcls.n;
     out->split_chunks = pl->split_chunks;
+    out->item_mod = pl->item_mod;
+    out->item_classes = pl->item_classes;
+    out->item_chunks = pl->item_chunks;
     if (pl->layout == 1) out->W = pl->Wc_max;
     return CS_OK;
 }

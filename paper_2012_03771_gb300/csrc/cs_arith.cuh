@@ -19,6 +19,33 @@
 
 namespace cs {
 
+// Bit helpers for 32-bit words, the shift taken mod 32 (one funnel shift on
+// the device, where a plain shift needs the mask as a second instruction):
+// bit (s mod 32) of x, and x with only its bits below position (s mod 32)
+// (shifted to the top, so that their population count is the number of set
+// bits below s; 0 for s = 0).
+CS_HD uint32_t bit_of(uint32_t x, uint32_t s) {
+#if defined(__CUDA_ARCH__)
+    return __funnelshift_r(x, 0u, s) & 1u;
+#else
+    return (x >> (s & 31)) & 1u;
+#endif
+}
+CS_HD uint32_t bits_below(uint32_t x, uint32_t s) {
+#if defined(__CUDA_ARCH__)
+    return __funnelshift_r(0u, x, s);
+#else
+    return (s & 31) ? x << (32 - (s & 31)) : 0u;
+#endif
+}
+CS_HD uint32_t bit_at(uint32_t s) {
+#if defined(__CUDA_ARCH__)
+    return __funnelshift_l(0u, 1u, s);
+#else
+    return 1u << (s & 31);
+#endif
+}
+
 CS_HD uint64_t mulhi64(uint64_t a, uint64_t b) {
 #if defined(__CUDA_ARCH__)
     return __umul64hi(a, b);

@@ -125,10 +125,18 @@ enum LargeMode { LARGE_PAPER = 1, LARGE_THREE_GAP = 2 };
 // m-classes of the three-gap walk: only m = c (mod Q) for the n classes c with
 // gcd(c, Q) = 1 are walked (Q | d, so the others are never rows).  off[k] is
 // class k's residue of m - M_start mod Q.  Q = 1, n = 1: every m.
+// items = 0: one work item walks all n <= 2 classes (off[0..n)).  items = n
+// (class items, Q up to 210, n up to 48): every class is a work item of its
+// own, item_off[k] its residue; the prime's walk is then split by class as
+// well as by m-segment.
+constexpr uint32_t MAX_CLASS_ITEMS = 48;
 struct MClasses {
     uint32_t Q, n;
     uint32_t off[2];
+    uint32_t items;
+    uint8_t item_off[MAX_CLASS_ITEMS];
 };
+constexpr MClasses EVERY_M = MClasses{1, 1, {0, 0}, 0, {}};
 // n_seg: the m-range of every prime is split into n_seg segments walked by
 // separate threads (each starts with its own solve), to balance primes with
 // many hits against primes with few.
@@ -138,7 +146,7 @@ struct MClasses {
 cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p, const void *r,
                          const void *v, const unsigned long long *count, uint64_t cap,
                          uint32_t n_seg, int grid, cudaStream_t stream, uint64_t p_lo = 0,
-                         uint64_t p_hi = ~0ull, MClasses mc = MClasses{1, 1, {0, 0}});
+                         uint64_t p_hi = ~0ull, MClasses mc = EVERY_M);
 cudaError_t launch_final(const DevPlan &pl, cudaStream_t stream);
 
 // batch of G solves (tests of the solver)

@@ -66,38 +66,42 @@ struct Counters {
     unsigned long long solves = 0, levels = 0, err = 0;
 };
 
-// One hit of prime p at m = M_start + moff with v = (r m + SL) mod p <= 2SL.
-// Branch-free up to the atomic: the row and column tests are bit lookups in
-// small tables (coprime-m mask, stored-x mask, each interleaved with its
-// per-word prefix counts) that stay in L1.
+// One hit of prime p at m = M_start + moff, raw offset z = x + SL = 2SL - v
+// for v = (r m + SL) mod p <= 2SL.  Branch-free up to the atomic: the row and
+// column tests are bit lookups in small tables (coprime-m mask, stored-x
+// mask, each interleaved with its per-word prefix counts) that stay in L1.
 template <class UT>
-__device__ __forceinline__ void record_hit(const DevPlan &pl, uint64_t moff, UT v, UT p, Counters &c) {
-    const uint32_t z = 2 * pl.SL - (uint32_t)v;          // raw offset x + SL
+__device__ __forceinline__ void record_hit_z(const DevPlan &pl, uint64_t moff, uint32_t z, UT p, Counters &c) {
+    const uint32_t ms = (uint32_t)moff;                  // bit of m in its 32-m word: ms mod 32
     const uint2 rt = __ldg(&pl.row_tab[moff >> 5]);      // {coprime-m mask, rows before}
     const uint2 ct = __ldg(&pl.col_tab[z >> 5]);         // {stored-x mask, columns before}
-    const uint32_t rb = 1u << (moff & 31), cb = 1u << (z & 31);
-    bool ok = (rt.x & rb) && (ct.x & cb);                // m coprime to d, x coprime to K
+    bool ok = (bit_of(rt.x, ms) & bit_of(ct.x, z)) != 0; // m coprime to d, x coprime to K
     if (pl.small_n) {
         unsigned __int128 n = (unsigned __int128)(pl.M_start + moff) * pl.K64 + z - pl.SL;
         ok = ok && n != (unsigned __int128)p;            // N + x is p itself
     }
-    const uint32_t row = rt.y + __popc(rt.x & (rb - 1));
-    uint32_t col = ct.y + __popc(ct.x & (cb - 1));
+    const uint32_t row_below = __popc(bits_below(rt.x, ms));
+    const uint32_t row = rt.y + row_below;
+    uint32_t col = ct.y + __popc(bits_below(ct.x, z));
     bool store = ok;                                     // F counts every stored x coprime to K
     if (pl.compact && ok) {
         // the row's class keeps only x with gcd(N + x, d) = 1; class of the
         // first row of this 32-m word, plus the rows before m in the word
-        uint32_t cls = __ldg(&pl.cls_word[moff >> 5]) + __popc(rt.x & (rb - 1));
+        uint32_t cls = __ldg(&pl.cls_word[moff >> 5]) + row_below;
         while (cls >= pl.n_cls) cls -= pl.n_cls;
         const uint32_t ccw = __ldg(&pl.cmask[(size_t)cls * pl.S32 + (z >> 5)]);
-        col = __ldg(&pl.cprefix[(size_t)cls * pl.S32 + (z >> 5)]) + __popc(ccw & (cb - 1));
-        store = (ccw & cb) != 0;
+        col = __ldg(&pl.cprefix[(size_t)cls * pl.S32 + (z >> 5)]) + __popc(bits_below(ccw, z));
+        store = bit_of(ccw, z) != 0;
     }
-    // 32-bit view of the row's words: column col is bit (col & 31) of word col >> 5
+    // 32-bit view of the row's words: column col is bit (col mod 32) of word col >> 5
     if (store)
         atomicAnd(reinterpret_cast<unsigned int *>(pl.bits) + (uint64_t)row * (2 * pl.wpr) + (col >> 5),
-                  ~(1u << (col & 31)));
+                  ~bit_at(col));
     c.F += ok;
+}
+template <class UT>
+__device__ __forceinline__ void record_hit(const DevPlan &pl, uint64_t moff, UT v, UT p, Counters &c) {
+    record_hit_z<UT>(pl, moff, 2 * pl.SL - (uint32_t)v, p, c);
 }
 
 template <class UT, class ST>
@@ -178,7 +182,9 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_large(const LargeArgs a) {
 // j in m = m_c + Q j: v steps by r' = Q r mod p per unit of j, the two step
 // windows are solved for r' (steps of Q j' in m), and each class needs its own
 // first hit.  The walk visits a third of the hits (Q = 6) or half of them
-// (Q = 2).  The two steps come from one run of Euclid's algorithm on (p, r')
+// (Q = 2).  Class items (NC = 1, mc.items classes, Q = 30 or 210): each work
+// item is one class of one (prime, m-segment), so the finer classes (4/15 or
+// 8/35 of the hits) cost one Euclid run per class walker.  The two steps come from one run of Euclid's algorithm on (p, r')
 // (tg_steps, the same answers as G for the two step windows); in the 32-bit
 // walk the first hits follow from the two step vectors, a basis of the lattice
 // of (j, r' j mod p) (first_hit32; first_hit64 in the 64-bit walk).
@@ -211,6 +217,15 @@ __device__ __forceinline__ UT add_times(UT v, UT r, uint32_t k, UT p) {
     }
     return v;
 }
+// the same for k < 2^31 in one reduction (fr = rcp_rn(p) for 32-bit p)
+__device__ __forceinline__ uint32_t mul_add_mod(uint32_t v, uint32_t r, uint32_t k, uint32_t p, float fr) {
+    int64_t rem;
+    udiv64_est((uint64_t)r * k + v, p, fr, rem);     // quotient <= k
+    return (uint32_t)rem;
+}
+__device__ __forceinline__ uint64_t mul_add_mod(uint64_t v, uint64_t r, uint32_t k, uint64_t p, float) {
+    return advance(v, r, k, p);
+}
 
 // resident CTAs per SM the 32-bit walk is compiled for: three (85 registers)
 // measured 7% faster than four (64 registers, with spills) on a GB300
@@ -223,10 +238,20 @@ __device__ __forceinline__ UT add_times(UT v, UT r, uint32_t k, UT p) {
 #define CS_TG_MIN_BLOCKS_WIDE 3
 #endif
 
-template <class UT, class ST, class MT, int NC>
+template <class UT, class ST, class MT, int NC, bool CI = false>
 __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLOCKS : CS_TG_MIN_BLOCKS_WIDE) k_large_tg(const LargeArgs a) {
+    static_assert(!CI || NC == 1, "class items walk one class per item");
     constexpr int QCAP = 32 * (NC + 1);   // a refill adds at most 32 NC walkers
     __shared__ TGItem<UT, ST, MT> queue[TG_WARPS][QCAP];
+    __shared__ uint8_t item_off[CI ? MAX_CLASS_ITEMS : 1];   // class items: residue of each class
+    const uint32_t n_cls_items = CI ? a.mc.items : 1;
+    if constexpr (CI) {
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (uint32_t k = 0; k < MAX_CLASS_ITEMS; k++) item_off[k] = a.mc.item_off[k];
+        }
+        __syncthreads();
+    }
     const DevPlan &pl = a.pl;
     const UT *Pp = reinterpret_cast<const UT *>(a.p);
     const UT *Rp = reinterpret_cast<const UT *>(a.r);
@@ -239,7 +264,7 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
     const uint32_t n_seg = a.n_seg;
     const unsigned lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1;
-    const uint64_t n_items = n * n_seg;
+    const uint64_t n_items = n * n_seg * n_cls_items;
     const uint64_t warp_id = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     // any step >= M ends a walker (its segment is at most M long); two clamped
@@ -253,11 +278,12 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
     uint64_t batch = warp_id;          // next batch of 32 items to prepare
     uint32_t qhead = 0, qcount = 0;    // warp-uniform ring state
     bool active = false;
-    // walker: m offset, segment end, residue v, and the three steps precomputed:
-    // down (v >= d_a): m += a, v -= d_a; up (v <= 2SL - u_b): m += b, v += u_b;
-    // else m += a + b, v += u_b - d_a
+    // walker: m offset, segment end, raw offset z = 2SL - v, and the three steps
+    // precomputed: down (v >= d_a, z <= 2SL - d_a): m += a, z += d_a; up
+    // (v <= 2SL - u_b, z >= u_b): m += b, z -= u_b; else m += a + b,
+    // z += d_a - u_b
     MT moff = 0, end = 0, ma = 0, mb = 0, mab = 0;
-    UT v = 0, p = 1, da = 0, ub = 0, nda = 0, ubd = 0, wmub = 0;
+    UT z = 0, p = 1, da = 0, ub = 0, wmda = 0, nub = 0, dmu = 0;
 
     while (true) {
         // refill: prepare 32 items when the queue can take their walkers
@@ -272,10 +298,17 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
             for (int k = 0; k < NC; k++) push[k] = false;
             if (item < n_items) {
                 uint64_t i = item, m_lo = 0, m_hi = M;
+                uint32_t off0 = a.mc.off[0];               // NC = 1: the class walked
+                if constexpr (CI) {
+                    // consecutive items are the classes of one (prime, segment)
+                    i = n_items >> 32 ? item / n_cls_items : (uint32_t)item / n_cls_items;
+                    off0 = item_off[item - i * n_cls_items];
+                }
                 if (n_seg > 1) {
                     // segments of seg_len m (the last one shorter)
-                    i = n_items >> 32 ? item / n_seg : (uint32_t)item / n_seg;
-                    const uint32_t sg = (uint32_t)(item - i * n_seg);
+                    const uint64_t ps = i;
+                    i = n_items >> 32 ? ps / n_seg : (uint32_t)ps / n_seg;
+                    const uint32_t sg = (uint32_t)(ps - i * n_seg);
                     m_lo = (uint64_t)sg * seg_len;
                     m_hi = min(M, m_lo + seg_len);
                 }
@@ -317,13 +350,16 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
                 } else if (ok) {
                     // class k starts at the first m_lo + dk with m = c_k (mod Q)
                     const uint32_t lo_res = (Q == 1 || m_lo == 0) ? 0u : (uint32_t)m_lo % Q;   // m_lo < M_inc < 2^31
-                    UT rq = add_times(r, r, Q - 1, pp);        // r' = Q r mod p
+                    const float fq = rcp_rn((float)pp);
+                    // r' = Q r mod p (Q <= 6 by additions, class items Q <= 210 by one reduction)
+                    const bool big_q = CI && Q > 6;
+                    const UT rq = big_q ? mul_add_mod((UT)0, r, Q, pp, fq) : add_times(r, r, Q - 1, pp);
 #pragma unroll
                     for (int k = 0; k < NC; k++) {
-                        uint32_t dd = a.mc.off[k] + Q - lo_res;
+                        uint32_t dd = (NC == 1 ? off0 : a.mc.off[k]) + Q - lo_res;
                         if (dd >= Q) dd -= Q;
                         dk[k] = dd;
-                        vk[k] = add_times(vv, r, dd, pp);
+                        vk[k] = big_q ? mul_add_mod(vv, r, dd, pp, fq) : add_times(vv, r, dd, pp);
                     }
                     // the two steps from one run of Euclid's algorithm on (p, r')
                     ok = tg_steps<UT>(pp, rq, w, ma_, da_, mb_, ub_, it, max_iter);
@@ -334,12 +370,11 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
                     c.solves += 2 + n_first;
                     if constexpr (sizeof(UT) == 4) {
                         // each walker's first hit from the step basis, without a solve
-                        const float fr = rcp_rn((float)pp);
 #pragma unroll
                         for (int k = 0; k < NC; k++) {
                             if (ok && vk[k] > w) {
                                 uint32_t y;
-                                first[k] = (uint64_t)first_hit32(pp, fr, w, ma_, da_, mb_, ub_, vk[k], y) * Q;
+                                first[k] = (uint64_t)first_hit32(pp, fq, w, ma_, da_, mb_, ub_, vk[k], y) * Q;
                                 vk[k] = y;
                             }
                         }
@@ -395,12 +430,12 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
             const uint32_t take = min((uint32_t)__popc(idle), qcount);
             if (!active && rank < take) {
                 const TGItem<UT, ST, MT> e = q[(qhead + rank) % QCAP];
-                moff = e.moff; end = e.end; v = e.v; p = e.p; da = e.da; ub = e.ub;
+                moff = e.moff; end = e.end; z = w - e.v; p = e.p; da = e.da; ub = e.ub;
                 ma = e.ma; mb = e.mb;
                 mab = ma + mb;                       // ma, mb <= M_inc < 2^31
-                nda = (UT)0 - da;
-                ubd = ub - da;                       // both wrap; v ends in [0, 2SL]
-                wmub = w - ub;
+                wmda = w - da;
+                nub = (UT)0 - ub;
+                dmu = da - ub;                       // both wrap; z ends in [0, 2SL]
                 active = true;
             }
             qhead = (qhead + take) % QCAP;
@@ -414,13 +449,13 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
         }
         // up to TG_STEPS three-distance steps per active lane between queue
         // checks (each step as selects)
-        constexpr int STEPS = NC == 1 ? TG_STEPS_ALL_M : TG_STEPS;
+        constexpr int STEPS = NC == 1 && !CI ? TG_STEPS_ALL_M : TG_STEPS;
         int u = 0;
         for (; u < STEPS && active; u++) {
-            record_hit<UT>(pl, (uint64_t)moff, v, p, c);
-            const bool down = v >= da;
-            const bool up = v <= wmub;
-            v += down ? nda : (up ? ub : ubd);
+            record_hit_z<UT>(pl, (uint64_t)moff, (uint32_t)z, p, c);
+            const bool down = z <= wmda;
+            const bool up = z >= ub;
+            z += down ? da : (up ? nub : dmu);
             const MT step = down ? ma : (up ? mb : mab);
             active = step < end - moff;
             moff += step;
@@ -461,25 +496,32 @@ __global__ void k_modsolve(const uint64_t *p, const uint64_t *K, const uint64_t 
 cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p, const void *r,
                          const void *v, const unsigned long long *count, uint64_t cap, uint32_t n_seg,
                          int grid, cudaStream_t stream, uint64_t p_lo, uint64_t p_hi, MClasses mc) {
-    if (mc.Q == 0 || mc.n < 1 || mc.n > 2 || mc.n > mc.Q || pl.SL == 0) mc = MClasses{1, 1, {0, 0}};
+    const bool items_ok = mc.items == mc.n && mc.n <= MAX_CLASS_ITEMS && mc.Q <= 256;
+    if (mc.Q == 0 || mc.n < 1 || mc.n > mc.Q || (mc.items ? !items_ok : mc.n > 2) || pl.SL == 0) mc = EVERY_M;
+    // walk kernel: 0 = one walker per item, 1 = two classes per item, 2 = class items
+    const int kind = mc.items ? 2 : mc.n == 2 ? 1 : 0;
     LargeArgs a{pl, p, r, v, count, cap, n_seg ? n_seg : 1, p_lo, p_hi, mc};
+    void (*walk)(const LargeArgs) = nullptr;
+    if (narrow) {
+        walk = kind == 2 ? k_large_tg<uint32_t, int32_t, uint32_t, 1, true>
+             : kind == 1 ? k_large_tg<uint32_t, int32_t, uint32_t, 2>
+                         : k_large_tg<uint32_t, int32_t, uint32_t, 1>;
+    } else {
+        walk = kind == 2 ? k_large_tg<uint64_t, int64_t, uint32_t, 1, true>
+             : kind == 1 ? k_large_tg<uint64_t, int64_t, uint32_t, 2>
+                         : k_large_tg<uint64_t, int64_t, uint32_t, 1>;
+    }
     // the three-gap walk's lanes are persistent: by default one wave of
     // resident CTAs (a partial last wave left SMs idle: 3% slower measured);
     // the paper's walk takes eight CTAs per SM
     if (grid <= 0) {
         grid = sm_count() * 8;
         if (mode != LARGE_PAPER) {
-            static std::atomic<int> resident[2][2];   // [narrow][NC - 1], looked up once
-            std::atomic<int> &cached = resident[narrow ? 1 : 0][mc.n == 2 ? 1 : 0];
+            static std::atomic<int> resident[2][3];   // [narrow][kind], looked up once
+            std::atomic<int> &cached = resident[narrow ? 1 : 0][kind];
             int per_sm = cached.load(std::memory_order_relaxed);
             if (per_sm == 0) {
-                cudaError_t e;
-                if (narrow)
-                    e = mc.n == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_large_tg<uint32_t, int32_t, uint32_t, 2>, LARGE_THREADS, 0)
-                                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_large_tg<uint32_t, int32_t, uint32_t, 1>, LARGE_THREADS, 0);
-                else
-                    e = mc.n == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_large_tg<uint64_t, int64_t, uint32_t, 2>, LARGE_THREADS, 0)
-                                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_large_tg<uint64_t, int64_t, uint32_t, 1>, LARGE_THREADS, 0);
+                cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk, LARGE_THREADS, 0);
                 if (e != cudaSuccess || per_sm <= 0) per_sm = -1;
                 cached.store(per_sm, std::memory_order_relaxed);
             }
@@ -487,20 +529,13 @@ cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p
         }
     }
     // m - M_start < M_inc < 2^31: 32-bit m offsets in both widths
-    if (narrow) {
-        if (mode == LARGE_PAPER)
+    if (mode == LARGE_PAPER) {
+        if (narrow)
             k_large<uint32_t, int32_t><<<grid, LARGE_THREADS, 0, stream>>>(a);
-        else if (mc.n == 2)
-            k_large_tg<uint32_t, int32_t, uint32_t, 2><<<grid, LARGE_THREADS, 0, stream>>>(a);
         else
-            k_large_tg<uint32_t, int32_t, uint32_t, 1><<<grid, LARGE_THREADS, 0, stream>>>(a);
-    } else {
-        if (mode == LARGE_PAPER)
             k_large<uint64_t, int64_t><<<grid, LARGE_THREADS, 0, stream>>>(a);
-        else if (mc.n == 2)
-            k_large_tg<uint64_t, int64_t, uint32_t, 2><<<grid, LARGE_THREADS, 0, stream>>>(a);
-        else
-            k_large_tg<uint64_t, int64_t, uint32_t, 1><<<grid, LARGE_THREADS, 0, stream>>>(a);
+    } else {
+        walk<<<grid, LARGE_THREADS, 0, stream>>>(a);
     }
     return cudaGetLastError();
 }

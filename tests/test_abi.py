@@ -59,7 +59,7 @@ def test_bad_tuning_rejected(lib):
 
 
 def test_bad_walk_and_layout_knobs_rejected(lib):
-    for kw in (dict(m_classes=3), dict(layout=2)):
+    for kw in (dict(m_classes=4), dict(layout=2)):
         t = cs.make_tuning(**kw)
         assert cs.cs_plan_status(503, 210, 1, 10, 1000, 10**6, t) == cs.CS_EINVAL, kw
 

@@ -74,7 +74,9 @@ def test_large_invariants(large):
     assert st["n_large_primes"] == n_large                 # every prime in (T, 1e11] generated
     S = 2 * prm.SL + 1
     expect_hits = prm.M_inc * S * inv                       # Section 3.2: M S sum 1/p
-    # chunks with many hits per prime walk only m = 1, 5 (mod 6): a third of their hits
+    # the chunks with the most hits per prime walk class items mod 210 (8/35 of
+    # their hits) or 30 (4/15), the next ones m = 1, 5 (mod 6) (a third)
     info = out["info"]
     assert info.m_mod == 6 and info.m_walked == 2 and info.split_chunks > 0
-    assert expect_hits / 3 * 0.995 < st["hits_all"] < expect_hits * 1.005
+    assert info.item_mod == 210 and info.item_chunks > 0
+    assert expect_hits * 8 / 35 * 0.995 < st["hits_all"] < expect_hits / 2 * 1.005

@@ -123,11 +123,17 @@ def test_tiny_cases_bit_exact(mode):
     assert n > 80
 
 
-@pytest.mark.parametrize("m_classes", [1, 2])
+def _finest_item_mod(d):
+    return next((Q for Q in (210, 30, 6, 2) if d % Q == 0), 0)
+
+
+@pytest.mark.parametrize("m_classes", [1, 2, 3])
 def test_m_class_walk_bit_exact(m_classes):
-    """The three-gap walk over every m (1) and over the m-classes coprime to
-    Q = 6 or 2 in every chunk (2) give the oracle's bitset; d = 6, 70 (Q = 2),
-    2310, and odd d (Q = 1), with M_start in every residue class mod 6."""
+    """The three-gap walk over every m (1), over the m-classes coprime to
+    Q = 6 or 2 in every chunk (2), and over class items (one work item per
+    class of m mod 210, 30, 6 or 2, the largest that divides d) in every chunk
+    (3) give the oracle's bitset; d = 6, 70 (Q = 2), 2310, and odd d (Q = 1),
+    with M_start in every residue class mod 6."""
     n = 0
     for prm in workloads.tiny_cases(150, seed=12):
         args = prm.as_tuple()
@@ -142,8 +148,37 @@ def test_m_class_walk_bit_exact(m_classes):
             args = (101, d, M_start, 200, 500, 10**6)
             got = _run(args, large_mode=2, threshold=1000, m_classes=m_classes)
             info = got["info"]
-            assert info.m_mod == ((6 if d % 6 == 0 else 2 if d % 2 == 0 else 1) if m_classes == 2 else 1)
+            assert info.m_mod == ((6 if d % 6 == 0 else 2 if d % 2 == 0 else 1) if m_classes != 1 else 1)
+            if m_classes == 3:
+                Q = _finest_item_mod(d)
+                assert info.item_mod == Q
+                assert info.item_chunks == (info.n_large_chunks if Q else 0)
+            else:
+                assert info.item_chunks == 0
             _check_full(args, got)
+
+
+@pytest.mark.parametrize("d", [30, 210, 2310])
+def test_class_items_with_segments_bit_exact(d):
+    """Class items (m coprime to 30 or 210, one work item per class) whose
+    primes are also split into several m-segments: every chunk takes the
+    finest class items (class_item_hits = 1) and items of about one hit, with
+    M_start in several residue classes mod 210."""
+    Q = 210 if d % 210 == 0 else 30
+    for M_start in (1000, 1001, 1003, 1049, 1091, 1177):
+        args = (101, d, M_start, 600, 300, 200_000)
+        # class items in every chunk
+        got = _run(args, large_mode=2, threshold=600, m_classes=3, item_hits=1)
+        info = got["info"]
+        assert info.item_mod == Q and info.item_classes == {30: 8, 210: 48}[Q]
+        assert info.item_chunks == info.n_large_chunks > 0
+        _check_full(args, got)
+        # automatic tiers: class items mod 210 / 30 where a class has a hit per
+        # prime, then the mod-6 classes and the odd m
+        mixed = _run(args, large_mode=2, threshold=600, class_item_hits=1, item_hits=1)
+        assert mixed["info"].item_mod == Q
+        assert 0 < mixed["info"].item_chunks < mixed["info"].n_large_chunks
+        assert np.array_equal(mixed["bits"], got["bits"]) and mixed["F"] == got["F"]
 
 
 def test_k1_survivors_are_primes():
@@ -222,9 +257,12 @@ def test_search_953_sampled_rows_and_invariants():
     T = got["info"].threshold
     _, _, inv = O.prime_stats(T, prm.L)
     all_hits = prm.M_inc * (2 * prm.SL + 1) * inv
-    # default: the chunks with many hits per prime walk m = 1, 5 (mod 6), the rest the odd m
-    assert all_hits / 3 * 0.995 < got["stats"]["hits_all"] < all_hits / 2 * 1.005
-    for m_classes, frac in ((1, 1.0), (2, 1.0 / 3.0)):
+    # default: the chunks with the most hits per prime walk class items mod 210
+    # (8/35 of the hits) or 30 (4/15), the next ones m = 1, 5 (mod 6), the rest the odd m
+    info = got["info"]
+    assert (info.item_mod, info.item_classes) in ((30, 8), (210, 48)) and info.item_chunks > 0
+    assert all_hits * 8 / 35 * 0.995 < got["stats"]["hits_all"] < all_hits / 2 * 1.005
+    for m_classes, frac in ((1, 1.0), (2, 1.0 / 3.0), (3, 8.0 / 35.0)):
         alt = _run(prm.as_tuple(), threshold=T, tile_rows=got["info"].tile_rows, m_classes=m_classes)
         assert alt["hash"] == got["hash"] and alt["F"] == got["F"]
         assert abs(alt["stats"]["hits_all"] - frac * all_hits) < 0.005 * frac * all_hits

@@ -320,20 +320,7 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
     // K as 32- and 64-bit factor words; K itself when it fits in 64 bits
     std::vector<uint32_t> kch32;
     std::vector<uint64_t> kch64;
-    {
-        uint64_t acc = 1;
-        for (uint32_t q : qK) {
-            if (acc > 0x7fffffffull / q) { kch32.push_back((uint32_t)acc); acc = 1; }   // words < 2^31
-            acc *= q;
-        }
-        if (acc > 1) kch32.push_back((uint32_t)acc);
-        unsigned __int128 a64 = 1;
-        for (uint32_t q : qK) {
-            if (a64 * q > (unsigned __int128)UINT64_MAX) { kch64.push_back((uint64_t)a64); a64 = 1; }
-            a64 *= q;
-        }
-        if (a64 > 1) kch64.push_back((uint64_t)a64);
-    }
+    k_factor_words(qK, kch32, kch64);
     bool k_fits = kch64.size() <= 1;
     uint64_t K64 = kch64.empty() ? 1 : kch64[0];
     if (k_fits) {
@@ -779,6 +766,32 @@ struct Prof {
 
 namespace cs {
 
+void k_factor_words(const std::vector<uint32_t> &qK, std::vector<uint32_t> &w32, std::vector<uint64_t> &w64) {
+    std::vector<uint32_t> q(qK);
+    std::sort(q.begin(), q.end(), [](uint32_t a, uint32_t b) { return a > b; });
+    // first fit decreasing: a word takes a factor while the product stays below
+    // the limit (search_953: 45 words below 2^31 instead of 48 in order)
+    auto pack = [&](unsigned __int128 limit) {
+        std::vector<unsigned __int128> bins;
+        for (uint32_t f : q) {
+            bool placed = false;
+            for (auto &b : bins)
+                if (b * f < limit) {
+                    b *= f;
+                    placed = true;
+                    break;
+                }
+            if (!placed) bins.push_back(f);
+        }
+        return bins;
+    };
+    w32.clear();
+    w64.clear();
+    for (auto b : pack((unsigned __int128)1 << 31)) w32.push_back((uint32_t)b);
+    for (auto b : pack((unsigned __int128)1 << 64)) w64.push_back((uint64_t)b);
+}
+
+
 cs_status plan_create(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL,
                       uint64_t L, const cs_tuning *tune, cudaStream_t alloc_stream, bool async_alloc,
                       cs_cache_t cache, cs_plan_t *out) {
@@ -1105,18 +1118,7 @@ cs_status cs_k_mod_p(uint32_t P, uint64_t d, const uint64_t *p, uint64_t n, uint
     if (!split_primes(P, d, qK, qd)) return fail(CS_EINVAL, "d must be squarefree and divide P#");
     std::vector<uint32_t> kch32;
     std::vector<uint64_t> kch64;
-    uint64_t acc = 1;
-    for (uint32_t q : qK) {
-        if (acc > 0x7fffffffull / q) { kch32.push_back((uint32_t)acc); acc = 1; }   // words < 2^31
-        acc *= q;
-    }
-    if (acc > 1) kch32.push_back((uint32_t)acc);
-    unsigned __int128 a64 = 1;
-    for (uint32_t q : qK) {
-        if (a64 * q > (unsigned __int128)UINT64_MAX) { kch64.push_back((uint64_t)a64); a64 = 1; }
-        a64 *= q;
-    }
-    if (a64 > 1) kch64.push_back((uint64_t)a64);
+    k_factor_words(qK, kch32, kch64);
     cudaStream_t st = (cudaStream_t)stream;
     uint32_t *d32 = nullptr;
     uint64_t *d64 = nullptr;

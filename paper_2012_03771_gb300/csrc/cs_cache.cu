@@ -180,18 +180,7 @@ cs_status cache_new(uint32_t P, uint64_t d, uint64_t L_max, cs_cache_t *out) {
     if (rest != 1) return set_error(CS_EINVAL, "d must be squarefree and divide P#");
     std::vector<uint32_t> kch32;
     std::vector<uint64_t> kch64;
-    uint64_t acc = 1;
-    for (uint32_t q : qK) {
-        if (acc > 0x7fffffffull / q) { kch32.push_back((uint32_t)acc); acc = 1; }   // words < 2^31
-        acc *= q;
-    }
-    if (acc > 1) kch32.push_back((uint32_t)acc);
-    unsigned __int128 a64 = 1;
-    for (uint32_t q : qK) {
-        if (a64 * q > (unsigned __int128)UINT64_MAX) { kch64.push_back((uint64_t)a64); a64 = 1; }
-        a64 *= q;
-    }
-    if (a64 > 1) kch64.push_back((uint64_t)a64);
+    k_factor_words(qK, kch32, kch64);
 
     cs_cache_s *c = new (std::nothrow) cs_cache_s();
     if (!c) return set_error(CS_ENOMEM, "host allocation failed");

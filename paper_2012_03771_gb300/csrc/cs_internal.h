@@ -1,6 +1,7 @@
 // Internal interfaces between the host orchestration (cs_api.cu) and the
 // kernel translation units.  Not part of the public C ABI.
 #pragma once
+#include <vector>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -148,6 +149,11 @@ cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p
                          uint32_t n_seg, int grid, cudaStream_t stream, uint64_t p_lo = 0,
                          uint64_t p_hi = ~0ull, MClasses mc = EVERY_M);
 cudaError_t launch_final(const DevPlan &pl, cudaStream_t stream);
+
+// K's prime factors qK packed into factor words below 2^31 (the generator's
+// lazily reduced Montgomery product) and below 2^64, first fit with the
+// largest factors first: K = product of either list.
+void k_factor_words(const std::vector<uint32_t> &qK, std::vector<uint32_t> &w32, std::vector<uint64_t> &w64);
 
 // batch of G solves (tests of the solver)
 cudaError_t launch_modsolve(const uint64_t *p, const uint64_t *K, const uint64_t *L,

@@ -113,7 +113,8 @@ typedef struct {
     uint64_t threshold;        /* effective T */
     uint32_t tile_rows;
     uint32_t large_mode;
-    uint32_t narrow;           /* 1: all large primes < 2^30 (32-bit kernels) */
+    uint32_t narrow;           /* 1: all large primes < 2^30 (32-bit kernels); with 0 the
+                                  chunks below 2^30 still take the 32-bit kernels */
     uint32_t wheel;
     uint64_t n_large_chunks;
     uint64_t launches_per_sieve;  /* kernels one cs_sieve launches */

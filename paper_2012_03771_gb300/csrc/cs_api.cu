@@ -565,6 +565,9 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
     } else {
         for (uint64_t lo = T; lo < L;) {
             uint64_t hi = std::min<uint64_t>({L, lo + std::max<uint64_t>(lo, 1), lo + chunk});
+            // a chunk ends below 2^30 when the next one starts above: it keeps the
+            // 32-bit kernels
+            if (lo < NARROW_LIMIT - 1 && hi >= NARROW_LIMIT) hi = NARROW_LIMIT - 1;
             add_chunk(lo, hi);
             widest = std::max(widest, hi - lo);
             lo = hi;
@@ -879,13 +882,16 @@ cs_status cs_sieve(cs_plan_t pl, void *stream) {
     }
     for (size_t c = 0; c < pl->chunks.size() && !pl->cache; c++) {
         unsigned long long *cnt = pl->d_counts + 1 + c;
+        // 32-bit entries and kernels for every chunk below 2^30, also in a plan
+        // whose L is above (its buffers hold 64-bit entries, so 32-bit ones fit)
+        const bool narrow = pl->narrow || pl->chunks[c].second < NARROW_LIMIT;
         if ((s = prof.begin(KC_GEN_LARGE))) return s;
-        CS_CUDA(launch_gen_large(dp, pl->narrow, pl->chunks[c].first, pl->chunks[c].second,
+        CS_CUDA(launch_gen_large(dp, narrow, pl->chunks[c].first, pl->chunks[c].second,
                                  pl->d_base, pl->n_base, pl->d_lp, pl->d_lr, pl->d_lv,
                                  pl->large_cap, cnt, st));
         if ((s = prof.end())) return s;
         if ((s = prof.begin(KC_LARGE))) return s;
-        CS_CUDA(launch_large(dp, pl->narrow, pl->mode, pl->d_lp, pl->d_lr, pl->d_lv, cnt,
+        CS_CUDA(launch_large(dp, narrow, pl->mode, pl->d_lp, pl->d_lr, pl->d_lv, cnt,
                              pl->large_cap, pl->chunk_seg[c], pl->large_grid, st, 0, ~0ull,
                              pl->chunk_mc[c]));
         if ((s = prof.end())) return s;

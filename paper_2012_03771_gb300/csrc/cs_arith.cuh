@@ -318,6 +318,27 @@ CS_HD uint32_t udiv_q21(uint32_t a, uint32_t b, float rb, uint32_t &rem) {
     return q;
 }
 
+// The same for 64-bit operands, a < 2^62, 1 <= b, a quotient below 2^21 + 2 and
+// rb = a reciprocal of u64_to_f(b) within a relative 2^-23: u64_to_f is within a
+// relative 2^-23 of its argument (each 32-bit half rounded once, and the sum),
+// so u64_to_f(a) * rb is within about 3.5 2^-23 relative, less than 0.875
+// absolute, of a / b, and its truncation is the quotient or off by one either
+// way (the remainder, in [-b, 2b), fits 64 signed bits).  Replaces the 64-bit
+// division of the Euclid steps for primes above 2^32 when p < 2SL 2^21.
+CS_HD uint64_t udiv_q21_64(uint64_t a, uint64_t b, float rb, uint64_t &rem) {
+    uint64_t q = (uint32_t)(u64_to_f(a) * rb);
+    int64_t r = (int64_t)(a - q * b);
+    if (r < 0) {
+        q--;
+        r += (int64_t)b;
+    } else if (r >= (int64_t)b) {
+        q++;
+        r -= (int64_t)b;
+    }
+    rem = (uint64_t)r;
+    return q;
+}
+
 // The two steps of the three-gap walk from one run of Euclid's algorithm.
 //
 // For 0 < r < p with gcd(r, p) = 1 and 1 <= w < p: a = the smallest m > 0 with
@@ -339,14 +360,20 @@ CS_HD bool tg_steps(UT p, UT r, UT w, UT &a, UT &da, UT &b, UT &ub, uint32_t &it
     UT x_pp = 0, m_pp = 0, x_prev = p, m_prev = 0, x = r, m = 1;
     uint32_t k = 1;
     // 32-bit, p < 2^30 and w >= 512: every partial quotient below x_prev / x <
-    // 2^30 / 512 = 2^21, so the float estimate with one correction is exact
+    // 2^30 / 512 = 2^21, so the float estimate with one correction is exact;
+    // 64-bit with p < w 2^21: every partial quotient below p / w < 2^21 likewise
     const bool small_q = sizeof(UT) == 4 && w >= 512 && p < (UT)(1u << 30);
+    const bool small_q64 = sizeof(UT) == 8 && (uint64_t)p < ((uint64_t)w << 21);
     while (x > w) {
         if (k > max_iter) return false;
         UT c, xn;
         if (small_q) {
             uint32_t rem;
             c = (UT)udiv_q21((uint32_t)x_prev, (uint32_t)x, rcp_approx((float)x), rem);
+            xn = (UT)rem;
+        } else if (small_q64) {
+            uint64_t rem;
+            c = (UT)udiv_q21_64((uint64_t)x_prev, (uint64_t)x, rcp_approx(u64_to_f((uint64_t)x)), rem);
             xn = (UT)rem;
         } else {
             c = udiv(x_prev, x);
@@ -369,6 +396,10 @@ CS_HD bool tg_steps(UT p, UT r, UT w, UT &a, UT &da, UT &b, UT &ub, uint32_t &it
         if (small_q) {
             uint32_t rem;
             t = (UT)udiv_q21((uint32_t)(x_pp - w + x_prev - 1), (uint32_t)x_prev, rcp_approx((float)x_prev), rem);
+        } else if (small_q64) {
+            uint64_t rem;
+            t = (UT)udiv_q21_64((uint64_t)(x_pp - w + x_prev - 1), (uint64_t)x_prev,
+                                rcp_approx(u64_to_f((uint64_t)x_prev)), rem);
         } else {
             t = udiv((UT)(x_pp - w + x_prev - 1), x_prev);
         }

@@ -52,6 +52,22 @@ int main(int argc, char **argv) {
         }
         return 0;
     }
+    if (argc > 1 && argv[1][0] == 'E') {
+        // "a b" -> floor(a / b) and a mod b from udiv_q21_64, with the reciprocal
+        // of u64_to_f(b) exact and off by a relative -2^-23 and +2^-23
+        unsigned long long a, b;
+        while (scanf("%llu %llu", &a, &b) == 2) {
+            const float rb = 1.0f / cs::u64_to_f(b);
+            const float lo = rb * (1.0f - 1.1920929e-07f), hi = rb * (1.0f + 1.1920929e-07f);
+            uint64_t r0, r1, r2;
+            const uint64_t q0 = cs::udiv_q21_64(a, b, rb, r0);
+            const uint64_t q1 = cs::udiv_q21_64(a, b, lo, r1);
+            const uint64_t q2 = cs::udiv_q21_64(a, b, hi, r2);
+            printf("%llu %llu %llu %llu %llu %llu\n", (unsigned long long)q0, (unsigned long long)r0,
+                   (unsigned long long)q1, (unsigned long long)r1, (unsigned long long)q2, (unsigned long long)r2);
+        }
+        return 0;
+    }
     if (argc > 1 && argv[1][0] == 'u') {
         // "n p" -> floor(n / p) and n mod p from the float-estimate division
         unsigned long long n, p;

@@ -91,12 +91,15 @@ def test_three_gap_steps_from_euclid(exe):
     """The walk's two steps from one run of Euclid's algorithm (32- and 64-bit)
     equal the paper's G for the windows [p - w, p - 1] and [1, w]."""
     rng = random.Random(19)
-    pool = [3, 5, 101, 7919, 1000003, 999999937, (1 << 30) - 35, 4294967291, 1099511627689]
+    # 64-bit primes below 2SL 2^21 take the float-estimate division (104857599947
+    # is just below 50000 2^21: partial quotients up to 2^21)
+    pool = [3, 5, 101, 7919, 1000003, 999999937, (1 << 30) - 35, 4294967291, 1099511627689,
+            1073741827, 2999999929, 17179869209, 99999999977, 104857599947, 83886079997]
     cases = []
     for _ in range(20000):
         p = rng.choice(pool)
         r = rng.randrange(1, p)
-        w = min(rng.choice([1, 2, 3, 17, 300, 40000, 50001, rng.randrange(1, p)]), p - 2)
+        w = min(rng.choice([1, 2, 3, 17, 300, 40000, 50000, 50001, rng.randrange(1, p)]), p - 2)
         if w < 1:
             continue
         cases.append((p, r, w))
@@ -182,6 +185,27 @@ def test_small_quotient_division(exe):
         cases.append((a, b))
     inp = "".join(f"{a} {b}\n" for a, b in cases)
     out = subprocess.run([exe, "e"], input=inp, capture_output=True, text=True, check=True).stdout.split("\n")
+    for (a, b), line in zip(cases, out):
+        v = [int(x) for x in line.split()]
+        for k in range(3):
+            assert (v[2 * k], v[2 * k + 1]) == (a // b, a % b), (a, b, k)
+
+
+def test_small_quotient_division_64(exe):
+    """floor(a / b) for 64-bit a (up to 2^41) and quotients up to 2^21 + 2 from a float
+    estimate through 32-bit halves and one correction, with the reciprocal exact and
+    perturbed by a relative 2^-23 (the Euclid steps' division for primes above 2^32)."""
+    rng = random.Random(41)
+    cases = []
+    for _ in range(60000):
+        b = rng.choice([1, 2, 3, 50000, 50001, rng.randrange(1, 1 << 16), rng.randrange(1 << 20, 1 << 32),
+                        rng.randrange(1 << 32, 1 << 40), (1 << 32) - 1, 1 << 32, (1 << 32) + 1])
+        qmax = min((1 << 21) + 2, ((1 << 41) - 1) // b)
+        q = rng.choice([0, 1, qmax, qmax - 1, rng.randrange(0, qmax + 1)])
+        a = min(q * b + rng.choice([0, b - 1, rng.randrange(0, b)]), (1 << 41) - 1)
+        cases.append((a, b))
+    inp = "".join(f"{a} {b}\n" for a, b in cases)
+    out = subprocess.run([exe, "E"], input=inp, capture_output=True, text=True, check=True).stdout.split("\n")
     for (a, b), line in zip(cases, out):
         v = [int(x) for x in line.split()]
         for k in range(3):

@@ -345,8 +345,8 @@ def csrc_sha() -> str:
 # constants for the walk sources whose digest is recorded (csrc_sha); they are
 # ignored when those sources change.
 WALK_COUNTERS = {
-    "search_953": {"csrc_sha": "39eed42f34709324", "threshold": 120003, "tile_rows": 16, "launches": 17,
-                   "thread_inst": 8.769045e+10, "dram_bytes": 1.243351e+09 + 1.475840e+06},
+    "search_953": {"csrc_sha": "536d03c644832bed", "threshold": 120003, "tile_rows": 16, "launches": 17,
+                   "thread_inst": 8.768939e+10, "dram_bytes": 1.243213e+09 + 1.264640e+06},
 }
 
 

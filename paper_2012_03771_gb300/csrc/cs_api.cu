@@ -942,8 +942,13 @@ cs_status cs_info(cs_plan_t pl, cs_info_t *out) {
     out->narrow = pl->narrow;
     out->wheel = pl->wheel;
     out->n_large_chunks = pl->chunks.size();
+    // per large-prime chunk: the walk, and without a cache the generator (and,
+    // for 64-bit primes, the residue kernel)
+    uint64_t large_launches = 0;
+    for (const auto &ch : pl->chunks)
+        large_launches += pl->cache ? 1 : (pl->narrow || ch.second < NARROW_LIMIT) ? 2 : 3;
     out->launches_per_sieve = (pl->small_hi > pl->P ? 1 : 0) + (pl->M_c && pl->W ? 1 : 0) +
-                              (pl->M_c ? 1 : 0) + (pl->cache ? 1 : 2) * pl->chunks.size();
+                              (pl->M_c ? 1 : 0) + large_launches;
     out->h2d_bytes = pl->h2d;
     out->device_bytes = pl->dev_bytes;
     out->est_cost = pl->est_cost;

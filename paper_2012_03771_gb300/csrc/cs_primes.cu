@@ -134,12 +134,7 @@ __device__ __forceinline__ void emit(const GenArgs &a, uint64_t p, bool valid, u
             uint32_t rt = mont32_mul(r, r2, p32, pinv);
             e0 = p32; e1 = r; e2 = mont32_affine(rt, a.M_start, a.SL, r2, p32, pinv);   // SL < p
         } else if (KIND == KIND_LARGE64) {
-            uint64_t pinv = mont64_neg_inv(p);
-            uint64_t r1 = mont64_r1(p), r2 = mont64_r2(p);
-            uint64_t r = kmodp64(p, pinv, r1, r2, a.kch64, a.n_kch64);
-            uint64_t rt = mont64_mul(r, r2, p, pinv);
-            uint64_t v = mont64_mul(rt, a.M_start % p, p, pinv) + a.SL;
-            w0 = p; w1 = r; w2 = v >= p ? v - p : v;
+            w0 = p;                                               // residues: k_large_res
         } else if (KIND == KIND_PR32) {
             uint32_t p32 = (uint32_t)p;
             uint32_t pinv = mont32_neg_inv(p32);
@@ -175,8 +170,6 @@ __device__ __forceinline__ void emit(const GenArgs &a, uint64_t p, bool valid, u
         reinterpret_cast<uint32_t *>(a.o2)[slot] = e2;
     } else if (KIND == KIND_LARGE64) {
         reinterpret_cast<uint64_t *>(a.o0)[slot] = w0;
-        reinterpret_cast<uint64_t *>(a.o1)[slot] = w1;
-        reinterpret_cast<uint64_t *>(a.o2)[slot] = w2;
     } else if (KIND == KIND_PR32) {
         reinterpret_cast<uint32_t *>(a.o0)[slot] = e0;
         reinterpret_cast<uint32_t *>(a.o1)[slot] = e1;
@@ -185,6 +178,29 @@ __device__ __forceinline__ void emit(const GenArgs &a, uint64_t p, bool valid, u
         reinterpret_cast<uint64_t *>(a.o1)[slot] = w1;
     } else {
         reinterpret_cast<uint64_t *>(a.o0)[slot] = w0;
+    }
+}
+
+// Residues of the 64-bit large primes the generator wrote (o0): r = K mod p
+// (Section 3.1) into o1 and v = (r M_start + SL) mod p into o2, one thread per
+// prime, every resident warp on the chain of 64-bit Montgomery products (9%
+// faster than inside the sieve kernel on L = 1e11).  The 32-bit residues stay in
+// the sieve kernel, where they fill issue slots that its barriers and marking
+// phases leave idle (split out, the generator took 3.06 instead of 2.57 ms per
+// sieve on L = 1e9).
+constexpr uint32_t RES_THREADS = 256;
+__global__ void __launch_bounds__(RES_THREADS) k_large_res(const GenArgs a) {
+    const uint64_t n = min((uint64_t)*a.count, a.cap);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t p = reinterpret_cast<const uint64_t *>(a.o0)[i];
+        const uint64_t pinv = mont64_neg_inv(p);
+        const uint64_t r1 = mont64_r1(p), r2 = mont64_r2(p);
+        const uint64_t r = kmodp64(p, pinv, r1, r2, a.kch64, a.n_kch64);
+        const uint64_t rt = mont64_mul(r, r2, p, pinv);
+        const uint64_t v = mont64_mul(rt, a.M_start % p, p, pinv) + a.SL;
+        reinterpret_cast<uint64_t *>(a.o1)[i] = r;
+        reinterpret_cast<uint64_t *>(a.o2)[i] = v >= p ? v - p : v;
     }
 }
 
@@ -454,10 +470,21 @@ cudaError_t launch_gen_large(const DevPlan &pl, bool narrow, uint64_t lo, uint64
     a.M_start = pl.M_start; a.SL = pl.SL;
     a.o0 = p_out; a.o1 = r_out; a.o2 = v_out;
     a.cap = cap; a.count = count; a.err = pl.stats + ST_ERROR;
-    if (narrow)
+    if (narrow) {
         k_gen<KIND_LARGE32><<<gen_grid(a.n_seg, res), GEN_THREADS, 0, stream>>>(a);
-    else
+    } else {
+        // residues of the primes written: one wave of resident CTAs over the count
+        static std::atomic<int> res_per_sm{0};
+        int per_sm = res_per_sm.load(std::memory_order_relaxed);
+        if (per_sm == 0) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_large_res, RES_THREADS, 0) != cudaSuccess ||
+                per_sm <= 0)
+                per_sm = 4;
+            res_per_sm.store(per_sm, std::memory_order_relaxed);
+        }
         k_gen<KIND_LARGE64><<<gen_grid(a.n_seg, res), GEN_THREADS, 0, stream>>>(a);
+        k_large_res<<<sm_count() * per_sm, RES_THREADS, 0, stream>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -371,8 +371,10 @@ def roofline(dom, kern_ms, kern_n, stats, info, params, peaks, peak_src, clk, co
            "peak": peak, "unit": "Tinst/s", "frac": None, "traffic": None,
            "peak_source": f"derived: {n_sm} SMs x 4 schedulers x 32 lanes x {sm_mhz:.0f} MHz (integer issue rate)"}
     ctr = WALK_COUNTERS.get(config)
-    same_setup = ctr is not None and (ctr.get("threshold"), ctr.get("tile_rows")) == (int(info.threshold),
-                                                                                     int(info.tile_rows))
+    # the counters hold for the same sources, threshold, tile height and chunking
+    # (one walk launch per large-prime chunk)
+    same_setup = ctr is not None and (ctr.get("threshold"), ctr.get("tile_rows"), ctr.get("launches")) == (
+        int(info.threshold), int(info.tile_rows), int(info.n_large_chunks))
     if name == "large_walk" and ctr and ctr["csrc_sha"] == csrc_sha() and same_setup:
         sieves = n_launch / ctr["launches"]
         inst_launch = ctr["thread_inst"] / ctr["launches"]

@@ -222,7 +222,7 @@ const char *cs_last_error(void);
  * *out receives a complete tuning (large_mode = 2).  Validation errors as for
  * cs_plan.  Tuning fields left at 0 in any plan may also be set from the
  * environment: CS_THRESHOLD, CS_TILE_ROWS, CS_LARGE_MODE, CS_LARGE_GRID, CS_M_CLASSES,
- * CS_ITEM_HITS, CS_CLASS_MIN_HITS. */
+ * CS_ITEM_HITS, CS_CLASS_MIN_HITS, CS_CLASS_ITEM_HITS, CS_CHUNK_NUMBERS. */
 cs_status cs_autotune(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL, uint64_t L,
                       const char *cache_path, cs_tuning *out);
 

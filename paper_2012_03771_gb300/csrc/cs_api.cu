@@ -304,6 +304,7 @@ void env_tuning(cs_tuning &t) {
     if (!t.item_hits) t.item_hits = (uint32_t)get("CS_ITEM_HITS");
     if (!t.class_min_hits) t.class_min_hits = (uint32_t)get("CS_CLASS_MIN_HITS");
     if (!t.class_item_hits) t.class_item_hits = (uint32_t)get("CS_CLASS_ITEM_HITS");
+    if (!t.chunk_numbers) t.chunk_numbers = get("CS_CHUNK_NUMBERS");
 }
 
 cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc,

@@ -16,6 +16,7 @@
 #include "../../include/combsieve.h"
 #include "cs_arith.cuh"
 #include "cs_internal.h"
+#include "cs_words.h"
 
 using namespace cs;
 
@@ -771,28 +772,7 @@ struct Prof {
 namespace cs {
 
 void k_factor_words(const std::vector<uint32_t> &qK, std::vector<uint32_t> &w32, std::vector<uint64_t> &w64) {
-    std::vector<uint32_t> q(qK);
-    std::sort(q.begin(), q.end(), [](uint32_t a, uint32_t b) { return a > b; });
-    // first fit decreasing: a word takes a factor while the product stays below
-    // the limit (search_953: 45 words below 2^31 instead of 48 in order)
-    auto pack = [&](unsigned __int128 limit) {
-        std::vector<unsigned __int128> bins;
-        for (uint32_t f : q) {
-            bool placed = false;
-            for (auto &b : bins)
-                if (b * f < limit) {
-                    b *= f;
-                    placed = true;
-                    break;
-                }
-            if (!placed) bins.push_back(f);
-        }
-        return bins;
-    };
-    w32.clear();
-    w64.clear();
-    for (auto b : pack((unsigned __int128)1 << 31)) w32.push_back((uint32_t)b);
-    for (auto b : pack((unsigned __int128)1 << 64)) w64.push_back((uint64_t)b);
+    pack_k_words(qK, w32, w64);
 }
 
 

@@ -5,11 +5,12 @@
 // first hit from the three-gap basis; mode "s" the walk's two steps from
 // Euclid's algorithm; mode "l" the generator's lazily reduced Montgomery
 // product; mode "u" the float-estimate division of 64-bit numerators; mode "F"
-// the first hit for 64-bit primes; mode "e" the Euclid steps' small-quotient
-// division.
+// the first hit for 64-bit primes; mode "e" (and "E", 64-bit) the Euclid steps'
+// small-quotient division; mode "k" K's factor words.
 #include <cstdio>
 #include <cstdint>
 #include "../../paper_2012_03771_gb300/csrc/cs_arith.cuh"
+#include "../../paper_2012_03771_gb300/csrc/cs_words.h"
 
 int main(int argc, char **argv) {
     const bool narrow = argc > 1 && argv[1][0] == 'n';
@@ -49,6 +50,21 @@ int main(int argc, char **argv) {
             const uint32_t q1 = cs::udiv_q21((uint32_t)a, (uint32_t)b, lo, r1);
             const uint32_t q2 = cs::udiv_q21((uint32_t)a, (uint32_t)b, hi, r2);
             printf("%u %u %u %u %u %u\n", q0, r0, q1, r1, q2, r2);
+        }
+        return 0;
+    }
+    if (argc > 1 && argv[1][0] == 'k') {
+        // "n q_1 ... q_n" -> the words below 2^31, then the words below 2^64, one line each
+        unsigned n;
+        while (scanf("%u", &n) == 1) {
+            std::vector<uint32_t> q(n), w32;
+            std::vector<uint64_t> w64;
+            for (unsigned i = 0; i < n; i++) scanf("%u", &q[i]);
+            cs::pack_k_words(q, w32, w64);
+            for (uint32_t w : w32) printf("%u ", w);
+            printf("\n");
+            for (uint64_t w : w64) printf("%llu ", (unsigned long long)w);
+            printf("\n");
         }
         return 0;
     }

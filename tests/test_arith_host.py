@@ -210,3 +210,39 @@ def test_small_quotient_division_64(exe):
         v = [int(x) for x in line.split()]
         for k in range(3):
             assert (v[2 * k], v[2 * k + 1]) == (a // b, a % b), (a, b, k)
+
+
+def test_k_factor_words(exe):
+    """K = P#/d packed into words below 2^31 (the 32-bit generator's lazily reduced
+    Montgomery product) and below 2^64: each list multiplies to K exactly, every word is
+    in range and a product of distinct primes of K, and first fit decreasing needs no
+    more words than packing in order (45 instead of 48 for 953#/210)."""
+    cases = [(503, 210), (953, 210), (1019, 210), (101, 2310), (37, 30), (7, 210), (953, 1)]
+    inp, qks = "", []
+    for P, d in cases:
+        qK = [q for q in O.primes(1, P) if d % q]
+        qks.append([int(q) for q in qK])
+        inp += f"{len(qK)} " + " ".join(str(int(q)) for q in qK) + "\n"
+    out = subprocess.run([exe, "k"], input=inp, capture_output=True, text=True, check=True).stdout.split("\n")
+    for k, ((P, d), qK) in enumerate(zip(cases, qks)):
+        K = 1
+        for q in qK:
+            K *= q
+        w32 = [int(x) for x in out[2 * k].split()]
+        w64 = [int(x) for x in out[2 * k + 1].split()]
+        for words, limit in ((w32, 1 << 31), (w64, 1 << 64)):
+            prod = 1
+            for w in words:
+                assert 1 < w < limit, (P, d, w)
+                prod *= w
+            assert prod == K, (P, d)
+        # words in order, as packed before: a new word when the next factor does not fit
+        seq, acc = 0, 1
+        for q in qK:
+            if acc * q >= 1 << 31:
+                seq, acc = seq + 1, 1
+            acc *= q
+        seq += acc > 1
+        assert len(w32) <= seq, (P, d)
+        if (P, d) == (953, 210):
+            assert (len(w32), seq) == (45, 48)

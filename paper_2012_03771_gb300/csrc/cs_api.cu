@@ -17,6 +17,7 @@
 #include "cs_arith.cuh"
 #include "cs_internal.h"
 #include "cs_words.h"
+#include "cs_classes.h"
 
 using namespace cs;
 
@@ -477,54 +478,14 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
     // chunk_numbers wide; a chunk's primes are split into n_seg m-segments of
     // about HITS_PER_ITEM expected hits each
     const uint64_t chunk = pl->tune.chunk_numbers ? pl->tune.chunk_numbers : (1ull << 27);
-    // m-classes: rows need gcd(m, d) = 1, so with 2 | d the walk can skip the
-    // even m, and with 6 | d the m = 0, 2, 3, 4 (mod 6).  The odd m are one
-    // walker per work item (half the hits for the same setup); m = 1, 5 (mod 6)
-    // are two walkers (a third of the hits, one more first hit and queue entry),
-    // taken only by chunks whose primes have enough hits to repay the second.
-    // Class items: with 30 | d (210 | d) the primes with the most hits walk only
-    // the m coprime to 30 (210), 4/15 (8/35) of the hits, each class of m mod Q
-    // as a work item of its own.  Those primes are split into m-segments of
-    // about HITS_PER_ITEM hits anyway, so splitting them by class instead costs
-    // about as many walker set-ups as the mod-6 walk.
+    // m-classes per chunk (cs_classes.h): class items mod 210 or 30 for the
+    // primes with the most hits, then m = 1, 5 (mod 6), then the odd m
     if (pl->tune.m_classes > 3) return fail(CS_EINVAL, "m_classes must be 0, 1, 2 or 3");
-    auto class_items = [&](uint32_t Q) {
-        MClasses mc = EVERY_M;
-        mc.Q = Q;
-        mc.n = 0;
-        const uint32_t ms = (uint32_t)(M_start % Q);
-        for (uint32_t c = 1; c < Q; c++)        // c: residue of m mod Q
-            if (std::gcd(c, Q) == 1) mc.item_off[mc.n++] = (uint8_t)((c + Q - ms) % Q);
-        mc.items = mc.n;
-        mc.off[0] = mc.item_off[0];
-        return mc;
-    };
-    std::vector<MClasses> fine;                 // class-item candidates, finest first
-    if (pl->mode == LARGE_THREE_GAP && SL > 0 && pl->tune.m_classes != 1) {
-        const uint32_t m6 = (uint32_t)(M_start % 6), m2 = (uint32_t)(M_start % 2);
-        if (d % 2 == 0) pl->mcls_light = pl->mcls = MClasses{2, 1, {(1 + 2 - m2) % 2, 0}, 0, {}};
-        if (d % 6 == 0) pl->mcls = MClasses{6, 2, {(1 + 6 - m6) % 6, (5 + 6 - m6) % 6}, 0, {}};
-        for (uint32_t Q : {210u, 30u, 6u, 2u})
-            if (d % Q == 0 && (Q > 6 || pl->tune.m_classes == 3)) fine.push_back(class_items(Q));
-    }
-    const double CLASS_ITEM_HITS = pl->tune.class_item_hits ? (double)pl->tune.class_item_hits : 64.0;
-    // expected hits per prime (every m) at a chunk's low end from which it walks
-    // the classes, and walked hits per work item
-    const double SPLIT_MIN_HITS = pl->tune.class_min_hits ? (double)pl->tune.class_min_hits : 48.0;
+    const ClassTiers tiers = class_tiers(pl->mode == LARGE_THREE_GAP && SL > 0, d, M_start, M_inc, S, pl->tune);
+    pl->mcls = tiers.mcls;
+    pl->mcls_light = tiers.mcls_light;
     const double HITS_PER_ITEM = pl->tune.item_hits ? (double)pl->tune.item_hits : 128.0;
-    auto split_for = [&](uint64_t lo) -> bool {
-        if (pl->mcls.Q == 1) return false;
-        if (pl->tune.m_classes == 2) return true;
-        return (double)M_inc * (double)S / (double)std::max<uint64_t>(lo, 1) >= SPLIT_MIN_HITS;
-    };
-    auto classes_for = [&](uint64_t lo) -> MClasses {
-        if (pl->tune.m_classes == 3) return fine.empty() ? EVERY_M : fine[0];
-        if (pl->tune.m_classes == 0)
-            for (const MClasses &mc : fine)
-                if ((double)M_inc * (double)S / ((double)std::max<uint64_t>(lo, 1) * mc.Q) >= CLASS_ITEM_HITS)
-                    return mc;
-        return split_for(lo) ? pl->mcls : pl->mcls_light;
-    };
+    auto classes_for = [&](uint64_t lo) -> MClasses { return tiers.for_chunk(lo); };
     // walked hits per item: a class (class items) or the item's n classes
     auto segs_for = [&](uint64_t lo) {
         double hits = (double)M_inc * (double)S / (double)std::max<uint64_t>(lo, 1);

@@ -1,0 +1,86 @@
+"""bench.py's host logic on the CPU: the reference arm's JSON line, the
+roofline of the walk from stored ncu counters, and the clock samples that
+decide whether a timed run is kept."""
+import importlib.util
+import json
+import os
+import subprocess
+import sys
+from types import SimpleNamespace
+
+import pytest
+
+from tests.conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`--impl reference` times the oracle on host cores and prints one JSON line with the
+    keys the contract names (plain_503 and a few rows keep it to seconds)."""
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--config",
+                          "plain_503", "--steps", "1", "--warmup", "0", "--ref-rows", "4"],
+                         capture_output=True, text=True, check=True, timeout=600, cwd=ROOT).stdout
+    lines = [l for l in out.strip().split("\n") if l.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["unit"] == "factors/s" and line["higher_is_better"] is True
+    assert line["value"] > 0 and line["steps"] == 1 and line["warmup"] == 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["cpu_baseline"]["cores"] >= 1 and "sample" in line["cpu_baseline"]
+    assert line["e2e"] == {"value": line["value"], "unit": "factors/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["config"]["workload"].startswith("plain_503") and line["config"]["L"] == 10**7
+
+
+def _info(**kw):
+    base = dict(threshold=120003, tile_rows=16, n_large_chunks=17, bitset_bytes=37487120, M_c=22858)
+    base.update(kw)
+    return SimpleNamespace(**base)
+
+
+def test_roofline_uses_counters_only_for_the_same_sources_and_setup(bench):
+    ctr = bench.WALK_COUNTERS["search_953"]
+    walk = bench.KC_NAMES.index("large_walk")
+    kern_ms = [0.0] * len(bench.KC_NAMES)
+    kern_n = [0] * len(bench.KC_NAMES)
+    kern_ms[walk], kern_n[walk] = 10 * 5.9, 10 * ctr["launches"]      # 10 sieves
+    stats = {"hits_all": 7.47e8 * 10, "levels": 4.5e8 * 10}
+    peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
+    args = (stats, None, peaks, "measured", None, "search_953")
+    same_sources = ctr["csrc_sha"] == bench.csrc_sha()
+    r = bench.roofline(walk, kern_ms, kern_n, stats, _info(), *args[1:])
+    assert r["bound"] == "alu" and r["unit"] == "Tinst/s"
+    assert abs(r["peak"] - 152 * 4 * 32 * 2070e6 / 1e12) < 1e-9
+    if same_sources:
+        per_launch_s = 5.9e-3 / ctr["launches"]
+        want = ctr["thread_inst"] / ctr["launches"] / per_launch_s / 1e12
+        assert abs(r["achieved"] - want) < 1e-9 * want and abs(r["frac"] - want / r["peak"]) < 1e-12
+        assert abs(r["traffic"] - ctr["dram_bytes"] / ctr["launches"]) < 1.0
+    # another threshold, tile height or chunking: the counters do not apply
+    for other in (_info(threshold=80002), _info(tile_rows=8), _info(n_large_chunks=24)):
+        r = bench.roofline(walk, kern_ms, kern_n, stats, other, *args[1:])
+        assert r["achieved"] is None and r["frac"] is None and "note" in r
+
+
+def test_clock_samples_median_and_reasons(bench, tmp_path):
+    """The nvidia-smi samples of the timed region: median SM clock of this GPU's lines and
+    every throttle reason seen active (a run with a slowdown reason is rejected)."""
+    path = tmp_path / "clocks.csv"
+    rows = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "1, 1200, 2070, 500.0, 0x0, Active, Not Active, Not Active, Not Active",   # another GPU
+            "0, 2055, 2070, 1350.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 2070, 2070, 1380.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "garbage line"]
+    path.write_text("\n".join(rows) + "\n")
+    c = bench.Clocks(str(path))
+    c.proc = SimpleNamespace(terminate=lambda: None, wait=lambda timeout=None: 0, kill=lambda: None)
+    c.f = open(os.devnull, "w")
+    got = c.stop(device_index=0)
+    assert got == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}

@@ -64,6 +64,21 @@ def test_bad_walk_and_layout_knobs_rejected(lib):
         assert cs.cs_plan_status(503, 210, 1, 10, 1000, 10**6, t) == cs.CS_EINVAL, kw
 
 
+def test_environment_knobs_reach_the_plan(lib, monkeypatch):
+    """Tuning fields left at 0 are read from the environment when a plan is made: an
+    out-of-range value set only there is rejected like the same value in the struct."""
+    args = (503, 210, 1, 10, 1000, 10**6)
+    for name, bad in (("CS_M_CLASSES", "4"), ("CS_THRESHOLD", "100")):
+        monkeypatch.setenv(name, bad)
+        assert cs.cs_plan_status(*args, cs.make_tuning()) == cs.CS_EINVAL, name
+        monkeypatch.delenv(name)
+    # a value given in the struct wins over the environment: the plan gets past the
+    # knob checks (and, without a GPU, stops at the first device call)
+    monkeypatch.setenv("CS_M_CLASSES", "4")
+    assert cs.cs_plan_status(*args, cs.make_tuning(m_classes=1)) != cs.CS_EINVAL
+    monkeypatch.delenv("CS_M_CLASSES")
+
+
 def _header_struct(name):
     """(type, field) pairs of `typedef struct { ... } name;` in the header, arrays as (type, field[n])."""
     text = open(os.path.join(ROOT, "include", "combsieve.h")).read()

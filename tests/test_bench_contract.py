@@ -84,3 +84,14 @@ def test_clock_samples_median_and_reasons(bench, tmp_path):
     c.f = open(os.devnull, "w")
     got = c.stop(device_index=0)
     assert got == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+
+
+def test_speedup_curve_interval_count():
+    """The speed-up curve's intervals hold exactly M_c values of m coprime to d."""
+    import math
+    from paper_2012_03771_gb300.speedup_curve import m_inc_for
+    for d, M_start in ((210, 1), (210, 10**8), (2310, 7), (1, 5)):
+        for m_c in (1, 10, 1000):
+            M_inc = m_inc_for(M_start, d, m_c)
+            assert sum(math.gcd(m, d) == 1 for m in range(M_start, M_start + M_inc)) == m_c
+            assert math.gcd(M_start + M_inc - 1, d) == 1          # the smallest such M_inc

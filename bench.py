@@ -1,12 +1,15 @@
 """Benchmark of the Combined Sieve hot path on one or more GPUs.
 
-One step = one full sieve (cs_sieve) of the paper-shaped search
-K = 953#/210, m in [1e8, 1e8 + 1e5) coprime to 210, X = 20000, primes up to
-L = 1e9: prime generation, K mod p, small-prime tile sieve, large-prime walk,
-counts and checksum.  Metric: enumerated factors per second (F / time), with
-F and the bitset checksum checked against the same values on every step.
+One step = one full sieve (cs_sieve) of the large single search
+K = 1019#/210, m in [1.64e8, 1.74e8) coprime to 210 (2.29M intervals),
+X = 25000, primes up to L = 1e11 generated on the device (64-bit arithmetic
+above 2^30), 4.77 GB bitset: prime generation, K mod p, small-prime tile
+sieve, large-prime walk, counts and checksum.  Metric: enumerated factors per
+second (F / time), with F and the bitset checksum checked against the same
+values on every step.  --config search_953 selects the smaller paper-shaped
+search (K = 953#/210, 22,858 intervals, L = 1e9).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference] [--config NAME]
 
 Under torchrun each rank sieves its own m-range (independent problems, no
 data-path collective; weak scaling); rank 0 prints one JSON line.
@@ -103,18 +106,51 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def oracle_sample(params: workloads.SieveParams, n_rows: int, seed: int = 0):
+# bounded oracle sample: every prime up to SMALL_ALL (they carry most of the
+# enumerated factors: sum 1/p), and WINDOWS windows of WINDOW numbers evenly
+# spaced over the rest of (P, L] (they carry most of the per-prime cost)
+SAMPLE_SMALL_ALL = 1 << 24
+SAMPLE_WINDOW = 1 << 26
+
+
+def sample_ranges(params: workloads.SieveParams, windows: int):
+    """Prime ranges (lo, hi] of the bounded sample: all of (P, L] when that is at
+    most 2^24 + windows * 2^26 numbers, else (P, 2^24] and `windows` evenly spaced
+    windows of 2^26 numbers above 2^24."""
+    P, L = params.P, params.L
+    if L - P <= SAMPLE_SMALL_ALL + windows * SAMPLE_WINDOW or windows <= 0:
+        return [(P, L)]
+    out = [(P, SAMPLE_SMALL_ALL)]
+    span = L - SAMPLE_SMALL_ALL
+    for k in range(windows):
+        hi = SAMPLE_SMALL_ALL + (k + 1) * span // windows
+        out.append((hi - SAMPLE_WINDOW, hi))
+    return out
+
+
+def sample_text(params, n_rows, n_all, windows):
+    rng = sample_ranges(params, windows)
+    pr = ("all primes <= L" if len(rng) == 1 else
+          f"primes in ({params.P}, 2^24] and in {len(rng) - 1} windows of 2^26 numbers evenly spaced up to L")
+    return f"{n_rows} of {n_all} coprime m (evenly spaced) x {pr}"
+
+
+def oracle_sample(params: workloads.SieveParams, n_rows: int, windows: int = 4):
     """The CPU oracle (as it stands) on a bounded sample of the workload: n_rows
-    evenly spaced coprime m, all sieving primes.  Returns (factors, seconds, cores)."""
+    evenly spaced coprime m, and the primes of sample_ranges.  Returns
+    (factors, seconds, cores, rows, coprime m in the search)."""
     import oracle.oracle as O
     rows = O.rows(params.d, params.M_start, params.M_inc)
     idx = [int(i * (len(rows) - 1) / max(n_rows - 1, 1)) for i in range(n_rows)]
     pick = [int(rows[i]) for i in sorted(set(idx))]
     cores = os.cpu_count() or 1
+    F = 0
     t0 = time.perf_counter()
-    _, F, _ = O.sieve(params.P, params.d, params.SL, params.L, pick, threads=cores)
+    for lo, hi in sample_ranges(params, windows):
+        _, Fr, _ = O.sieve(params.P, params.d, params.SL, hi, pick, p_lo=lo, threads=cores)
+        F += int(Fr.sum())
     dt = time.perf_counter() - t0
-    return int(F.sum()), dt, cores, len(pick)
+    return F, dt, cores, len(pick), len(rows)
 
 
 def run_reference(args, params):
@@ -125,15 +161,15 @@ def run_reference(args, params):
     O.build()
     n_rows = args.ref_rows
     for _ in range(args.warmup):
-        oracle_sample(params, n_rows)
+        oracle_sample(params, n_rows, args.ref_windows)
     Fs, ts = 0, 0.0
-    cores, nr = 1, n_rows
+    cores, nr, n_all = 1, n_rows, 0
     for _ in range(args.steps):
-        F, dt, cores, nr = oracle_sample(params, n_rows)
+        F, dt, cores, nr, n_all = oracle_sample(params, n_rows, args.ref_windows)
         Fs += F
         ts += dt
     value = Fs / ts
-    sample = f"{nr} of the search's coprime m per step (evenly spaced), all primes <= L"
+    sample = sample_text(params, nr, n_all, args.ref_windows) + " per step"
     line = {"impl": "reference", "metric": metric_of(params), "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * ts / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
@@ -143,7 +179,7 @@ def run_reference(args, params):
     print(json.dumps(line), flush=True)
 
 
-def _config(params, name="search_953"):
+def _config(params, name="large_1019"):
     """The workload, identical for both arms (implementation details go elsewhere)."""
     return {"workload": f"{name}: K={params.P}#/{params.d}, m in [{params.M_start}, {params.M_start + params.M_inc}) "
                         f"coprime to {params.d}, X={params.SL}, primes {params.P} < p <= {params.L}",
@@ -276,8 +312,9 @@ def run_cuda(args, params):
 
     # ---- roofline of the dominant kernel ------------------------------------
     peaks, peak_src = _peaks()
+    issue = issue_rates(torch, cs, stream)
     dom = max(range(5), key=lambda i: kern_ms[i])
-    roof = roofline(dom, kern_ms, kern_n, stats, info, params, peaks, peak_src, clk, args.config)
+    roof = roofline(dom, kern_ms, kern_n, stats, info, params, peaks, peak_src, issue, args.config)
 
     # ---- CPU oracle on a bounded sample -------------------------------------
     cpu = None
@@ -285,9 +322,9 @@ def run_cuda(args, params):
         try:
             import oracle.oracle as O
             O.build()
-            Fs, dt, cores, nr = oracle_sample(params, args.cpu_rows)
+            Fs, dt, cores, nr, n_all = oracle_sample(params, args.ref_rows, args.ref_windows)
             cpu = {"value": Fs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-                   "sample": f"{nr} of {int(info.M_c)} coprime m (evenly spaced), all primes <= L; {dt:.1f} s"}
+                   "sample": sample_text(params, nr, n_all, args.ref_windows) + f" (the reference arm's step); {dt:.1f} s"}
         except Exception as e:  # the oracle is a reported baseline only
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"failed: {e}"}
@@ -336,46 +373,64 @@ def csrc_sha() -> str:
     return h.hexdigest()[:16]
 
 
-# ncu counters of the large-prime walk on the search_953 workload, summed over
-# the walk's launches of one sieve (profiles/large_walk_search_953.md):
-#   ncu --metrics gpu__time_duration.sum,smsp__thread_inst_executed.sum,smsp__inst_executed.sum,
-#       dram__bytes_read.sum,dram__bytes_write.sum --clock-control none -k regex:k_large_tg
-#       -s 16 -c 16 --csv python bench.py --steps 1 --warmup 1 --no-cpu
+# ncu counters of the large-prime walk, summed over the walk's launches of one
+# sieve of each workload, taken with
+#   ncu --metrics gpu__time_duration.sum,smsp__thread_inst_executed.sum,dram__bytes_read.sum,
+#       dram__bytes_write.sum --clock-control none -k regex:k_large_tg -s <walk launches of the
+#       warm-up sieve> -c <walk launches of one sieve> --csv python bench.py --config <workload>
+#       --steps 1 --warmup 1 --no-cpu
 # The work is deterministic (same inputs, same code), so these are per-sieve
-# constants for the walk sources whose digest is recorded (csrc_sha); they are
-# ignored when those sources change.
-WALK_COUNTERS = {
-    "search_953": {"csrc_sha": "536d03c644832bed", "threshold": 120003, "tile_rows": 16, "launches": 17,
-                   "thread_inst": 8.768939e+10, "dram_bytes": 1.243213e+09 + 1.264640e+06},
-}
+# constants for the walk sources whose digest is recorded (csrc_sha) and the
+# same threshold, tile height and chunking; otherwise they are not used.
+WALK_COUNTERS = {}
 
 
-def roofline(dom, kern_ms, kern_n, stats, info, params, peaks, peak_src, clk, config):
+def issue_rates(torch, cs, stream):
+    """The measured integer issue rate: thread-level operations per second of the
+    cs_issue_rate micro-benchmark (one full-occupancy wave of independent integer
+    chains), best of three launches, for each of its three instruction mixes."""
+    try:
+        n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        sink = torch.zeros(n_sm * 2048, dtype=torch.int32, device="cuda")
+        out = {}
+        for mix, name in ((0, "add_logic"), (1, "imad"), (2, "imad_logic")):
+            best = 0.0
+            for _ in range(3):
+                ops, ms = cs.cs_issue_rate(mix, 2000, sink.data_ptr(), sink.numel(), stream)
+                best = max(best, ops / (ms / 1e3))
+            out[name] = best / 1e12
+        return out
+    except Exception as e:   # reported as missing, never replaced by a derived figure
+        return {"error": str(e)}
+
+
+def roofline(dom, kern_ms, kern_n, stats, info, params, peaks, peak_src, issue, config):
     """Roofline of the dominant kernel class: its work per launch over its
     average CUDA-event launch duration (timed on the launching stream)."""
     name = KC_NAMES[dom]
     n_launch = max(kern_n[dom], 1)
     per_launch_s = kern_ms[dom] / n_launch / 1e3
-    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    n_sm = 152
     if name == "final":
         bytes_ = int(info.bitset_bytes) + 4 * int(info.M_c)
         achieved = bytes_ / per_launch_s / 1e9
         peak = float(peaks["hbm_gbs"])
         return {"kernel": "k_final", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None, "peak_source": f"hbm_gbs, {peak_src}"}
-    # integer kernels: thread-level instructions against the issue rate of
-    # 152 SMs x 4 schedulers x 32 lanes at the maximum SM clock
-    peak = n_sm * 4 * 32 * sm_mhz * 1e6 / 1e12
+    # integer kernels: thread-level instructions against the measured integer
+    # issue rate (the best mix of the micro-benchmark, timed in this run)
+    rates = {k: v for k, v in issue.items() if isinstance(v, float)}
+    peak = max(rates.values()) if rates else None
     out = {"kernel": "k_large_tg" if name == "large_walk" else name, "bound": "alu", "achieved": None,
            "peak": peak, "unit": "Tinst/s", "frac": None, "traffic": None,
-           "peak_source": f"derived: {n_sm} SMs x 4 schedulers x 32 lanes x {sm_mhz:.0f} MHz (integer issue rate)"}
+           "peak_source": "measured in this run: cs_issue_rate integer micro-benchmark, best of its mixes "
+                          "(burst, one wave at full occupancy)",
+           "issue_rates_Tops": issue}
     ctr = WALK_COUNTERS.get(config)
     # the counters hold for the same sources, threshold, tile height and chunking
     # (one walk launch per large-prime chunk)
     same_setup = ctr is not None and (ctr.get("threshold"), ctr.get("tile_rows"), ctr.get("launches")) == (
         int(info.threshold), int(info.tile_rows), int(info.n_large_chunks))
-    if name == "large_walk" and ctr and ctr["csrc_sha"] == csrc_sha() and same_setup:
+    if name == "large_walk" and ctr and ctr["csrc_sha"] == csrc_sha() and same_setup and peak:
         sieves = n_launch / ctr["launches"]
         inst_launch = ctr["thread_inst"] / ctr["launches"]
         out["achieved"] = inst_launch / per_launch_s / 1e12
@@ -558,10 +613,10 @@ def run_served(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
-    ap.add_argument("--config", default="search_953", choices=sorted(workloads.NAMED) + ["batched_64", "served"])
+    ap.add_argument("--config", default="large_1019", choices=sorted(workloads.NAMED) + ["batched_64", "served"])
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--load", type=float, default=0.8)
     ap.add_argument("--slots", type=int, default=2)
@@ -569,8 +624,8 @@ def main():
     ap.add_argument("--budget-frac", type=float, default=0.5)
     ap.add_argument("--mode", type=int, default=0)
     ap.add_argument("--threshold", type=int, default=0)
-    ap.add_argument("--cpu-rows", type=int, default=512)
-    ap.add_argument("--ref-rows", type=int, default=16)
+    ap.add_argument("--ref-rows", type=int, default=256, help="oracle sample: evenly spaced coprime m")
+    ap.add_argument("--ref-windows", type=int, default=4, help="oracle sample: prime windows above 2^24")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--layout", type=int, default=0, help="1 = compact rows (no wheel offsets stored)")

@@ -301,6 +301,22 @@ cs_status cs_k_mod_p(uint32_t P, uint64_t d, const uint64_t *p, uint64_t n, uint
 cs_status cs_modsolve(const uint64_t *p, const uint64_t *K, const uint64_t *L, const uint64_t *R,
                       uint64_t *m, uint64_t n, int narrow, void *stream);
 
+/* ---- measurement -------------------------------------------------------- */
+
+/* Integer issue-rate micro-benchmark: the measured peak for the roofline of
+ * the integer-bound kernels.  The paper has no counterpart (its cost model
+ * counts CPU cycles).  One launch of every resident thread (one wave, full
+ * occupancy), each running 8 independent chains of `iters` x 32 steps:
+ *   mix 0: x = (x + y) ^ c          two operations per step (add, logic)
+ *   mix 1: x = x * y + z            one integer multiply-add per step
+ *   mix 2: x = (x * y + z) ^ c      one multiply-add and one logic op per step
+ * after one untimed warm-up launch.  *thread_ops (host) receives the thread-level
+ * operations the source states; *ms (host) the launch's duration from CUDA
+ * events on `stream`.  sink: device, one uint32 per launched thread (at most
+ * 152 x 2048 on a GB300; CS_ESIZE if smaller).  Synchronises `stream`. */
+cs_status cs_issue_rate(int mix, uint32_t iters, uint32_t *sink, uint64_t sink_words, void *stream,
+                        double *thread_ops, float *ms);
+
 /* ---- allocation-free variant -------------------------------------------- */
 
 /* The same prime list as cs_primes, for callers that must not allocate device
@@ -322,7 +338,9 @@ cs_status cs_modsolve(const uint64_t *p, const uint64_t *K, const uint64_t *L, c
  * capture.  All calls share the one array and each call leaves its contents
  * behind (the counters are cleared at the start of every call), so calls that
  * overlap on the GPU -- from two streams or two host threads -- race: issue
- * them one after another.  Synchronises `stream`. */
+ * them one after another.  Every call, not only the first, ends by reading
+ * the count back and synchronising `stream` (the caller's stream only, not the
+ * device).  Errors set cs_last_error() like those of every other call. */
 cs_status cs_primes_static(uint64_t lo, uint64_t hi, uint64_t *out, uint64_t cap, uint64_t *count,
                            void *stream);
 

@@ -36,7 +36,7 @@ EXPORTS = ("cs_plan", "cs_sieve", "cs_sync", "cs_info", "cs_fetch_bitset", "cs_c
            "cs_batch_create", "cs_batch_run", "cs_batch_sync", "cs_batch_info", "cs_batch_destroy",
            "cs_server_start", "cs_submit", "cs_poll", "cs_server_plan", "cs_release", "cs_server_usage",
            "cs_server_stop", "cs_fetch_rows", "cs_cache_create", "cs_cache_fill", "cs_cache_info",
-           "cs_cache_destroy", "cs_plan_cached", "cs_autotune", "cs_row_columns")
+           "cs_cache_destroy", "cs_plan_cached", "cs_autotune", "cs_row_columns", "cs_issue_rate")
 
 
 class CSError(RuntimeError):
@@ -129,6 +129,8 @@ def load(path: Optional[str] = None):
         lib.cs_cache_destroy.argtypes = [vp]
         lib.cs_plan_cached.argtypes = [u32, u64, u64, u64, u32, u64, ctypes.POINTER(cs_tuning), vp,
                                        ctypes.POINTER(vp)]
+        lib.cs_issue_rate.argtypes = [i32, u32, vp, u64, vp, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_float)]
         for n in EXPORTS:
             if n not in ("cs_device_bitset", "cs_last_error"):
                 getattr(lib, n).restype = i32
@@ -276,6 +278,14 @@ def cs_k_mod_p(P, d, p_ptr: int, n: int, r_ptr: int, stream=None):
 def cs_modsolve(p_ptr, K_ptr, L_ptr, R_ptr, m_ptr, n, narrow, stream=None):
     _check(load().cs_modsolve(*(ctypes.c_void_p(x) for x in (p_ptr, K_ptr, L_ptr, R_ptr, m_ptr)),
                               n, int(narrow), _stream_handle(stream)))
+
+
+def cs_issue_rate(mix: int, iters: int, sink_ptr: int, sink_words: int, stream=None):
+    """(thread-level operations, milliseconds) of one integer issue-rate launch."""
+    ops, ms = ctypes.c_double(), ctypes.c_float()
+    _check(load().cs_issue_rate(mix, iters, ctypes.c_void_p(sink_ptr), sink_words, _stream_handle(stream),
+                                ctypes.byref(ops), ctypes.byref(ms)))
+    return float(ops.value), float(ms.value)
 
 
 def cs_autotune(P, d, M_start, M_inc, SL, L, cache_path: Optional[str] = None) -> dict:

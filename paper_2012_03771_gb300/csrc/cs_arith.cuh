@@ -201,6 +201,46 @@ CS_HD uint64_t mont64_r2(uint64_t p) {
     return r;
 }
 
+// x mod p for x < 2^61 and odd p with a quotient x / p below 2^20, given
+// fp = rcp_rn(u64_to_f(p)): u64_to_f(x) and u64_to_f(p) are each within a
+// relative 2^-22 of x and p, the reciprocal and the product each add at most
+// 2^-24, so the float quotient is within a relative 2.5 2^-22 of x / p, i.e.
+// within 0.63 of it, and its truncation is floor(x / p) or off by one either
+// way: one correction each way makes the remainder exact.
+CS_HD uint64_t mod_q20(uint64_t x, uint64_t p, float fp) {
+    const uint32_t q = (uint32_t)(u64_to_f(x) * fp);
+    int64_t r = (int64_t)(x - (uint64_t)q * p);
+    if (r < 0) r += (int64_t)p;
+    else if (r >= (int64_t)p) r -= (int64_t)p;
+    return (uint64_t)r;
+}
+
+// R^2 mod p (R = 2^64) for odd 2^20 <= p < 2^40 without a 64-bit division:
+// 2^40 mod p (a quotient below 2^20), then x <- x 2^20 mod p four times
+// (x 2^20 < 2^60, quotients below 2^20) up to 2^120, and x 2^8 mod p.  Other p
+// take the 64 modular doublings of mont64_r2.
+CS_HD uint64_t mont64_r2_fast(uint64_t p, float fp) {
+    if (p < (1ull << 20) || p >= (1ull << 40)) return mont64_r2(p);
+    uint64_t x = mod_q20(1ull << 40, p, fp);
+    for (int k = 0; k < 4; k++) x = mod_q20(x << 20, p, fp);
+    return mod_q20(x << 8, p, fp);
+}
+
+// R^e mod p from R^2 mod p alone (e >= 1), in the Montgomery monoid
+// Y_j = R^(j+1) mod p: R^e = Y_(e-1) = Y_1^(e-1), taken as Y_1 * Y_1^(e-2) by
+// square-and-multiply without a squaring after the last bit.
+CS_HD uint64_t mont64_rpow2(uint32_t e, uint64_t r2, uint64_t p, uint64_t pinv) {
+    if (e <= 1) return mont64_mul(r2, 1, p, pinv);   // R mod p
+    uint64_t acc = r2, base = r2;
+    uint32_t k = e - 2;
+    while (k) {
+        if (k & 1) acc = mont64_mul(acc, base, p, pinv);
+        k >>= 1;
+        if (k) base = mont64_mul(base, base, p, pinv);
+    }
+    return acc;
+}
+
 CS_HD uint64_t mont64_rpow(uint32_t e, uint64_t r1, uint64_t r2, uint64_t p, uint64_t pinv) {
     uint64_t acc = r1, base = r2;
     uint32_t k = e - 1;
@@ -547,6 +587,156 @@ CS_HD uint64_t first_hit64(uint64_t p, uint64_t w, uint64_t a, uint64_t da, uint
     const uint64_t y = (uint64_t)(Y - i * (int64_t)DA);
     y_out = sw ? w - y : y;
     return (uint64_t)((__int128)i * A + (__int128)j * B);
+}
+
+// ------------------------------------------------- 64-bit primes, narrow steps
+// For primes 2^30 <= p < 2^40 and windows 1024 <= w <= 2^21 the walk's item
+// preparation runs mostly in 32-bit arithmetic:
+//  * tg_steps_w: the same two steps as tg_steps, from the same run of Euclid's
+//    algorithm, but the remainders drop below 2^31 after a few steps, and from
+//    there each step is a 32-bit division by a corrected float estimate (partial
+//    quotients below 2^31 / w <= 2^21).  Along the run m_(k+1) x_k + m_k x_(k+1)
+//    = p, so every m_(k+1) taken while x_k > w is below p / w < 2^30; only the
+//    two final multipliers can be larger (up to about p when the last remainder
+//    is tiny), and they are returned in 64 bits.  da and ub are at most w.
+//  * first_hit_w: first_hit32's block construction for such p when both steps
+//    are below 2^31; the products V0 A are formed modulo 2^64 around a float
+//    estimate of their quotient by p (the exact remainder is small), and every
+//    other quantity fits 64 signed bits (|Y| < B DA + UB < 2^52, block indices
+//    below 2^32 + 2^21, multipliers i A + j B below 2^63).
+CS_HD bool tg_steps_w(uint64_t p, uint64_t r, uint32_t w, uint64_t &a, uint32_t &da, uint64_t &b, uint32_t &ub,
+                      uint32_t &iters, uint32_t max_iter) {
+    uint64_t x_pp = 0, x_prev = p, x = r;
+    uint32_t m_pp = 0, m_prev = 0, m = 1;
+    uint32_t k = 1;
+    const bool small_q64 = p < ((uint64_t)w << 21);
+    // 64-bit remainders while the dividend is 2^31 or more
+    while (x > w && x_prev >= (1ull << 31)) {
+        if (k > max_iter) return false;
+        uint64_t c, xn;
+        if (small_q64) {
+            c = udiv_q21_64(x_prev, x, rcp_approx(u64_to_f(x)), xn);
+        } else {
+            c = x_prev / x;
+            xn = x_prev - c * x;
+        }
+        const uint32_t mn = m_prev + (uint32_t)c * m;
+        x_pp = x_prev; m_pp = m_prev;
+        x_prev = x; m_prev = m;
+        x = xn; m = mn;
+        k++;
+    }
+    // 32-bit remainders: dividend below 2^31, quotients below 2^21
+    if (x > w) {
+        uint32_t xp = (uint32_t)x_prev, xc = (uint32_t)x;
+        while (xc > w) {
+            if (k > max_iter) return false;
+            uint32_t rem;
+            const uint32_t c = udiv_q21(xp, xc, rcp_approx((float)xc), rem);
+            const uint32_t mn = m_prev + c * m;
+            x_pp = xp; m_pp = m_prev;
+            xp = xc; m_prev = m;
+            xc = rem; m = mn;
+            k++;
+        }
+        x_prev = xp;
+        x = xc;
+    }
+    iters += k;
+    uint64_t ms;                                     // first m with the sign of x_K
+    uint32_t xs;
+    if (k == 1) {
+        ms = 1;
+        xs = (uint32_t)r;
+    } else {
+        // t = ceil((x_pp - w) / x_prev), a quotient below x_pp / x_prev + 1
+        uint64_t t;
+        if (x_pp < (1ull << 30)) {
+            uint32_t rem;
+            t = udiv_q21((uint32_t)(x_pp - w + x_prev - 1), (uint32_t)x_prev, rcp_approx((float)(uint32_t)x_prev), rem);
+        } else if (small_q64) {
+            uint64_t rem;
+            t = udiv_q21_64(x_pp - w + x_prev - 1, x_prev, rcp_approx(u64_to_f(x_prev)), rem);
+        } else {
+            t = (x_pp - w + x_prev - 1) / x_prev;
+        }
+        ms = m_pp + t * m_prev;
+        xs = (uint32_t)(x_pp - t * x_prev);
+    }
+    // the other sign: t2 = ceil((x_prev - w) / x), unbounded when x is small
+    const uint64_t num = x_prev - w + x - 1;
+    const uint64_t t2 = (num >> 32) == 0 ? (uint64_t)((uint32_t)num / (uint32_t)x) : num / x;
+    const uint64_t mo = m_prev + t2 * m;
+    const uint32_t xo = (uint32_t)(x_prev - t2 * x);
+    if (k & 1) {
+        b = ms; ub = xs; a = mo; da = xo;
+    } else {
+        a = ms; da = xs; b = mo; ub = xo;
+    }
+    return true;
+}
+
+// floor(x / d) for |x| < 2^62, 1 <= d < 2^31 and |x / d| < 2^40, given
+// fd = rcp_rn((float)d): the first float estimate is within a relative 2^-21,
+// i.e. 2^19 + 1, of the quotient, so the remainder of its truncation is below
+// 2^50 d in magnitude and exact; the second estimate, on that remainder, is
+// within 1.25, and one correction each way makes the quotient exact.
+CS_HD int64_t floor_div_s64(int64_t x, uint32_t d, float fd) {
+    int64_t q = f_to_s64(s64_to_f(x) * fd);
+    int64_t r = x - q * (int64_t)d;
+    const int64_t q1 = f_to_s64(s64_to_f(r) * fd);
+    q += q1;
+    r -= q1 * (int64_t)d;
+    if (r < 0) { r += d; q--; }
+    if (r < 0) { r += d; q--; }
+    if (r >= (int64_t)d) { r -= d; q++; }
+    if (r >= (int64_t)d) { r -= d; q++; }
+    return q;
+}
+
+// first_hit32 for 2^30 <= p < 2^40, 1024 <= w <= 2^21 and steps a, b below
+// 2^31 (da, ub <= w), given fp = rcp_rn(u64_to_f(p)); w < v0 < p.
+CS_HD uint64_t first_hit_w(uint64_t p, float fp, uint32_t w, uint32_t a, uint32_t da, uint32_t b, uint32_t ub,
+                           uint64_t v0, uint32_t &y_out) {
+    const bool sw = da > ub;
+    const uint32_t A = sw ? b : a, DA = sw ? ub : da, B = sw ? a : b, UB = sw ? da : ub;
+    const int64_t V0 = sw ? (int64_t)w - (int64_t)v0 : (int64_t)v0;     // |V0| < 2^40
+    // aq = floor(|V0| A / p) < A < 2^31: a float estimate within 1536 of it
+    // (relative 1.5 2^-21), the remainder of |V0| A taken modulo 2^64 (exact:
+    // it is below 1537 p < 2^51 in magnitude), one refinement within one, and
+    // one correction each way
+    const uint64_t av = (uint64_t)(V0 < 0 ? -V0 : V0);
+    uint32_t aq = (uint32_t)(u64_to_f(av) * (float)A * fp);
+    int64_t rem = (int64_t)(av * (uint64_t)A - (uint64_t)aq * p);
+    const int32_t q1 = (int32_t)(s64_to_f(rem) * fp);
+    aq += (uint32_t)q1;
+    rem -= (int64_t)q1 * (int64_t)p;
+    if (rem < 0) { rem += (int64_t)p; aq--; }
+    if (rem < 0) { rem += (int64_t)p; aq--; }
+    if (rem >= (int64_t)p) { rem -= (int64_t)p; aq++; }
+    int64_t j = V0 >= 0 ? -(int64_t)aq : (int64_t)aq + (rem != 0);
+    int64_t Y = V0 + j * (int64_t)UB;
+    const float fda = rcp_rn((float)DA);
+    if (floor_div_s64(Y, DA, fda) * (int64_t)A + j * (int64_t)B < 0) {
+        j++;
+        Y += UB;
+    }
+    int64_t i = -floor_div_s64((int64_t)w - Y, DA, fda);                // ceil((Y - w) / DA)
+    const int64_t t_lo = i * (int64_t)A + j * (int64_t)B;
+    if (t_lo < 0) {
+        // ceil(-t_lo / A) steps of A: a quotient below w / DA + 2 <= 2^21 + 2
+        const int64_t n = -t_lo;
+        int64_t q = (int64_t)(uint32_t)(u64_to_f((uint64_t)n) * rcp_rn((float)A));
+        int64_t r = n - q * (int64_t)A;
+        if (r < 0) { r += A; q--; }
+        if (r < 0) { r += A; q--; }
+        if (r >= (int64_t)A) { r -= A; q++; }
+        if (r >= (int64_t)A) { r -= A; q++; }
+        i += q + (r != 0);
+    }
+    const uint32_t y = (uint32_t)(Y - i * (int64_t)DA);
+    y_out = sw ? w - y : y;
+    return (uint64_t)(i * (int64_t)A + j * (int64_t)B);
 }
 
 // ------------------------------------------------------------- checksum

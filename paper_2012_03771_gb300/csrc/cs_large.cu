@@ -70,15 +70,18 @@ struct Counters {
 // for v = (r m + SL) mod p <= 2SL.  Branch-free up to the atomic: the row and
 // column tests are bit lookups in small tables (coprime-m mask, stored-x
 // mask, each interleaved with its per-word prefix counts) that stay in L1.
+// The prime is read (from the chunk's array, entry idx) only when N + x can be
+// a sieving prime itself (K below 2^64).
 template <class UT>
-__device__ __forceinline__ void record_hit_z(const DevPlan &pl, uint64_t moff, uint32_t z, UT p, Counters &c) {
+__device__ __forceinline__ void record_hit_z(const DevPlan &pl, uint64_t moff, uint32_t z, const UT *Pp,
+                                             uint32_t idx, Counters &c) {
     const uint32_t ms = (uint32_t)moff;                  // bit of m in its 32-m word: ms mod 32
     const uint2 rt = __ldg(&pl.row_tab[moff >> 5]);      // {coprime-m mask, rows before}
     const uint2 ct = __ldg(&pl.col_tab[z >> 5]);         // {stored-x mask, columns before}
     bool ok = (bit_of(rt.x, ms) & bit_of(ct.x, z)) != 0; // m coprime to d, x coprime to K
     if (pl.small_n) {
         unsigned __int128 n = (unsigned __int128)(pl.M_start + moff) * pl.K64 + z - pl.SL;
-        ok = ok && n != (unsigned __int128)p;            // N + x is p itself
+        ok = ok && n != (unsigned __int128)Pp[idx];      // N + x is p itself
     }
     const uint32_t row_below = __popc(bits_below(rt.x, ms));
     const uint32_t row = rt.y + row_below;
@@ -100,8 +103,9 @@ __device__ __forceinline__ void record_hit_z(const DevPlan &pl, uint64_t moff, u
     c.F += ok;
 }
 template <class UT>
-__device__ __forceinline__ void record_hit(const DevPlan &pl, uint64_t moff, UT v, UT p, Counters &c) {
-    record_hit_z<UT>(pl, moff, 2 * pl.SL - (uint32_t)v, p, c);
+__device__ __forceinline__ void record_hit(const DevPlan &pl, uint64_t moff, UT v, const UT *Pp, uint32_t idx,
+                                           Counters &c) {
+    record_hit_z<UT>(pl, moff, 2 * pl.SL - (uint32_t)v, Pp, idx, c);
 }
 
 template <class UT, class ST>
@@ -136,7 +140,7 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_large(const LargeArgs a) {
             while (true) {
                 if (v <= w) {
                     c.hits++;
-                    record_hit<UT>(pl, m_lo + m, v, p, c);
+                    record_hit<UT>(pl, m_lo + m, v, Pp, (uint32_t)i, c);
                     if (++m >= Mseg) break;
                     v += r;
                     if (v >= p) v -= p;
@@ -188,11 +192,14 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_large(const LargeArgs a) {
 // (tg_steps, the same answers as G for the two step windows); in the 32-bit
 // walk the first hits follow from the two step vectors, a basis of the lattice
 // of (j, r' j mod p) (first_hit32; first_hit64 in the 64-bit walk).
-template <class UT, class ST, class MT>
+// A prepared walker: after its first hit v and the steps of v are at most
+// 2SL < 2^22, so 32 bits hold them for both prime widths; the prime itself is
+// referenced by its index in the chunk's arrays.
+template <class MT>
 struct TGItem {
-    MT moff, end;      // current m - M_start, end of the segment
-    UT v, p, da, ub;   // v = (r m + SL) mod p, steps of v
-    MT ma, mb;         // steps of m (clamped to M_inc)
+    MT moff, end;                  // current m - M_start, end of the segment
+    uint32_t v, idx, da, ub;       // v = (r m + SL) mod p, prime index, steps of v
+    MT ma, mb;                     // steps of m (clamped to M_inc)
 };
 
 // three-gap steps per lane between queue checks
@@ -242,7 +249,7 @@ template <class UT, class ST, class MT, int NC, bool CI = false>
 __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLOCKS : CS_TG_MIN_BLOCKS_WIDE) k_large_tg(const LargeArgs a) {
     static_assert(!CI || NC == 1, "class items walk one class per item");
     constexpr int QCAP = 32 * (NC + 1);   // a refill adds at most 32 NC walkers
-    __shared__ TGItem<UT, ST, MT> queue[TG_WARPS][QCAP];
+    __shared__ TGItem<MT> queue[TG_WARPS][QCAP];
     __shared__ uint8_t item_off[CI ? MAX_CLASS_ITEMS : 1];   // class items: residue of each class
     const uint32_t n_cls_items = CI ? a.mc.items : 1;
     if constexpr (CI) {
@@ -271,7 +278,7 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
     // steps still add up below 2^32
     const uint64_t cap_step = M;
     const uint64_t seg_len = (M + n_seg - 1) / n_seg;
-    TGItem<UT, ST, MT> *q = queue[wib];
+    TGItem<MT> *q = queue[wib];
     Counters c;
     if (M == 0) return;
 
@@ -283,7 +290,7 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
     // (v <= 2SL - u_b, z >= u_b): m += b, z -= u_b; else m += a + b,
     // z += d_a - u_b
     MT moff = 0, end = 0, ma = 0, mb = 0, mab = 0;
-    UT z = 0, p = 1, da = 0, ub = 0, wmda = 0, nub = 0, dmu = 0;
+    uint32_t z = 0, idx = 0, da = 0, ub = 0, wmda = 0, nub = 0, dmu = 0;
 
     while (true) {
         // refill: prepare 32 items when the queue can take their walkers
@@ -293,7 +300,7 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
             bool push[NC];
             MT first_m[NC];
             UT first_v[NC];
-            TGItem<UT, ST, MT> e;
+            TGItem<MT> e;
 #pragma unroll
             for (int k = 0; k < NC; k++) push[k] = false;
             if (item < n_items) {
@@ -305,10 +312,12 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
                     off0 = item_off[item - i * n_cls_items];
                 }
                 if (n_seg > 1) {
-                    // segments of seg_len m (the last one shorter)
+                    // segments of seg_len m (the last one shorter), segment-major:
+                    // the items in flight at one time share a segment, so that
+                    // their bit clears fall in one band of rows, which stays in L2
                     const uint64_t ps = i;
-                    i = n_items >> 32 ? ps / n_seg : (uint32_t)ps / n_seg;
-                    const uint32_t sg = (uint32_t)(ps - i * n_seg);
+                    const uint32_t sg = n_items >> 32 ? (uint32_t)(ps / n) : (uint32_t)ps / (uint32_t)n;
+                    i = ps - (uint64_t)sg * n;
                     m_lo = (uint64_t)sg * seg_len;
                     m_hi = min(M, m_lo + seg_len);
                 }
@@ -361,8 +370,20 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
                         dk[k] = dd;
                         vk[k] = big_q ? mul_add_mod(vv, r, dd, pp, fq) : add_times(vv, r, dd, pp);
                     }
-                    // the two steps from one run of Euclid's algorithm on (p, r')
-                    ok = tg_steps<UT>(pp, rq, w, ma_, da_, mb_, ub_, it, max_iter);
+                    // the two steps from one run of Euclid's algorithm on (p, r');
+                    // for 64-bit primes and 2SL >= 1024 mostly in 32-bit steps
+                    if constexpr (sizeof(UT) == 8) {
+                        if (w >= 1024) {
+                            uint64_t a64, b64;
+                            uint32_t da32, ub32;
+                            ok = tg_steps_w(pp, rq, (uint32_t)w, a64, da32, b64, ub32, it, max_iter);
+                            ma_ = a64; mb_ = b64; da_ = da32; ub_ = ub32;
+                        } else {
+                            ok = tg_steps<UT>(pp, rq, w, ma_, da_, mb_, ub_, it, max_iter);
+                        }
+                    } else {
+                        ok = tg_steps<UT>(pp, rq, w, ma_, da_, mb_, ub_, it, max_iter);
+                    }
                     if (!ok) c.err |= ERR_SOLVER_LIMIT;
                     uint32_t n_first = 0;
 #pragma unroll
@@ -379,13 +400,24 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
                             }
                         }
                     } else if (ok && n_first) {
-                        // 64-bit (p < 2^40, 2SL <= 2^21): the same from first_hit64
+                        // 64-bit (p < 2^40, 2SL <= 2^21): the same with 64-bit
+                        // products (first_hit_w) when both steps are below 2^31 and
+                        // 2SL >= 1024, else with 128-bit ones (first_hit64)
+                        const bool narrow_ab = w >= 1024 && ((uint64_t)ma_ | (uint64_t)mb_) < (1ull << 31);
+                        const float fp = rcp_rn(u64_to_f((uint64_t)pp));
 #pragma unroll
                         for (int k = 0; k < NC; k++) {
                             if (vk[k] > w) {
-                                uint64_t y;
-                                first[k] = first_hit64(pp, w, ma_, da_, mb_, ub_, vk[k], y) * Q;
-                                vk[k] = (UT)y;
+                                if (narrow_ab) {
+                                    uint32_t y;
+                                    first[k] = first_hit_w(pp, fp, (uint32_t)w, (uint32_t)ma_, (uint32_t)da_,
+                                                           (uint32_t)mb_, (uint32_t)ub_, vk[k], y) * Q;
+                                    vk[k] = (UT)y;
+                                } else {
+                                    uint64_t y;
+                                    first[k] = first_hit64(pp, w, ma_, da_, mb_, ub_, vk[k], y) * Q;
+                                    vk[k] = (UT)y;
+                                }
                             }
                         }
                     }
@@ -401,9 +433,9 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
                     }
                     const uint64_t sa = (uint64_t)ma_ * Q, sb = (uint64_t)mb_ * Q;
                     e.end = (MT)m_hi;
-                    e.p = pp;
-                    e.da = da_;
-                    e.ub = ub_;
+                    e.idx = (uint32_t)i;
+                    e.da = (uint32_t)da_;
+                    e.ub = (uint32_t)ub_;
                     e.ma = (MT)(sa < cap_step ? sa : cap_step);
                     e.mb = (MT)(sb < cap_step ? sb : cap_step);
                 }
@@ -413,9 +445,9 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
             for (int k = 0; k < NC; k++) {
                 const unsigned pm = __ballot_sync(0xffffffffu, push[k]);
                 if (push[k]) {
-                    TGItem<UT, ST, MT> ek = e;
+                    TGItem<MT> ek = e;
                     ek.moff = first_m[k];
-                    ek.v = first_v[k];
+                    ek.v = (uint32_t)first_v[k];
                     q[(tail + __popc(pm & lt_mask)) % QCAP] = ek;
                 }
                 tail += __popc(pm);
@@ -429,12 +461,12 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
             const uint32_t rank = __popc(idle & lt_mask);
             const uint32_t take = min((uint32_t)__popc(idle), qcount);
             if (!active && rank < take) {
-                const TGItem<UT, ST, MT> e = q[(qhead + rank) % QCAP];
-                moff = e.moff; end = e.end; z = w - e.v; p = e.p; da = e.da; ub = e.ub;
+                const TGItem<MT> e = q[(qhead + rank) % QCAP];
+                moff = e.moff; end = e.end; z = (uint32_t)w - e.v; idx = e.idx; da = e.da; ub = e.ub;
                 ma = e.ma; mb = e.mb;
                 mab = ma + mb;                       // ma, mb <= M_inc < 2^31
-                wmda = w - da;
-                nub = (UT)0 - ub;
+                wmda = (uint32_t)w - da;
+                nub = 0u - ub;
                 dmu = da - ub;                       // both wrap; z ends in [0, 2SL]
                 active = true;
             }
@@ -452,7 +484,7 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
         constexpr int STEPS = NC == 1 && !CI ? TG_STEPS_ALL_M : TG_STEPS;
         int u = 0;
         for (; u < STEPS && active; u++) {
-            record_hit_z<UT>(pl, (uint64_t)moff, (uint32_t)z, p, c);
+            record_hit_z<UT>(pl, (uint64_t)moff, z, Pp, idx, c);
             const bool down = z <= wmda;
             const bool up = z >= ub;
             z += down ? da : (up ? nub : dmu);

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <string>
 
 #include "../../include/combsieve.h"
 #include "cs_internal.h"
@@ -35,7 +36,7 @@ constexpr int BASE_THREADS = 1024;
 __global__ void __launch_bounds__(BASE_THREADS) k_base_primes(uint32_t *scratch, uint32_t limit) {
     uint32_t *bm = scratch + BITMAP_OFF;
     uint32_t *base = scratch + BASE_OFF;
-    const uint32_t n_odd = limit / 2 + 1;                 // odd numbers 1, 3, ..., <= limit
+    const uint32_t n_odd = (limit + 1) / 2;               // odd numbers 1, 3, ..., <= limit
     const uint32_t n_words = (n_odd + 31) / 32;
     for (uint32_t w = threadIdx.x; w < n_words; w += BASE_THREADS) bm[w] = 0;
     __syncthreads();
@@ -106,17 +107,22 @@ uint64_t isqrt_floor(uint64_t n) {
     return r;
 }
 
+// errors go through the library's error text, like those of cs_primes
+cs_status cuda_error(cudaError_t e, const char *what) {
+    return cs::set_error(CS_EDEVICE, (std::string(what) + ": " + cudaGetErrorString(e)).c_str());
+}
+
 }  // namespace
 
 extern "C" cs_status cs_primes_static(uint64_t lo, uint64_t hi, uint64_t *out, uint64_t cap,
                                       uint64_t *count, void *stream) {
-    if (!count) return CS_EINVAL;
+    if (!count) return cs::set_error(CS_EINVAL, "cs_primes_static: count is NULL");
     *count = 0;
-    if (hi > (1ull << 40)) return CS_EINVAL;
+    if (hi > (1ull << 40)) return cs::set_error(CS_EINVAL, "cs_primes_static: hi above 2^40");
     if (hi <= lo || hi < 2) return CS_OK;
     uint32_t *scratch = nullptr;
     cs_status s = scratch_for_current_device(&scratch);
-    if (s) return s;
+    if (s) return cs::set_error(s, "cs_primes_static: no device address for the static scratch");
     cudaStream_t st = (cudaStream_t)stream;
     const uint32_t limit = (uint32_t)isqrt_floor(hi) + 1;   // <= 2^20 + 1, odd part <= 2^20
     const uint32_t lim = limit > LIMIT_MAX ? LIMIT_MAX : limit;
@@ -131,8 +137,8 @@ extern "C" cs_status cs_primes_static(uint64_t lo, uint64_t hi, uint64_t *out, u
     unsigned long long h[2] = {0, 0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(h, ctr, 16, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return CS_EDEVICE;
+    if (e != cudaSuccess) return cuda_error(e, "cs_primes_static");
     *count = h[0];
-    if (h[1] || h[0] > cap) return CS_EOVERFLOW;
+    if (h[1] || h[0] > cap) return cs::set_error(CS_EOVERFLOW, "cs_primes_static: more primes than cap");
     return CS_OK;
 }

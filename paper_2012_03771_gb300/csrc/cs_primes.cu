@@ -97,10 +97,12 @@ __device__ __forceinline__ uint32_t kmodp32(uint32_t p, uint32_t pinv, uint32_t 
     return acc >= p ? acc - p : acc;
 }
 
-__device__ __forceinline__ uint64_t kmodp64(uint64_t p, uint64_t pinv, uint64_t r1, uint64_t r2,
+// K mod p for 64-bit p from R^2 mod p: the product of the n factor words
+// starts at R^n mod p, which cancels their n factors R^-1
+__device__ __forceinline__ uint64_t kmodp64(uint64_t p, uint64_t pinv, uint64_t r2,
                                             const uint64_t *kch, uint32_t n) {
     if (n == 0) return 1ull % p;
-    uint64_t acc = mont64_rpow(n, r1, r2, p, pinv);
+    uint64_t acc = mont64_rpow2(n, r2, p, pinv);
     for (uint32_t i = 0; i < n; i++) acc = mont64_mul(acc, __ldg(&kch[i]), p, pinv);
     return acc;
 }
@@ -144,7 +146,7 @@ __device__ __forceinline__ void emit(const GenArgs &a, uint64_t p, bool valid, u
         } else if (KIND == KIND_PR64) {
             uint64_t pinv = mont64_neg_inv(p);
             w0 = p;
-            w1 = kmodp64(p, pinv, mont64_r1(p), mont64_r2(p), a.kch64, a.n_kch64);
+            w1 = kmodp64(p, pinv, mont64_r2_fast(p, rcp_rn(u64_to_f(p))), a.kch64, a.n_kch64);
         } else {
             w0 = p;
         }
@@ -195,10 +197,13 @@ __global__ void __launch_bounds__(RES_THREADS) k_large_res(const GenArgs a) {
          i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t p = reinterpret_cast<const uint64_t *>(a.o0)[i];
         const uint64_t pinv = mont64_neg_inv(p);
-        const uint64_t r1 = mont64_r1(p), r2 = mont64_r2(p);
-        const uint64_t r = kmodp64(p, pinv, r1, r2, a.kch64, a.n_kch64);
+        const float fp = rcp_rn(u64_to_f(p));
+        const uint64_t r2 = mont64_r2_fast(p, fp);
+        const uint64_t r = kmodp64(p, pinv, r2, a.kch64, a.n_kch64);
         const uint64_t rt = mont64_mul(r, r2, p, pinv);
-        const uint64_t v = mont64_mul(rt, a.M_start % p, p, pinv) + a.SL;
+        // M_start < 2^40: below p, or a quotient below 2^20 for p >= 2^20
+        const uint64_t ms = a.M_start < p ? a.M_start : p >= (1ull << 20) ? mod_q20(a.M_start, p, fp) : a.M_start % p;
+        const uint64_t v = mont64_mul(rt, ms, p, pinv) + a.SL;
         reinterpret_cast<uint64_t *>(a.o1)[i] = r;
         reinterpret_cast<uint64_t *>(a.o2)[i] = v >= p ? v - p : v;
     }
@@ -528,7 +533,7 @@ __global__ void k_kmodp(const uint64_t *p, uint64_t n, uint64_t *r, const uint32
             r[i] = kmodp32(q32, pinv, mont32_r1(q32), mont32_r2(q32), kch32, n32);
         } else {
             uint64_t pinv = mont64_neg_inv(q);
-            r[i] = kmodp64(q, pinv, mont64_r1(q), mont64_r2(q), kch64, n64);
+            r[i] = kmodp64(q, pinv, mont64_r2_fast(q, rcp_rn(u64_to_f(q))), kch64, n64);
         }
     }
 }

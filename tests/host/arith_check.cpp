@@ -6,7 +6,9 @@
 // Euclid's algorithm; mode "l" the generator's lazily reduced Montgomery
 // product; mode "u" the float-estimate division of 64-bit numerators; mode "F"
 // the first hit for 64-bit primes; mode "e" (and "E", 64-bit) the Euclid steps'
-// small-quotient division; mode "k" K's factor words.
+// small-quotient division; mode "k" K's factor words; mode "R" the 64-bit
+// residue kernel's division-free R^2 mod p, M mod p and R^e mod p; mode "W"
+// the narrow-step Euclid run and first hit for 64-bit primes.
 #include <cstdio>
 #include <cstdint>
 #include "../../paper_2012_03771_gb300/csrc/cs_arith.cuh"
@@ -22,6 +24,48 @@ int main(int argc, char **argv) {
             const uint32_t r2 = cs::mont32_r2_fast(p32);
             const uint32_t rt = cs::mont32_mul((uint32_t)r, r2, p32, pinv);
             printf("%u %u\n", r2, cs::mont32_affine(rt, M, (uint32_t)s, r2, p32, pinv));
+        }
+        return 0;
+    }
+    if (argc > 1 && argv[1][0] == 'R') {
+        // "p M" -> R^2 mod p (R = 2^64) without a division, M mod p by one float
+        // quotient (M / p < 2^20), then R^e mod p for e = 1 .. 40 from R^2 alone
+        unsigned long long p, M;
+        while (scanf("%llu %llu", &p, &M) == 2) {
+            const float fp = cs::rcp_rn(cs::u64_to_f(p));
+            const uint64_t pinv = cs::mont64_neg_inv(p);
+            const uint64_t r2 = cs::mont64_r2_fast(p, fp);
+            printf("%llu %llu", (unsigned long long)r2, (unsigned long long)cs::mod_q20(M, p, fp));
+            for (uint32_t e = 1; e <= 40; e++)
+                printf(" %llu", (unsigned long long)cs::mont64_rpow2(e, r2, p, pinv));
+            printf("\n");
+        }
+        return 0;
+    }
+    if (argc > 1 && argv[1][0] == 'W') {
+        // "p r w v0" -> the narrow-step Euclid run and first hit for 64-bit primes,
+        // beside the general 64-bit ones: ok a da b ub | ok a da b ub | t y | t y
+        // (the first hits only when both steps are below 2^31, else "- -")
+        unsigned long long p, r, w, v0;
+        while (scanf("%llu %llu %llu %llu", &p, &r, &w, &v0) == 4) {
+            uint64_t a, b, a2, da2, b2, ub2;
+            uint32_t da, ub, it = 0, it2 = 0;
+            const bool ok = cs::tg_steps_w(p, r, (uint32_t)w, a, da, b, ub, it, 400);
+            const bool ok2 = cs::tg_steps<uint64_t>(p, r, w, a2, da2, b2, ub2, it2, 400);
+            printf("%d %llu %u %llu %u %d %llu %llu %llu %llu", ok, (unsigned long long)a, da,
+                   (unsigned long long)b, ub, ok2, (unsigned long long)a2, (unsigned long long)da2,
+                   (unsigned long long)b2, (unsigned long long)ub2);
+            if (ok && a < (1ull << 31) && b < (1ull << 31)) {
+                uint32_t y;
+                uint64_t y2;
+                const uint64_t t = cs::first_hit_w(p, cs::rcp_rn(cs::u64_to_f(p)), (uint32_t)w, (uint32_t)a, da,
+                                                   (uint32_t)b, ub, v0, y);
+                const uint64_t t2 = cs::first_hit64(p, w, a2, da2, b2, ub2, v0, y2);
+                printf(" %llu %u %llu %llu\n", (unsigned long long)t, y, (unsigned long long)t2,
+                       (unsigned long long)y2);
+            } else {
+                printf(" - - - -\n");
+            }
         }
         return 0;
     }

@@ -1,5 +1,6 @@
 """The kernels' solver arithmetic (cs_arith.cuh), compiled for the host with
 g++, against the paper's recursion G of Section 3.3 in the oracle."""
+import math
 import os
 import random
 import subprocess
@@ -38,6 +39,75 @@ def test_g_solve_matches_paper_recursion(exe, narrow):
         ok, m, y = (int(v) for v in line.split())
         g = O.G(p, K, L, R)
         assert ok and (m, y) == (g, g * K % p), (p, K, L, R)
+
+
+def test_narrow_steps_and_first_hit_64(exe):
+    """For 2^30 <= p < 2^40 and 1024 <= 2SL <= 2^21: the Euclid run with 32-bit
+    steps below 2^31 gives the same two steps as the general 64-bit run, and the
+    first hit from them (64-bit products modulo 2^64 around float quotients)
+    equals the general first hit and the paper's G of the window, on random
+    residues and on the edge cases r = 1, r = p - 1, residues next to the window
+    and tiny last remainders."""
+    rng = random.Random(41)
+    ps = [(1 << 30) + 3, (1 << 31) - 1, (1 << 32) + 15, 99999999977, 100000000003, (1 << 37) - 25,
+          (1 << 40) - 87]
+    cases = []
+    for _ in range(20000):
+        p = rng.choice(ps) if rng.random() < 0.2 else rng.randrange(1 << 30, 1 << 40) | 1
+        w = rng.choice([1024, 1025, 4000, 40000, 50000, 2 * rng.randrange(512, 1 << 20), 1 << 21])
+        w = min(w, p - 2)
+        kind = rng.random()
+        if kind < 0.05:
+            r = rng.choice([1, 2, p - 1, p - 2, w, w + 1, p - w])
+        elif kind < 0.1:
+            # r just above a multiple of p / k, so that some remainder is tiny
+            k = rng.randrange(1, 1000)
+            r = (p * rng.randrange(1, k + 1)) // k + rng.randrange(-3, 4)
+        else:
+            r = rng.randrange(1, p)
+        r = min(max(r, 1), p - 1)
+        if math.gcd(r, p) != 1:
+            continue
+        v0 = rng.choice([w + 1, p - 1, rng.randrange(w + 1, p)])
+        cases.append((p, r, w, v0))
+    inp = "".join(f"{p} {r} {w} {v0}\n" for p, r, w, v0 in cases)
+    out = subprocess.run([exe, "W"], input=inp, capture_output=True, text=True, check=True).stdout.split("\n")
+    n_fast = 0
+    for (p, r, w, v0), line in zip(cases, out):
+        f = line.split()
+        assert f[0] == "1" and f[5] == "1", (p, r, w)
+        assert [int(x) for x in f[1:5]] == [int(x) for x in f[6:10]], (p, r, w)
+        if f[10] != "-":
+            n_fast += 1
+            t, y, t2, y2 = (int(x) for x in f[10:14])
+            g = O.G(p, r, p - v0, p - v0 + w)
+            assert (t, y) == (t2, y2) == (g, (v0 + r * g) % p), (p, r, w, v0)
+    assert n_fast > 0.9 * len(cases)
+
+
+def test_division_free_montgomery_constants_64(exe):
+    """R^2 mod p for R = 2^64 from float quotient estimates (odd p in
+    [2^20, 2^40); the 64 doublings below), M mod p from one float quotient
+    (M / p < 2^20), and R^e mod p for e = 1..40 from R^2 alone, against exact
+    integers."""
+    rng = random.Random(31)
+    ps = [(1 << 20) + 1, (1 << 20) + 7, (1 << 30) - 35, (1 << 30) + 3, (1 << 32) - 5, (1 << 32) + 15,
+          (1 << 40) - 87, (1 << 40) - 1, 99999999977, 100000000003, 3, 1000003]
+    ps += [rng.randrange(1 << 20, 1 << 40) | 1 for _ in range(20000)]
+    ps += [rng.randrange(1 << 39, 1 << 40) | 1 for _ in range(2000)]
+    cases = []
+    for p in ps:
+        hi = min(p * (1 << 20) - 1, (1 << 61) - 1)
+        M = rng.choice([0, 1, p - 1, p, p + 1, rng.randrange(0, p), rng.randrange(0, hi + 1), hi])
+        cases.append((p, M))
+    inp = "".join(f"{p} {M}\n" for p, M in cases)
+    out = subprocess.run([exe, "R"], input=inp, capture_output=True, text=True, check=True).stdout.split("\n")
+    for (p, M), line in zip(cases, out):
+        v = [int(t) for t in line.split()]
+        assert v[0] == pow(2, 128, p), p
+        if p >= 1 << 20:
+            assert v[1] == M % p, (p, M)
+        assert v[2:] == [pow(2, 64 * e, p) for e in range(1, 41)], p
 
 
 def test_division_free_montgomery_constants(exe):

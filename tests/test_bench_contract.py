@@ -45,28 +45,49 @@ def _info(**kw):
     return SimpleNamespace(**base)
 
 
-def test_roofline_uses_counters_only_for_the_same_sources_and_setup(bench):
-    ctr = bench.WALK_COUNTERS["search_953"]
+def test_roofline_uses_counters_only_for_the_same_sources_and_setup(bench, monkeypatch):
+    """achieved = stored thread instructions per walk launch / the launch's timed
+    duration; peak = the best measured issue rate of the micro-benchmark; the
+    counters apply only to the same sources, threshold, tile height and chunking."""
+    ctr = {"csrc_sha": bench.csrc_sha(), "threshold": 120003, "tile_rows": 16, "launches": 17,
+           "thread_inst": 8.77e10, "dram_bytes": 1.24e9}
+    monkeypatch.setitem(bench.WALK_COUNTERS, "search_953", ctr)
     walk = bench.KC_NAMES.index("large_walk")
     kern_ms = [0.0] * len(bench.KC_NAMES)
     kern_n = [0] * len(bench.KC_NAMES)
     kern_ms[walk], kern_n[walk] = 10 * 5.9, 10 * ctr["launches"]      # 10 sieves
     stats = {"hits_all": 7.47e8 * 10, "levels": 4.5e8 * 10}
     peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
-    args = (stats, None, peaks, "measured", None, "search_953")
-    same_sources = ctr["csrc_sha"] == bench.csrc_sha()
-    r = bench.roofline(walk, kern_ms, kern_n, stats, _info(), *args[1:])
-    assert r["bound"] == "alu" and r["unit"] == "Tinst/s"
-    assert abs(r["peak"] - 152 * 4 * 32 * 2070e6 / 1e12) < 1e-9
-    if same_sources:
-        per_launch_s = 5.9e-3 / ctr["launches"]
-        want = ctr["thread_inst"] / ctr["launches"] / per_launch_s / 1e12
-        assert abs(r["achieved"] - want) < 1e-9 * want and abs(r["frac"] - want / r["peak"]) < 1e-12
-        assert abs(r["traffic"] - ctr["dram_bytes"] / ctr["launches"]) < 1.0
-    # another threshold, tile height or chunking: the counters do not apply
+    issue = {"add_logic": 20.5, "imad": 19.0, "imad_logic": 38.25}
+    r = bench.roofline(walk, kern_ms, kern_n, stats, _info(), None, peaks, "measured", issue, "search_953")
+    assert r["bound"] == "alu" and r["unit"] == "Tinst/s" and r["peak"] == 38.25
+    per_launch_s = 5.9e-3 / ctr["launches"]
+    want = ctr["thread_inst"] / ctr["launches"] / per_launch_s / 1e12
+    assert abs(r["achieved"] - want) < 1e-9 * want and abs(r["frac"] - want / 38.25) < 1e-12
+    assert abs(r["traffic"] - ctr["dram_bytes"] / ctr["launches"]) < 1.0
+    # another threshold, tile height, chunking or source digest: the counters do not apply
     for other in (_info(threshold=80002), _info(tile_rows=8), _info(n_large_chunks=24)):
-        r = bench.roofline(walk, kern_ms, kern_n, stats, other, *args[1:])
+        r = bench.roofline(walk, kern_ms, kern_n, stats, other, None, peaks, "measured", issue, "search_953")
         assert r["achieved"] is None and r["frac"] is None and "note" in r
+    monkeypatch.setitem(bench.WALK_COUNTERS, "search_953", dict(ctr, csrc_sha="0" * 16))
+    r = bench.roofline(walk, kern_ms, kern_n, stats, _info(), None, peaks, "measured", issue, "search_953")
+    assert r["achieved"] is None
+    # no measured peak: no fraction (never a derived stand-in)
+    monkeypatch.setitem(bench.WALK_COUNTERS, "search_953", ctr)
+    r = bench.roofline(walk, kern_ms, kern_n, stats, _info(), None, peaks, "measured", {"error": "x"}, "search_953")
+    assert r["peak"] is None and r["frac"] is None
+
+
+def test_oracle_sample_ranges(bench):
+    """The bounded oracle sample: all of (P, L] for small L, else (P, 2^24] plus
+    evenly spaced 2^26-wide windows ending at L, disjoint and inside (P, L]."""
+    from paper_2012_03771_gb300 import workloads
+    assert bench.sample_ranges(workloads.PLAIN_503, 4) == [(503, 10**7)]
+    rng = bench.sample_ranges(workloads.LARGE_1019, 4)
+    assert rng[0] == (1019, 1 << 24) and len(rng) == 5 and rng[-1][1] == 10**11
+    for (a, b), (c, e) in zip(rng, rng[1:]):
+        assert b <= c and e - c == 1 << 26
+    assert bench.sample_ranges(workloads.LARGE_1019, 0) == [(1019, 10**11)]
 
 
 def test_clock_samples_median_and_reasons(bench, tmp_path):

@@ -249,7 +249,7 @@ def run_cuda(args, params):
         clocks.start()
         barrier()
         torch.cuda.synchronize()
-        step_ms, kern_ms, kern_n = [], [0.0] * 5, [0] * 5
+        step_ms, kern_ms, kern_n = [], [0.0] * len(KC_NAMES), [0] * len(KC_NAMES)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         for k in range(args.steps):
             flush.fill_(k & 0xff)                       # evict the previous step from L2
@@ -313,7 +313,7 @@ def run_cuda(args, params):
     # ---- roofline of the dominant kernel ------------------------------------
     peaks, peak_src = _peaks()
     issue = issue_rates(torch, cs, stream)
-    dom = max(range(5), key=lambda i: kern_ms[i])
+    dom = max(range(len(KC_NAMES)), key=lambda i: kern_ms[i])
     roof = roofline(dom, kern_ms, kern_n, stats, info, params, peaks, peak_src, issue, args.config)
 
     # ---- CPU oracle on a bounded sample -------------------------------------

@@ -216,7 +216,10 @@ const char *cs_last_error(void);
 /* ---- autotuning -------------------------------------------------------------
  * Picks the threshold T (as a multiple of S) and the tile height for a
  * parameter set by timing candidates on the device, on a proxy instance with
- * the same P, d and SL, M_inc clipped to 1e5 and L to 1e9.  The choice is kept
+ * the same P, d and SL, M_inc clipped to 1e5 and L to 1e9, then the walk's
+ * work-item size (item_hits: 32, 64, 128, 256 or 512 expected walked hits per
+ * item, which sets how many primes and m-segments the CTAs take at a time)
+ * for that threshold and tile height.  The choice is kept
  * per (P, d, SL, ceil(log2 L)) in memory and, if cache_path is not NULL,
  * appended to that text file and read back by later calls (one line per key).
  * *out receives a complete tuning (large_mode = 2).  Validation errors as for

@@ -293,7 +293,8 @@ def cs_autotune(P, d, M_start, M_inc, SL, L, cache_path: Optional[str] = None) -
     t = cs_tuning()
     _check(load().cs_autotune(P, d, M_start, M_inc, SL, L, cache_path.encode() if cache_path else None,
                               ctypes.byref(t)))
-    return {"threshold": int(t.threshold), "tile_rows": int(t.tile_rows), "large_mode": int(t.large_mode)}
+    return {"threshold": int(t.threshold), "tile_rows": int(t.tile_rows), "large_mode": int(t.large_mode),
+            "item_hits": int(t.item_hits)}
 
 
 # ---------------------------------------------------------------- wrapper

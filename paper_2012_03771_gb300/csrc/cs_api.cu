@@ -176,6 +176,10 @@ struct cs_plan_s {
     bool async_alloc = false;
     PlanPool *pool = nullptr;             // plain plans: the device's plan pool
     bool built = false;                   // build_plan finished
+    // host-side fault injection for tests: the fail_alloc_at-th device
+    // allocation of the build fails as if the device were out of memory
+    // (environment CS_FAIL_ALLOC_AT; 0 = off)
+    uint64_t fail_alloc_at = 0, n_allocs = 0;
     // stream of the plan's allocations and uploads: the server's, else the
     // device pool's (set up by the first dalloc)
     cudaStream_t upload_stream() { return async_alloc ? alloc_stream : pool->upload_stream; }
@@ -216,6 +220,8 @@ struct cs_plan_s {
     template <class T>
     cs_status dalloc(T **p, size_t count) {
         size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+        if (fail_alloc_at && ++n_allocs == fail_alloc_at)
+            return fail(CS_ENOMEM, "device allocation failed (injected by CS_FAIL_ALLOC_AT)");
         cudaError_t e;
         if (async_alloc) {
             e = cudaMallocAsync((void **)p, bytes, alloc_stream);
@@ -318,6 +324,7 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
     pl->P = P; pl->d = d; pl->M_start = M_start; pl->M_inc = M_inc; pl->SL = SL; pl->L = L;
     if (tune) pl->tune = *tune;
     env_tuning(pl->tune);
+    if (const char *fa = getenv("CS_FAIL_ALLOC_AT")) pl->fail_alloc_at = strtoull(fa, nullptr, 10);
     pl->wheel = !pl->tune.no_wheel;
 
     // K as 32- and 64-bit factor words; K itself when it fits in 64 bits
@@ -864,10 +871,9 @@ cs_status cs_sync(cs_plan_t pl) {
         CS_CUDA(cudaMemcpy(&cerr, cv.err, sizeof(cerr), cudaMemcpyDeviceToHost));
         err |= cerr;
     }
-    if (err & ERR_PRIME_OVERFLOW) return fail(CS_EOVERFLOW, "prime buffer overflow");
-    if (err & ERR_SOLVER_LIMIT) return fail(CS_EDEVICE, "modular solver exceeded its pass bound");
-    if (err & ERR_STAGE_TIMEOUT) return fail(CS_ETIMEOUT, "tile sieve: a staging copy did not complete");
-    return CS_OK;
+    const char *msg = nullptr;
+    const cs_status st = status_of_device_errors(err, &msg);
+    return st ? fail(st, msg) : CS_OK;
 }
 
 cs_status cs_info(cs_plan_t pl, cs_info_t *out) {

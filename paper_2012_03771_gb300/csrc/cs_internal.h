@@ -8,6 +8,7 @@
 #include <mutex>
 
 #include "../../include/combsieve.h"
+#include "cs_errors.h"
 
 namespace cs {
 
@@ -26,11 +27,6 @@ enum Stat {
     ST_COUNT = 16
 };
 
-enum Err : uint64_t {
-    ERR_PRIME_OVERFLOW = 1,   // a prime chunk produced more primes than its buffer holds
-    ERR_SOLVER_LIMIT = 2,     // the solver exceeded its pass bound (never expected)
-    ERR_STAGE_TIMEOUT = 4,    // a bounded wait for a shared-memory staging copy gave up
-};
 
 // layout of one small sieving prime (p <= T < 2^31), for the tile sieve
 struct SmallPrime {

@@ -1,4 +1,6 @@
-// Autotuner for the small/large prime threshold T and the tile height.
+// Autotuner for the small/large prime threshold T, the tile height and the
+// size of the large-prime walk's work items (expected walked hits per item,
+// i.e. how many primes and m-segments a CTA's warps take at a time).
 //
 // Section 3.2 leaves the threshold open ("naively p > 10 S"; the runtime
 // model's C_mult is about 50).  Here it trades two kernels: the tile sieve costs
@@ -6,9 +8,11 @@
 // per large prime.  Both grow with M_inc at the same rate, so the best T hardly
 // depends on M_inc; it depends on S, on the primes near T and on the GPU.  The
 // tuner therefore times candidate settings on a proxy with the same P, d and SL,
-// M_inc clipped to 1e5 and L to 1e9 (a few tens of milliseconds per run), and
-// keeps the winner per (P, d, SL, ceil(log2 L)) in memory and, if a path is
-// given, in a text file that later processes read back.
+// M_inc clipped to 1e5 and L to 1e9 (a few tens of milliseconds per run): first
+// T and the tile height together, then the item size for the winner.  The
+// choice is kept per (P, d, SL, ceil(log2 L)) in memory and, if a path is
+// given, in a text file that later processes read back (lines of six fields,
+// without an item size, mean the automatic one).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -32,6 +36,7 @@ using Key = std::tuple<uint32_t, uint64_t, uint32_t, uint32_t>;   // P, d, SL, c
 struct Choice {
     uint64_t T_over_S_x100;   // threshold as a multiple of S, times 100
     uint32_t tile_rows;
+    uint32_t item_hits;       // walked hits per work item (0: the automatic 128)
 };
 
 std::mutex g_mu;
@@ -46,18 +51,21 @@ uint32_t log2_ceil(uint64_t x) {
 void load_file(const char *path) {
     FILE *f = fopen(path, "r");
     if (!f) return;
-    unsigned P, SL, lg, rows;
-    unsigned long long d, tx;
-    while (fscanf(f, "%u %llu %u %u %llu %u", &P, &d, &SL, &lg, &tx, &rows) == 6)
-        g_mem[Key{P, d, SL, lg}] = Choice{tx, rows};
+    char line[256];
+    while (fgets(line, sizeof(line), f)) {
+        unsigned P, SL, lg, rows, items = 0;
+        unsigned long long d, tx;
+        const int n = sscanf(line, "%u %llu %u %u %llu %u %u", &P, &d, &SL, &lg, &tx, &rows, &items);
+        if (n == 6 || n == 7) g_mem[Key{P, d, SL, lg}] = Choice{tx, rows, n == 7 ? items : 0u};
+    }
     fclose(f);
 }
 
 void append_file(const char *path, const Key &k, const Choice &c) {
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%u %llu %u %u %llu %u\n", std::get<0>(k), (unsigned long long)std::get<1>(k), std::get<2>(k),
-            std::get<3>(k), (unsigned long long)c.T_over_S_x100, c.tile_rows);
+    fprintf(f, "%u %llu %u %u %llu %u %u\n", std::get<0>(k), (unsigned long long)std::get<1>(k), std::get<2>(k),
+            std::get<3>(k), (unsigned long long)c.T_over_S_x100, c.tile_rows, c.item_hits);
     fclose(f);
 }
 
@@ -111,7 +119,7 @@ extern "C" cs_status cs_autotune(uint32_t P, uint64_t d, uint64_t M_start, uint6
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
             return set_error(CS_EDEVICE, "cudaStreamCreate");
         double best = -1;
-        Choice pick{800, 0};
+        Choice pick{800, 0, 0};
         for (uint64_t mx : mults_x100)
             for (uint32_t tr : rows) {
                 cs_tuning t{};
@@ -122,9 +130,25 @@ extern "C" cs_status cs_autotune(uint32_t P, uint64_t d, uint64_t M_start, uint6
                 double ms = time_once(P, d, M_start, pM, SL, pL, t, st);
                 if (ms >= 0 && (best < 0 || ms < best)) {
                     best = ms;
-                    pick = Choice{mx, tr};
+                    pick = Choice{mx, tr, 0};
                 }
             }
+        if (best >= 0) {
+            // work-item size for the chosen threshold and tile height (the
+            // automatic 128 is the timing above)
+            for (uint32_t ih : {32u, 64u, 256u, 512u}) {
+                cs_tuning t{};
+                t.large_mode = 2;
+                t.tile_rows = pick.tile_rows;
+                t.threshold = std::max<uint64_t>(S * pick.T_over_S_x100 / 100, 2ull * SL);
+                t.item_hits = ih;
+                double ms = time_once(P, d, M_start, pM, SL, pL, t, st);
+                if (ms >= 0 && ms < best) {
+                    best = ms;
+                    pick.item_hits = ih;
+                }
+            }
+        }
         cudaStreamDestroy(st);
         if (best < 0) return set_error(CS_EDEVICE, "autotune: no candidate ran");
         g_mem[key] = pick;
@@ -133,5 +157,6 @@ extern "C" cs_status cs_autotune(uint32_t P, uint64_t d, uint64_t M_start, uint6
     }
     out->threshold = std::min<uint64_t>(std::max<uint64_t>(S * it->second.T_over_S_x100 / 100, 2ull * SL), 1ull << 30);
     out->tile_rows = it->second.tile_rows;
+    out->item_hits = it->second.item_hits;
     return CS_OK;
 }

@@ -8,11 +8,13 @@
 // the first hit for 64-bit primes; mode "e" (and "E", 64-bit) the Euclid steps'
 // small-quotient division; mode "k" K's factor words; mode "R" the 64-bit
 // residue kernel's division-free R^2 mod p, M mod p and R^e mod p; mode "W"
-// the narrow-step Euclid run and first hit for 64-bit primes.
+// the narrow-step Euclid run and first hit for 64-bit primes; mode "X" the
+// status of a sieve's device error flags.
 #include <cstdio>
 #include <cstdint>
 #include "../../paper_2012_03771_gb300/csrc/cs_arith.cuh"
 #include "../../paper_2012_03771_gb300/csrc/cs_words.h"
+#include "../../paper_2012_03771_gb300/csrc/cs_errors.h"
 
 int main(int argc, char **argv) {
     const bool narrow = argc > 1 && argv[1][0] == 'n';
@@ -24,6 +26,16 @@ int main(int argc, char **argv) {
             const uint32_t r2 = cs::mont32_r2_fast(p32);
             const uint32_t rt = cs::mont32_mul((uint32_t)r, r2, p32, pinv);
             printf("%u %u\n", r2, cs::mont32_affine(rt, M, (uint32_t)s, r2, p32, pinv));
+        }
+        return 0;
+    }
+    if (argc > 1 && argv[1][0] == 'X') {
+        // "flags" -> the status cs_sync reports for a sieve's device error word, and its message
+        unsigned long long f;
+        while (scanf("%llu", &f) == 1) {
+            const char *msg = nullptr;
+            const int st = cs::status_of_device_errors(f, &msg);
+            printf("%d %s\n", st, msg);
         }
         return 0;
     }

@@ -85,6 +85,21 @@ def test_narrow_steps_and_first_hit_64(exe):
     assert n_fast > 0.9 * len(cases)
 
 
+def test_device_error_flags_map_to_one_status(exe):
+    """The error word a sieve's kernels leave behind (bounded waits and
+    capacity checks set flags instead of trapping) becomes one status in
+    cs_sync: a prime-buffer overflow first (the result lacks primes), then a
+    solver that ran out of passes, then a staging copy that timed out."""
+    cases = {0: (0, ""), 1: (-7, "prime buffer overflow"), 2: (-3, "modular solver"),
+             4: (-4, "staging copy"), 3: (-7, "prime buffer"), 6: (-3, "modular solver"),
+             5: (-7, "prime buffer"), 8: (-3, "unknown")}
+    out = subprocess.run([exe, "X"], input="".join(f"{f}\n" for f in cases), capture_output=True, text=True,
+                         check=True).stdout.split("\n")
+    for (f, (st, msg)), line in zip(cases.items(), out):
+        code, _, text = line.partition(" ")
+        assert int(code) == st and msg in text, (f, line)
+
+
 def test_division_free_montgomery_constants_64(exe):
     """R^2 mod p for R = 2^64 from float quotient estimates (odd p in
     [2^20, 2^40); the 64 doublings below), M mod p from one float quotient

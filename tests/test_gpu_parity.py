@@ -34,6 +34,14 @@ def _run(params, **tuning):
                     stats=plan.stats(), info=plan.info)
 
 
+def _bits_only(params, **tuning):
+    """Bitset, F and counts (also for the compact layout, whose columns vary by row)."""
+    with cs.Plan(*params, **tuning) as plan:
+        plan.sieve(torch.cuda.current_stream()).sync()
+        counts, F, h = plan.counts()
+        return dict(bits=plan.bitset(), counts=counts, F=F, hash=h, info=plan.info)
+
+
 def _check_full(params, got, wheel=True):
     m_ref, bits_ref, F_ref = O.full_sieve(*params, wheel=wheel)
     assert np.array_equal(got["rows"], m_ref)
@@ -273,7 +281,8 @@ def test_autotune_picks_a_valid_tuning_and_caches_it(tmp_path):
     path = str(tmp_path / "tune.txt")
     t = cs.cs_autotune(*prm.as_tuple(), cache_path=path)
     assert t["threshold"] >= 2 * prm.SL and t["tile_rows"] in (8, 16, 32) and t["large_mode"] == 2
-    assert len(open(path).read().split()) == 6                  # one line: key and choice
+    assert t["item_hits"] in (0, 32, 64, 256, 512)              # 0: the automatic 128 won
+    assert len(open(path).read().split()) == 7                  # one line: key and choice
     assert cs.cs_autotune(*prm.as_tuple(), cache_path=path) == t
     ref = _run(prm.as_tuple())
     got = _run(prm.as_tuple(), **t)

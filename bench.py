@@ -313,8 +313,10 @@ def run_cuda(args, params):
     # ---- roofline of the dominant kernel ------------------------------------
     peaks, peak_src = _peaks()
     issue = issue_rates(torch, cs, stream)
+    plan.close()                                    # room for the scattered-clear probe
+    clears_peak = clear_rate(torch, cs, stream, int(info.bitset_bytes) // 4)
     dom = max(range(len(KC_NAMES)), key=lambda i: kern_ms[i])
-    roof = roofline(dom, kern_ms, kern_n, stats, info, params, peaks, peak_src, issue, args.config)
+    roof = roofline(dom, kern_ms, kern_n, stats, info, params, peaks, peak_src, issue, args.config, clears_peak)
 
     # ---- CPU oracle on a bounded sample -------------------------------------
     cpu = None
@@ -404,9 +406,30 @@ def issue_rates(torch, cs, stream):
         return {"error": str(e)}
 
 
-def roofline(dom, kern_ms, kern_n, stats, info, params, peaks, peak_src, issue, config):
-    """Roofline of the dominant kernel class: its work per launch over its
-    average CUDA-event launch duration (timed on the launching stream)."""
+def clear_rate(torch, cs, stream, words):
+    """The measured rate of scattered bit clears (cs_atomic_rate: one-bit 32-bit
+    atomic ANDs at random words) over a region of `words` 32-bit words, the
+    bitset's size: best of three launches, in clears per second."""
+    try:
+        buf = torch.full((max(int(words), 1),), -1, dtype=torch.int32, device="cuda")
+        best = 0.0
+        for _ in range(3):
+            n, ms = cs.cs_atomic_rate(buf.data_ptr(), buf.numel(), 256, stream)
+            best = max(best, n / (ms / 1e3))
+        del buf
+        return best
+    except Exception:   # reported as missing, never replaced by a derived figure
+        return None
+
+
+def roofline(dom, kern_ms, kern_n, stats, info, params, peaks, peak_src, issue, config, clears_peak=None):
+    """Roofline of the dominant kernel class over its average CUDA-event launch
+    duration (timed on the launching stream).  The large-prime walk has two
+    bounds: the integer issue rate (thread instructions per sieve, from stored
+    ncu counters, against cs_issue_rate) and the scattered bit clears (its
+    stored hits, F_large, counted live, against cs_atomic_rate over a region of
+    the bitset's size).  The bound that needs more time binds; achieved, peak
+    and frac are given in its units, the other bound beside it."""
     name = KC_NAMES[dom]
     n_launch = max(kern_n[dom], 1)
     per_launch_s = kern_ms[dom] / n_launch / 1e3
@@ -425,24 +448,54 @@ def roofline(dom, kern_ms, kern_n, stats, info, params, peaks, peak_src, issue, 
            "peak_source": "measured in this run: cs_issue_rate integer micro-benchmark, best of its mixes "
                           "(burst, one wave at full occupancy)",
            "issue_rates_Tops": issue}
+    if name != "large_walk":
+        out["note"] = "no stored instruction counts for this kernel"
+        return out
+    n_chunks = max(int(info.n_large_chunks), 1)
     ctr = WALK_COUNTERS.get(config)
     # the counters hold for the same sources, threshold, tile height and chunking
     # (one walk launch per large-prime chunk)
     same_setup = ctr is not None and (ctr.get("threshold"), ctr.get("tile_rows"), ctr.get("launches")) == (
         int(info.threshold), int(info.tile_rows), int(info.n_large_chunks))
-    if name == "large_walk" and ctr and ctr["csrc_sha"] == csrc_sha() and same_setup and peak:
-        sieves = n_launch / ctr["launches"]
+    issue_b = None
+    if ctr and ctr["csrc_sha"] == csrc_sha() and same_setup and peak:
         inst_launch = ctr["thread_inst"] / ctr["launches"]
-        out["achieved"] = inst_launch / per_launch_s / 1e12
-        out["frac"] = out["achieved"] / peak
-        out["traffic"] = ctr["dram_bytes"] / ctr["launches"]
-        out["work_per_launch"] = {"thread_inst": inst_launch, "hits": stats["hits_all"] / ctr["launches"],
-                                  "solver_passes": stats["levels"] / ctr["launches"]}
-        out["launches_timed"] = n_launch
-        del sieves
-    else:
+        achieved = inst_launch / per_launch_s / 1e12
+        issue_b = {"achieved": achieved, "peak": peak, "unit": "Tinst/s", "frac": achieved / peak,
+                   "min_ms_per_launch": inst_launch / (peak * 1e12) * 1e3, "thread_inst_per_launch": inst_launch}
+        if ctr.get("dram_bytes") is not None:
+            out["traffic"] = ctr["dram_bytes"] / ctr["launches"]
+    clears_b = None
+    if clears_peak:
+        clears_launch = stats["F_large"] / n_chunks           # stored hits: one bit clear each
+        achieved = clears_launch / per_launch_s / 1e9
+        clears_b = {"achieved": achieved, "peak": clears_peak / 1e9, "unit": "Gclears/s",
+                    "frac": achieved / (clears_peak / 1e9), "min_ms_per_launch": clears_launch / clears_peak * 1e3,
+                    "clears_per_launch": clears_launch}
+    out["bounds"] = {"issue": issue_b, "clears": clears_b}
+    out["launches_timed"] = n_launch
+    walk_s = kern_ms[dom] / 1e3 / max(n_launch / n_chunks, 1)   # walk seconds per sieve
+    out["per_unit_rates"] = {"visited_hits_per_s": stats["hits_all"] / walk_s, "levels_per_s": stats["levels"] / walk_s,
+                             "clears_per_s": stats["F_large"] / walk_s}
+    binding = None
+    if issue_b and clears_b:
+        binding = "clears" if clears_b["min_ms_per_launch"] >= issue_b["min_ms_per_launch"] else "issue"
+    elif clears_b:
+        binding = "clears"
+    elif issue_b:
+        binding = "issue"
+    if binding == "issue":
+        out.update(achieved=issue_b["achieved"], frac=issue_b["frac"])
+    elif binding == "clears":
+        out.update(bound="hbm", achieved=clears_b["achieved"], peak=clears_b["peak"], unit="Gclears/s",
+                   frac=clears_b["frac"],
+                   peak_source="measured in this run: cs_atomic_rate, one-bit 32-bit atomic ANDs at random "
+                               "words of a region the size of the bitset (best of three launches)")
+    if not issue_b:
         out["note"] = "ncu instruction counts not recorded for these sources and this threshold / tile height"
     return out
+
+
 
 
 # ------------------------------------------------------------ batched / served
@@ -452,8 +505,16 @@ def _flush(torch, buf, k):
 
 
 def run_batched(args):
-    """64 seeded instances of uneven size: plain (one stream, one instance after
-    another) against the batch (worker streams, one CUDA-graph launch)."""
+    """64 seeded instances of uneven size (the batched workload), four ways, each
+    step timed on one stream with CUDA events:
+      plain          one instance after another, each generating its own primes;
+      plain_cached   one instance after another, large primes from the shared
+                     residue caches (filled once per step, as in the batch);
+      graph_launches the batch graph with one walk launch per prime chunk;
+      batch          the batch graph with the walks of all instances as jobs of
+                     a few persistent launches (the default batch).
+    The headline ratio is batch against plain_cached: the caches on both arms."""
+    import numpy as np
     import torch
     import paper_2012_03771_gb300 as cs
     from paper_2012_03771_gb300 import build
@@ -468,8 +529,16 @@ def run_batched(args):
     ref = []
     for p in plans:
         p.sieve(s).sync()
-        ref.append(cs.cs_counts(p.h))
-    F_total = sum(f for f, _ in ref)
+        counts, F, h = p.counts()
+        ref.append((F, h, counts.copy()))
+    F_total = sum(r[0] for r in ref)
+
+    def same(ps):
+        out = True
+        for p, r in zip(ps, ref):
+            counts, F, h = p.counts()
+            out = out and (F, h) == r[:2] and np.array_equal(counts, r[2])
+        return out
 
     def time_steps(fn):
         for _ in range(args.warmup):
@@ -484,46 +553,57 @@ def run_batched(args):
             b.record(s)
             s.synchronize()
             ms.append(a.elapsed_time(b))
-        return ms
+        return statistics.median(ms)
 
     def plain():
         for p in plans:
             p.sieve(s)
 
-    plain_ms = time_steps(plain)
-    # batched: one residue cache per (P, d), regenerated once per run inside the
-    # graph and shared by that group's plans
+    arms = {"plain": time_steps(plain)}
+    ok = same(plans)
     lim = {}
     for prm in mix:
         lim[(prm.P, prm.d)] = max(lim.get((prm.P, prm.d), 0), prm.L)
     caches = {k: cs.Cache(k[0], k[1], L) for k, L in lim.items()}
     cplans = [cs.Plan(*prm.as_tuple(), cache=caches[(prm.P, prm.d)]) for prm in mix]
+
+    def plain_cached():
+        for c in caches.values():
+            c.fill(s)
+        for p in cplans:
+            p.sieve(s)
+
+    arms["plain_cached"] = time_steps(plain_cached)
+    ok = ok and same(cplans)
+    os.environ["CS_BATCH_JOBS"] = "0"
+    b_launch = cs.Batch(cplans, n_streams=args.batch_streams)
+    del os.environ["CS_BATCH_JOBS"]
+    arms["graph_launches"] = time_steps(lambda: b_launch.run(s))
+    b_launch.sync()
+    ok = ok and same(cplans)
+    launches_per_chunk = b_launch.launches
+    b_launch.close()
     batch = cs.Batch(cplans, n_streams=args.batch_streams)
-    batch_ms = time_steps(lambda: batch.run(s))
+    arms["batch"] = time_steps(lambda: batch.run(s))
     batch.sync()
-    same = all(cs.cs_counts(p.h) == r for p, r in zip(cplans, ref))
-    # the graph over worker streams alone, without the shared cache
-    batch_nc = cs.Batch(plans, n_streams=args.batch_streams)
-    nocache_ms = time_steps(lambda: batch_nc.run(s))
-    batch_nc.sync()
-    same = same and all(cs.cs_counts(p.h) == r for p, r in zip(plans, ref))
+    ok = ok and same(cplans)
     cache_bytes = sum(c.info()[1] for c in caches.values())
     line = {"metric": "enumerated factors/s, 64-instance batch (bit-exact)", "unit": UNIT,
-            "value": F_total / (statistics.median(batch_ms) / 1e3), "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": statistics.median(batch_ms),
-            "plain": {"value": F_total / (statistics.median(plain_ms) / 1e3), "ms_per_step": statistics.median(plain_ms)},
-            "speedup_vs_plain": statistics.median(plain_ms) / statistics.median(batch_ms),
-            "graph_without_cache": {"value": F_total / (statistics.median(nocache_ms) / 1e3),
-                                    "ms_per_step": statistics.median(nocache_ms)},
+            "value": F_total / (arms["batch"] / 1e3), "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": arms["batch"],
+            "arms_ms_per_step": arms,
+            "arms_value": {k: F_total / (v / 1e3) for k, v in arms.items()},
+            "speedup_vs_plain_cached": arms["plain_cached"] / arms["batch"],
+            "speedup_vs_plain": arms["plain"] / arms["batch"],
             "residue_caches": {"count": len(caches), "device_bytes": cache_bytes},
-            "n_streams": batch.n_streams, "gpu_launches_per_step": batch.launches, "F_per_step": F_total,
-            "results_equal_alone": same,
+            "n_streams": batch.n_streams, "gpu_launches_per_step": batch.launches,
+            "gpu_launches_per_step_one_per_chunk": launches_per_chunk, "F_per_step": F_total,
+            "results_equal_alone": ok,
             "config": {"workload": "batched_64: P in {503,701,953,1019}, d in {210,2310}, M_inc log-U[1e3,1e6], "
                                    "SL U[5000,25000], L log-U[1e8,1e10], M_start log-U[1e6,1e8], seed 201203771",
                        "l2": "flushed between steps (256 MB device write)"}}
     print(json.dumps(line), flush=True)
     batch.close()
-    batch_nc.close()
     for p in plans + cplans:
         p.close()
     for c in caches.values():
@@ -610,13 +690,53 @@ def run_served(args):
     print(json.dumps(line), flush=True)
 
 
+def run_fig1(args):
+    """The speed-up curve of combined sieving against sieving the intervals one
+    at a time (the shape of Figure 1: K = 1511#/210, X = 18,000, L = 1e11), on
+    the GPU (median of --fig1-repeats sieves per point), beside the CPU oracle's
+    time for one interval: the oracle as it stands on this host's cores, timed
+    on a bounded sample of the primes (those up to 2^24 and four windows of
+    2^26 numbers) and scaled to all primes of (P, L] by the prime count."""
+    import torch
+    import paper_2012_03771_gb300 as cs
+    from paper_2012_03771_gb300 import build, speedup_curve as sc
+    build.build()
+    cs.load()
+    torch.cuda.set_device(0)
+    res = sc.curve(repeats=args.fig1_repeats)
+    f = sc.FIG1
+    one = workloads.SieveParams(P=f["P"], d=f["d"], M_start=f["M_start"], M_inc=1, SL=f["SL"], L=f["L"])
+    with cs.Plan(*one.as_tuple()) as p:
+        p.sieve().sync()
+        st = p.stats()
+    n_all = st["n_small_primes"] + st["n_large_primes"]          # primes in (P, L], counted on the GPU
+    oracle = None
+    if not args.no_cpu:
+        import oracle.oracle as O
+        O.build()
+        n_sample = sum(O.prime_stats(lo, hi)[0] for lo, hi in sample_ranges(one, args.ref_windows))
+        F, dt, cores, _, _ = oracle_sample(one, 1, args.ref_windows)
+        per_interval = dt * n_all / max(n_sample, 1)
+        oracle = {"seconds_per_interval": per_interval, "sample_seconds": dt, "cores": cores,
+                  "sample": f"1 interval (m = 1) x {sample_text(one, 1, 1, args.ref_windows).split(' x ')[1]}; "
+                            f"{n_sample} of {n_all} primes, time scaled by the prime count"}
+        for pt in res["points"]:
+            pt["speedup_vs_oracle"] = pt["M_c"] * per_interval / pt["seconds"]
+    line = {"metric": "speed-up of the combined sieve over one interval at a time (Figure 1 shape)",
+            "config": {"workload": "fig1_1511: K=1511#/210, X=18000, primes 1511 < p <= 1e11, m from 1"},
+            "curve": res, "oracle_one_interval": oracle}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
-    ap.add_argument("--config", default="large_1019", choices=sorted(workloads.NAMED) + ["batched_64", "served"])
+    ap.add_argument("--config", default="large_1019",
+                    choices=sorted(workloads.NAMED) + ["batched_64", "served", "fig1_1511"])
+    ap.add_argument("--fig1-repeats", type=int, default=5)
     ap.add_argument("--requests", type=int, default=256)
     ap.add_argument("--load", type=float, default=0.8)
     ap.add_argument("--slots", type=int, default=2)
@@ -635,6 +755,8 @@ def main():
         return run_batched(args)
     if args.config == "served":
         return run_served(args)
+    if args.config == "fig1_1511":
+        return run_fig1(args)
     params = _params_for_rank(workloads.NAMED[args.config], rank)
     if args.impl == "reference":
         run_reference(args, params)

@@ -320,6 +320,16 @@ cs_status cs_modsolve(const uint64_t *p, const uint64_t *K, const uint64_t *L, c
 cs_status cs_issue_rate(int mix, uint32_t iters, uint32_t *sink, uint64_t sink_words, void *stream,
                         double *thread_ops, float *ms);
 
+/* Scattered bit clears: every resident thread (one wave) performs
+ * ops_per_thread 32-bit atomic ANDs, each clearing one pseudo-random bit of a
+ * pseudo-random word of region[0 .. n_words) (device memory owned by the
+ * caller, whose contents it changes), after one untimed shorter launch.  The
+ * access pattern of the large-prime walk's bit clears, measured over a region
+ * of the bitset's size.  *clears (host): atomics of the timed launch; *ms: its
+ * duration from CUDA events on `stream`.  Synchronises `stream`. */
+cs_status cs_atomic_rate(uint32_t *region, uint64_t n_words, uint32_t ops_per_thread, void *stream,
+                         double *clears, float *ms);
+
 /* ---- allocation-free variant -------------------------------------------- */
 
 /* The same prime list as cs_primes, for callers that must not allocate device

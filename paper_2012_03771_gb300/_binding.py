@@ -36,7 +36,8 @@ EXPORTS = ("cs_plan", "cs_sieve", "cs_sync", "cs_info", "cs_fetch_bitset", "cs_c
            "cs_batch_create", "cs_batch_run", "cs_batch_sync", "cs_batch_info", "cs_batch_destroy",
            "cs_server_start", "cs_submit", "cs_poll", "cs_server_plan", "cs_release", "cs_server_usage",
            "cs_server_stop", "cs_fetch_rows", "cs_cache_create", "cs_cache_fill", "cs_cache_info",
-           "cs_cache_destroy", "cs_plan_cached", "cs_autotune", "cs_row_columns", "cs_issue_rate")
+           "cs_cache_destroy", "cs_plan_cached", "cs_autotune", "cs_row_columns", "cs_issue_rate",
+           "cs_atomic_rate")
 
 
 class CSError(RuntimeError):
@@ -131,6 +132,8 @@ def load(path: Optional[str] = None):
                                        ctypes.POINTER(vp)]
         lib.cs_issue_rate.argtypes = [i32, u32, vp, u64, vp, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_float)]
+        lib.cs_atomic_rate.argtypes = [vp, u64, u32, vp, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_float)]
         for n in EXPORTS:
             if n not in ("cs_device_bitset", "cs_last_error"):
                 getattr(lib, n).restype = i32
@@ -286,6 +289,14 @@ def cs_issue_rate(mix: int, iters: int, sink_ptr: int, sink_words: int, stream=N
     _check(load().cs_issue_rate(mix, iters, ctypes.c_void_p(sink_ptr), sink_words, _stream_handle(stream),
                                 ctypes.byref(ops), ctypes.byref(ms)))
     return float(ops.value), float(ms.value)
+
+
+def cs_atomic_rate(region_ptr: int, n_words: int, ops_per_thread: int, stream=None):
+    """(atomic bit clears, milliseconds) of one scattered-clear launch over region_ptr[0 .. n_words)."""
+    n, ms = ctypes.c_double(), ctypes.c_float()
+    _check(load().cs_atomic_rate(ctypes.c_void_p(region_ptr), n_words, ops_per_thread, _stream_handle(stream),
+                                 ctypes.byref(n), ctypes.byref(ms)))
+    return float(n.value), float(ms.value)
 
 
 def cs_autotune(P, d, M_start, M_inc, SL, L, cache_path: Optional[str] = None) -> dict:

@@ -780,23 +780,10 @@ cs_status validate_params(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_i
 
 }  // namespace cs
 
-extern "C" {
+namespace cs {
 
-cs_status cs_plan(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL,
-                  uint64_t L, const cs_tuning *tune, cs_plan_t *out) {
-    return cs::plan_create(P, d, M_start, M_inc, SL, L, tune, nullptr, false, nullptr, out);
-}
-
-cs_status cs_plan_cached(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL,
-                         uint64_t L, const cs_tuning *tune, cs_cache_t cache, cs_plan_t *out) {
-    if (!cache) return fail(CS_EINVAL, "cache is NULL");
-    return cs::plan_create(P, d, M_start, M_inc, SL, L, tune, nullptr, false, cache, out);
-}
-
-cs_status cs_sieve(cs_plan_t pl, void *stream) {
-    if (!pl) return fail(CS_EINVAL, "plan is NULL");
+cs_status plan_sieve_head(cs_plan_t pl, cudaStream_t st) {
     if (pl->sticky) return pl->sticky;
-    cudaStream_t st = (cudaStream_t)stream;
     pl->stream = st;
     const DevPlan &dp = pl->dp;
     Prof prof{pl, st, pl->tune.profile != 0};
@@ -812,7 +799,63 @@ cs_status cs_sieve(cs_plan_t pl, void *stream) {
     }
     if ((s = prof.begin(KC_TILE))) return s;
     CS_CUDA(launch_tile(dp, pl->tc, pl->d_small, pl->d_counts, pl->small_cap, st));
+    return prof.end();
+}
+
+bool plan_walk_jobs(cs_plan_t pl, std::vector<WalkJob> &out) {
+    if (!pl->cache || pl->mode != LARGE_THREE_GAP || pl->tune.profile || pl->tune.large_grid) return false;
+    ResidueCacheView cv;
+    cache_view(pl->cache, &cv);
+    for (size_t c = 0; c < pl->chunks.size(); c++) {
+        const CacheChunk &ch = cv.chunks[pl->cache_idx[c]];
+        out.push_back(WalkJob{pl->dp, ch.narrow, ch.p, ch.r, ch.count, ch.cap, pl->chunk_seg[c], pl->T, pl->L,
+                              pl->chunk_mc[c]});
+    }
+    return true;
+}
+
+cs_status plan_sieve_tail(cs_plan_t pl, cudaStream_t st) {
+    Prof prof{pl, st, pl->tune.profile != 0};
+    cs_status s;
+    if ((s = prof.begin(KC_FINAL))) return s;
+    CS_CUDA(launch_final(pl->dp, st));
     if ((s = prof.end())) return s;
+    // inside a stream capture the completion event becomes an event-record node
+    // of the graph, so that it is recorded each time the graph runs
+    cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
+    CS_CUDA(cudaStreamIsCapturing(st, &capst));
+    if (capst == cudaStreamCaptureStatusActive)
+        CS_CUDA(cudaEventRecordWithFlags(pl->done, st, cudaEventRecordExternal));
+    else
+        CS_CUDA(cudaEventRecord(pl->done, st));
+    pl->sieved = true;
+    return CS_OK;
+}
+
+}  // namespace cs
+
+extern "C" {
+
+cs_status cs_plan(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL,
+                  uint64_t L, const cs_tuning *tune, cs_plan_t *out) {
+    return cs::plan_create(P, d, M_start, M_inc, SL, L, tune, nullptr, false, nullptr, out);
+}
+
+cs_status cs_plan_cached(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL,
+                         uint64_t L, const cs_tuning *tune, cs_cache_t cache, cs_plan_t *out) {
+    if (!cache) return fail(CS_EINVAL, "cache is NULL");
+    return cs::plan_create(P, d, M_start, M_inc, SL, L, tune, nullptr, false, cache, out);
+}
+
+
+cs_status cs_sieve(cs_plan_t pl, void *stream) {
+    if (!pl) return fail(CS_EINVAL, "plan is NULL");
+    if (pl->sticky) return pl->sticky;
+    cudaStream_t st = (cudaStream_t)stream;
+    const DevPlan &dp = pl->dp;
+    cs_status s;
+    if ((s = cs::plan_sieve_head(pl, st))) return s;
+    Prof prof{pl, st, pl->tune.profile != 0};
     cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
     CS_CUDA(cudaStreamIsCapturing(st, &capst));
     if (pl->cache) {
@@ -845,17 +888,7 @@ cs_status cs_sieve(cs_plan_t pl, void *stream) {
                              pl->chunk_mc[c]));
         if ((s = prof.end())) return s;
     }
-    if ((s = prof.begin(KC_FINAL))) return s;
-    CS_CUDA(launch_final(dp, st));
-    if ((s = prof.end())) return s;
-    // inside a stream capture the completion event becomes an event-record node
-    // of the graph, so that it is recorded each time the graph runs
-    if (capst == cudaStreamCaptureStatusActive)
-        CS_CUDA(cudaEventRecordWithFlags(pl->done, st, cudaEventRecordExternal));
-    else
-        CS_CUDA(cudaEventRecord(pl->done, st));
-    pl->sieved = true;
-    return CS_OK;
+    return cs::plan_sieve_tail(pl, st);
 }
 
 cs_status cs_sync(cs_plan_t pl) {

@@ -146,6 +146,27 @@ cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p
                          uint64_t p_hi = ~0ull, MClasses mc = EVERY_M);
 cudaError_t launch_final(const DevPlan &pl, cudaStream_t stream);
 
+// One chunk's three-gap walk as a job of a persistent multi-job launch (the
+// arguments launch_large takes, primes from a residue-cache chunk).
+struct WalkJob {
+    DevPlan pl;
+    bool narrow;
+    const void *p, *r;
+    const unsigned long long *count;
+    uint64_t cap;
+    uint32_t n_seg;
+    uint64_t p_lo, p_hi;
+    MClasses mc;
+};
+// The jobs grouped by walk kernel, in device memory; walk_jobs_launch enqueues
+// one persistent launch per kernel that has jobs (each job's walk in its
+// order within the group).
+struct WalkJobs;
+cudaError_t walk_jobs_create(const std::vector<WalkJob> &jobs, WalkJobs **out);
+cudaError_t walk_jobs_launch(const WalkJobs *wj, cudaStream_t stream);
+uint64_t walk_jobs_launches(const WalkJobs *wj);
+void walk_jobs_destroy(WalkJobs *wj);
+
 // K's prime factors qK packed into factor words below 2^31 (the generator's
 // lazily reduced Montgomery product) and below 2^64, first fit with the
 // largest factors first: K = product of either list.
@@ -190,6 +211,14 @@ cs_status cache_new(uint32_t P, uint64_t d, uint64_t L_max, cs_cache_t *out);
 // ---- plan internals used by the batch and server runtime (cs_runtime.cu) ----
 // Builds a plan; with async_alloc its device memory is stream-ordered on
 // alloc_stream (cudaMallocAsync / cudaFreeAsync).
+// A cached three-gap plan's sieve in three phases, for batches that run the
+// walks of all their plans in persistent multi-job launches: the head
+// (statistics reset, small primes, tile sieve), the walk jobs (one per large
+// prime chunk; false if the plan does not qualify), the tail (counts and
+// checksum, completion event).
+cs_status plan_sieve_head(cs_plan_t pl, cudaStream_t stream);
+bool plan_walk_jobs(cs_plan_t pl, std::vector<WalkJob> &out);
+cs_status plan_sieve_tail(cs_plan_t pl, cudaStream_t stream);
 cs_status plan_create(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL,
                       uint64_t L, const cs_tuning *tune, cudaStream_t alloc_stream, bool async_alloc,
                       cs_cache_t cache, cs_plan_t *out);

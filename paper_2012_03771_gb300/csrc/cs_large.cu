@@ -19,6 +19,8 @@
 // Each hit on a coprime m and a stored x clears one bit of the device bitset
 // with a 32-bit atomic AND and counts one enumerated factor.
 #include <atomic>
+#include <new>
+#include <vector>
 
 #include "cs_arith.cuh"
 #include "cs_internal.h"
@@ -245,20 +247,17 @@ __device__ __forceinline__ uint64_t mul_add_mod(uint64_t v, uint64_t r, uint32_t
 #define CS_TG_MIN_BLOCKS_WIDE 3
 #endif
 
-template <class UT, class ST, class MT, int NC, bool CI = false>
-__global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLOCKS : CS_TG_MIN_BLOCKS_WIDE) k_large_tg(const LargeArgs a) {
+// One warp's share of a walk: the batches warp_id, warp_id + n_warps, ... of
+// 32 work items of the chunk that `a` describes, prepared into the warp's
+// queue q and walked by its lanes until the share is done and the queue is
+// empty; then the warp's counters go to the plan's statistics.  item_off: the
+// class residues of class items (shared memory).
+template <class UT, class ST, class MT, int NC, bool CI>
+__device__ __forceinline__ void walk_warp(const LargeArgs &a, TGItem<MT> *q, const uint8_t *item_off,
+                                          uint64_t warp_id, uint64_t n_warps) {
     static_assert(!CI || NC == 1, "class items walk one class per item");
     constexpr int QCAP = 32 * (NC + 1);   // a refill adds at most 32 NC walkers
-    __shared__ TGItem<MT> queue[TG_WARPS][QCAP];
-    __shared__ uint8_t item_off[CI ? MAX_CLASS_ITEMS : 1];   // class items: residue of each class
     const uint32_t n_cls_items = CI ? a.mc.items : 1;
-    if constexpr (CI) {
-        if (threadIdx.x == 0) {
-#pragma unroll
-            for (uint32_t k = 0; k < MAX_CLASS_ITEMS; k++) item_off[k] = a.mc.item_off[k];
-        }
-        __syncthreads();
-    }
     const DevPlan &pl = a.pl;
     const UT *Pp = reinterpret_cast<const UT *>(a.p);
     const UT *Rp = reinterpret_cast<const UT *>(a.r);
@@ -269,16 +268,13 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
     const uint32_t Q = a.mc.Q;
     const uint32_t max_iter = 4 * 8 * sizeof(UT) + 8;
     const uint32_t n_seg = a.n_seg;
-    const unsigned lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1;
     const uint64_t n_items = n * n_seg * n_cls_items;
-    const uint64_t warp_id = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-    const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     // any step >= M ends a walker (its segment is at most M long); two clamped
     // steps still add up below 2^32
     const uint64_t cap_step = M;
     const uint64_t seg_len = (M + n_seg - 1) / n_seg;
-    TGItem<MT> *q = queue[wib];
     Counters c;
     if (M == 0) return;
 
@@ -508,6 +504,49 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
     }
 }
 
+template <class UT, class ST, class MT, int NC, bool CI = false>
+__global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLOCKS : CS_TG_MIN_BLOCKS_WIDE) k_large_tg(const LargeArgs a) {
+    constexpr int QCAP = 32 * (NC + 1);
+    __shared__ TGItem<MT> queue[TG_WARPS][QCAP];
+    __shared__ uint8_t item_off[CI ? MAX_CLASS_ITEMS : 1];   // class items: residue of each class
+    if constexpr (CI) {
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (uint32_t k = 0; k < MAX_CLASS_ITEMS; k++) item_off[k] = a.mc.item_off[k];
+        }
+        __syncthreads();
+    }
+    walk_warp<UT, ST, MT, NC, CI>(a, queue[threadIdx.x >> 5], item_off,
+                                  (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5,
+                                  ((uint64_t)gridDim.x * blockDim.x) >> 5);
+}
+
+// The walks of many chunks, of many plans, in one persistent launch: every
+// warp takes its share of job 0, then of job 1, and so on, without waiting for
+// the other warps between jobs (a launch per chunk would wait for its slowest
+// warp each time).  The jobs' descriptors are in device memory; each warp
+// copies the current one into shared memory.
+template <class UT, class ST, class MT, int NC, bool CI = false>
+__global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLOCKS : CS_TG_MIN_BLOCKS_WIDE)
+    k_large_tg_jobs(const LargeArgs *jobs, uint32_t n_jobs) {
+    constexpr int QCAP = 32 * (NC + 1);
+    __shared__ TGItem<MT> queue[TG_WARPS][QCAP];
+    __shared__ LargeArgs job[TG_WARPS];
+    const unsigned lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint64_t warp_id = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    static_assert(sizeof(LargeArgs) % 4 == 0, "copied as 32-bit words");
+    constexpr uint32_t WORDS = sizeof(LargeArgs) / 4;
+    for (uint32_t j = 0; j < n_jobs; j++) {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(jobs + j);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&job[wib]);
+        for (uint32_t k = lane; k < WORDS; k += 32) dst[k] = __ldg(src + k);
+        __syncwarp();
+        walk_warp<UT, ST, MT, NC, CI>(job[wib], queue[wib], job[wib].mc.item_off, warp_id, n_warps);
+        __syncwarp();
+    }
+}
+
 template <class UT, class ST>
 __global__ void k_modsolve(const uint64_t *p, const uint64_t *K, const uint64_t *L,
                            const uint64_t *R, uint64_t *m, uint64_t n) {
@@ -570,6 +609,88 @@ cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p
         walk<<<grid, LARGE_THREADS, 0, stream>>>(a);
     }
     return cudaGetLastError();
+}
+
+struct WalkJobs {
+    // one group per walk kernel: [narrow][kind]
+    LargeArgs *d_jobs[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    uint32_t n_jobs[2][3] = {{0, 0, 0}, {0, 0, 0}};
+};
+
+namespace {
+// MClasses as launch_large normalises them, and the walk kernel they select
+int walk_kind(MClasses &mc, uint32_t SL) {
+    const bool items_ok = mc.items == mc.n && mc.n <= MAX_CLASS_ITEMS && mc.Q <= 256;
+    if (mc.Q == 0 || mc.n < 1 || mc.n > mc.Q || (mc.items ? !items_ok : mc.n > 2) || SL == 0) mc = EVERY_M;
+    return mc.items ? 2 : mc.n == 2 ? 1 : 0;
+}
+}  // namespace
+
+cudaError_t walk_jobs_create(const std::vector<WalkJob> &jobs, WalkJobs **out) {
+    *out = nullptr;
+    std::vector<LargeArgs> g[2][3];
+    for (const WalkJob &j : jobs) {
+        MClasses mc = j.mc;
+        const int kind = walk_kind(mc, j.pl.SL);
+        g[j.narrow ? 1 : 0][kind].push_back(
+            LargeArgs{j.pl, j.p, j.r, nullptr, j.count, j.cap, j.n_seg ? j.n_seg : 1, j.p_lo, j.p_hi, mc});
+    }
+    WalkJobs *wj = new (std::nothrow) WalkJobs();
+    if (!wj) return cudaErrorMemoryAllocation;
+    for (int nw = 0; nw < 2; nw++)
+        for (int k = 0; k < 3; k++) {
+            if (g[nw][k].empty()) continue;
+            const size_t bytes = g[nw][k].size() * sizeof(LargeArgs);
+            cudaError_t e = cudaMalloc(&wj->d_jobs[nw][k], bytes);
+            if (e == cudaSuccess) e = cudaMemcpy(wj->d_jobs[nw][k], g[nw][k].data(), bytes, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                walk_jobs_destroy(wj);
+                return e;
+            }
+            wj->n_jobs[nw][k] = (uint32_t)g[nw][k].size();
+        }
+    *out = wj;
+    return cudaSuccess;
+}
+
+cudaError_t walk_jobs_launch(const WalkJobs *wj, cudaStream_t stream) {
+    for (int nw = 0; nw < 2; nw++)
+        for (int k = 0; k < 3; k++) {
+            if (!wj->n_jobs[nw][k]) continue;
+            void (*kern)(const LargeArgs *, uint32_t);
+            if (nw) {
+                kern = k == 2 ? k_large_tg_jobs<uint32_t, int32_t, uint32_t, 1, true>
+                     : k == 1 ? k_large_tg_jobs<uint32_t, int32_t, uint32_t, 2>
+                              : k_large_tg_jobs<uint32_t, int32_t, uint32_t, 1>;
+            } else {
+                kern = k == 2 ? k_large_tg_jobs<uint64_t, int64_t, uint32_t, 1, true>
+                     : k == 1 ? k_large_tg_jobs<uint64_t, int64_t, uint32_t, 2>
+                              : k_large_tg_jobs<uint64_t, int64_t, uint32_t, 1>;
+            }
+            int per_sm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, LARGE_THREADS, 0) != cudaSuccess ||
+                per_sm <= 0)
+                per_sm = 1;
+            kern<<<sm_count() * per_sm, LARGE_THREADS, 0, stream>>>(wj->d_jobs[nw][k], wj->n_jobs[nw][k]);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
+uint64_t walk_jobs_launches(const WalkJobs *wj) {
+    uint64_t n = 0;
+    for (int nw = 0; nw < 2; nw++)
+        for (int k = 0; k < 3; k++) n += wj->n_jobs[nw][k] ? 1 : 0;
+    return n;
+}
+
+void walk_jobs_destroy(WalkJobs *wj) {
+    if (!wj) return;
+    for (int nw = 0; nw < 2; nw++)
+        for (int k = 0; k < 3; k++)
+            if (wj->d_jobs[nw][k]) cudaFree(wj->d_jobs[nw][k]);
+    delete wj;
 }
 
 cudaError_t launch_modsolve(const uint64_t *p, const uint64_t *K, const uint64_t *L,

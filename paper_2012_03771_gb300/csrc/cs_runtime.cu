@@ -7,13 +7,19 @@
 // * Batch: a fixed set of plans, spread over worker streams with the longest
 //   first (greedy longest-processing-time assignment on each plan's cost
 //   estimate), the whole launch sequence captured once into a CUDA graph and
-//   replayed with one launch.
+//   replayed with one launch.  When every plan reads its large primes from a
+//   residue cache, the walks of all plans and all their prime chunks run as
+//   jobs of a few persistent launches (one per walk kernel, the most costly
+//   plans' jobs first) between the plans' tile sieves and their counts, so that
+//   no warp waits at the end of a chunk for the slowest one.
 // * Server: requests arrive over time; a request is admitted when a slot (a
 //   stream) is free and its device memory fits the budget, its plan is built
 //   with stream-ordered allocation and sieved on the slot's stream, so it
 //   overlaps with the requests already running; its bitset stays resident until
 //   the caller releases the ticket.
 #include <cuda_runtime.h>
+
+#include <stdlib.h>
 
 #include <algorithm>
 #include <mutex>
@@ -30,8 +36,9 @@ struct cs_batch_s {
     std::vector<cs_plan_t> plans;
     std::vector<cudaStream_t> streams;
     cudaStream_t origin = nullptr;
-    cudaEvent_t fork = nullptr, done = nullptr;
-    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr, fork2 = nullptr, done = nullptr;
+    std::vector<cudaEvent_t> join, join2;
+    WalkJobs *wj = nullptr;               // persistent multi-job walks (cached plans)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool launched = false;
@@ -41,7 +48,10 @@ struct cs_batch_s {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         for (auto e : join) cudaEventDestroy(e);
+        for (auto e : join2) cudaEventDestroy(e);
         if (fork) cudaEventDestroy(fork);
+        if (fork2) cudaEventDestroy(fork2);
+        walk_jobs_destroy(wj);
         if (done) cudaEventDestroy(done);
         for (auto s : streams) cudaStreamDestroy(s);
         if (origin) cudaStreamDestroy(origin);
@@ -148,6 +158,19 @@ cs_status cs_batch_create(const cs_plan_t *plans, int n, int n_streams, cs_batch
     if (!b) return set_error(CS_ENOMEM, "host allocation failed");
     b->plans.assign(plans, plans + n);
     cs_status s = CS_OK;
+    // the walks as jobs of persistent launches when every plan is a cached
+    // three-gap plan (CS_BATCH_JOBS=0: one launch per chunk, as cs_sieve)
+    std::vector<WalkJob> jobs;
+    const char *bj = getenv("CS_BATCH_JOBS");
+    bool use_jobs = !(bj && atoi(bj) == 0);
+    for (size_t o = 0; o < order.size() && use_jobs; o++) use_jobs = plan_walk_jobs(plans[order[o].second], jobs);
+    if (use_jobs) {
+        cudaError_t ej = walk_jobs_create(jobs, &b->wj);
+        if (ej != cudaSuccess) {
+            delete b;
+            return cuda_err(ej, "walk_jobs_create");
+        }
+    }
 #define BT(call)                                          \
     do {                                                  \
         s = cuda_err((call), #call);                      \
@@ -155,14 +178,17 @@ cs_status cs_batch_create(const cs_plan_t *plans, int n, int n_streams, cs_batch
     } while (0)
     BT(cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking));
     BT(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    BT(cudaEventCreateWithFlags(&b->fork2, cudaEventDisableTiming));
     BT(cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming));
     for (int k = 0; k < n_streams + (int)caches.size(); k++) {
         cudaStream_t st;
         BT(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
         b->streams.push_back(st);
-        cudaEvent_t ev;
+        cudaEvent_t ev, ev2;
         BT(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
         b->join.push_back(ev);
+        BT(cudaEventCreateWithFlags(&ev2, cudaEventDisableTiming));
+        b->join2.push_back(ev2);
     }
     BT(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
     cs_status cap = CS_OK;
@@ -183,12 +209,29 @@ cs_status cs_batch_create(const cs_plan_t *plans, int n, int n_streams, cs_batch
         e = cudaStreamWaitEvent(b->streams[k], b->fork, 0);
         for (int i : lane[k]) {
             if (e != cudaSuccess || cap) break;
-            cap = cs_sieve(b->plans[i], b->streams[k]);
+            cap = b->wj ? plan_sieve_head(b->plans[i], b->streams[k]) : cs_sieve(b->plans[i], b->streams[k]);
             cs_info_t info;
-            if (!cap && !cs_info(b->plans[i], &info)) b->launches += info.launches_per_sieve;
+            if (!cap && !cs_info(b->plans[i], &info))
+                b->launches += info.launches_per_sieve - (b->wj ? info.n_large_chunks : 0);
         }
         if (e == cudaSuccess && !cap) e = cudaEventRecord(b->join[k], b->streams[k]);
         if (e == cudaSuccess && !cap) e = cudaStreamWaitEvent(b->origin, b->join[k], 0);
+    }
+    if (b->wj && e == cudaSuccess && !cap) {
+        // every plan's tile sieve and every cache are done: the walks of all
+        // plans, then each plan's counts on its worker stream
+        e = walk_jobs_launch(b->wj, b->origin);
+        b->launches += walk_jobs_launches(b->wj);
+        if (e == cudaSuccess) e = cudaEventRecord(b->fork2, b->origin);
+        for (int k = 0; k < n_streams && e == cudaSuccess && !cap; k++) {
+            e = cudaStreamWaitEvent(b->streams[k], b->fork2, 0);
+            for (int i : lane[k]) {
+                if (e != cudaSuccess || cap) break;
+                cap = plan_sieve_tail(b->plans[i], b->streams[k]);
+            }
+            if (e == cudaSuccess && !cap) e = cudaEventRecord(b->join2[k], b->streams[k]);
+            if (e == cudaSuccess && !cap) e = cudaStreamWaitEvent(b->origin, b->join2[k], 0);
+        }
     }
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(b->origin, &g);

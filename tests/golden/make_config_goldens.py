@@ -20,6 +20,9 @@ NAME is one of:
                every instance.
   served_256   the 256-request served stream (seed 201203772): 4 evenly
                spaced rows of every request.
+  fig1_1511    the speed-up curve's 10-interval point (Figure 1's shape: K =
+               1511#/210, X = 18,000, primes up to 1e11, m = 1 .. 41): every
+               row.  About 6 minutes on 8 cores.
 
 Per-row checksum: the oracle's bitset checksum of the row alone, taken at the
 row's position in the whole bitset (``oracle.bitset_hash(row, row0=i)``); the
@@ -120,6 +123,16 @@ def _instances(mix, threads: int, per: int = 4):
                 F_rows=np.array(Fr, dtype=np.uint32), row_hash=np.array(rh, dtype=U64))
 
 
+def fig1_1511(threads: int):
+    P, d, SL, L = 1511, 210, 18000, 10**11
+    rows = O.rows(d, 1, 41)                           # the first 10 m coprime to 210
+    assert len(rows) == 10
+    bits, F, _ = O.sieve(P, d, SL, L, rows, threads=threads)
+    return dict(params=np.array((P, d, 1, 41, SL, L), dtype=np.int64), m=rows.astype(U64),
+                counts=O.row_counts(bits).astype(np.uint32), F_rows=F.astype(np.uint32),
+                row_hash=_row_hashes(bits, range(len(rows))), F=U64(int(F.sum())), hash=U64(O.bitset_hash(bits)))
+
+
 def batched_64(threads: int):
     return _instances(WL.batched_instances(64, seed=WL.BATCH_SEED), threads)
 
@@ -128,7 +141,8 @@ def served_256(threads: int):
     return _instances(WL.batched_instances(256, seed=WL.BATCH_SEED + 1), threads)
 
 
-JOBS = {"search_953": search_953, "large_1019": large_1019, "batched_64": batched_64, "served_256": served_256}
+JOBS = {"search_953": search_953, "large_1019": large_1019, "batched_64": batched_64, "served_256": served_256,
+        "fig1_1511": fig1_1511}
 
 
 def main():

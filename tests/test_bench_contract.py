@@ -46,9 +46,11 @@ def _info(**kw):
 
 
 def test_roofline_uses_counters_only_for_the_same_sources_and_setup(bench, monkeypatch):
-    """achieved = stored thread instructions per walk launch / the launch's timed
-    duration; peak = the best measured issue rate of the micro-benchmark; the
-    counters apply only to the same sources, threshold, tile height and chunking."""
+    """The walk's two bounds: issue (stored thread instructions per launch over the
+    launch's timed duration, against the best measured issue rate; the counters
+    apply only to the same sources, threshold, tile height and chunking) and
+    scattered clears (live stored hits against the measured clear rate).  The
+    bound that needs more time binds."""
     ctr = {"csrc_sha": bench.csrc_sha(), "threshold": 120003, "tile_rows": 16, "launches": 17,
            "thread_inst": 8.77e10, "dram_bytes": 1.24e9}
     monkeypatch.setitem(bench.WALK_COUNTERS, "search_953", ctr)
@@ -56,23 +58,31 @@ def test_roofline_uses_counters_only_for_the_same_sources_and_setup(bench, monke
     kern_ms = [0.0] * len(bench.KC_NAMES)
     kern_n = [0] * len(bench.KC_NAMES)
     kern_ms[walk], kern_n[walk] = 10 * 5.9, 10 * ctr["launches"]      # 10 sieves
-    stats = {"hits_all": 7.47e8 * 10, "levels": 4.5e8 * 10}
+    stats = {"hits_all": 7.47e8, "levels": 4.5e8, "F_large": 1.71e8}
     peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
     issue = {"add_logic": 20.5, "imad": 19.0, "imad_logic": 38.25}
-    r = bench.roofline(walk, kern_ms, kern_n, stats, _info(), None, peaks, "measured", issue, "search_953")
+    args = (None, peaks, "measured", issue, "search_953")
+    # issue binds (fast clears, as for a bitset in L2)
+    r = bench.roofline(walk, kern_ms, kern_n, stats, _info(), *args, clears_peak=2e11)
     assert r["bound"] == "alu" and r["unit"] == "Tinst/s" and r["peak"] == 38.25
     per_launch_s = 5.9e-3 / ctr["launches"]
     want = ctr["thread_inst"] / ctr["launches"] / per_launch_s / 1e12
     assert abs(r["achieved"] - want) < 1e-9 * want and abs(r["frac"] - want / 38.25) < 1e-12
     assert abs(r["traffic"] - ctr["dram_bytes"] / ctr["launches"]) < 1.0
-    # another threshold, tile height, chunking or source digest: the counters do not apply
+    assert r["bounds"]["clears"]["min_ms_per_launch"] < r["bounds"]["issue"]["min_ms_per_launch"]
+    # clears bind (slow scattered clears, as for a bitset far larger than L2)
+    r = bench.roofline(walk, kern_ms, kern_n, stats, _info(), *args, clears_peak=2e10)
+    want_c = stats["F_large"] / ctr["launches"] / per_launch_s / 1e9
+    assert r["bound"] == "hbm" and r["unit"] == "Gclears/s" and r["peak"] == 20.0
+    assert abs(r["achieved"] - want_c) < 1e-9 * want_c and abs(r["frac"] - want_c / 20.0) < 1e-12
+    # another threshold, tile height, chunking or source digest: no issue bound
     for other in (_info(threshold=80002), _info(tile_rows=8), _info(n_large_chunks=24)):
-        r = bench.roofline(walk, kern_ms, kern_n, stats, other, None, peaks, "measured", issue, "search_953")
+        r = bench.roofline(walk, kern_ms, kern_n, stats, other, *args)
         assert r["achieved"] is None and r["frac"] is None and "note" in r
     monkeypatch.setitem(bench.WALK_COUNTERS, "search_953", dict(ctr, csrc_sha="0" * 16))
-    r = bench.roofline(walk, kern_ms, kern_n, stats, _info(), None, peaks, "measured", issue, "search_953")
+    r = bench.roofline(walk, kern_ms, kern_n, stats, _info(), *args)
     assert r["achieved"] is None
-    # no measured peak: no fraction (never a derived stand-in)
+    # no measured peaks: no fraction (never a derived stand-in)
     monkeypatch.setitem(bench.WALK_COUNTERS, "search_953", ctr)
     r = bench.roofline(walk, kern_ms, kern_n, stats, _info(), None, peaks, "measured", {"error": "x"}, "search_953")
     assert r["peak"] is None and r["frac"] is None

@@ -237,3 +237,35 @@ def test_batch_of_cached_plans_equals_alone():
         p.close()
     for c in caches.values():
         c.close()
+
+
+def test_batch_walk_jobs_equal_one_launch_per_chunk(monkeypatch):
+    """Cached plans in a batch walk as jobs of a few persistent launches (one per
+    walk kernel); with CS_BATCH_JOBS=0 every chunk has its own launch.  Both give
+    every instance's alone result, in fewer launches with the jobs."""
+    mix = _small_mix(12, seed=12) + [workloads.SieveParams(P=503, d=2310, M_start=10**6, M_inc=3000, SL=3000,
+                                                           L=3 * 10**9)]
+    ref = [_alone(prm) for prm in mix]
+    caches = {}
+    for prm in mix:
+        caches[(prm.P, prm.d)] = max(caches.get((prm.P, prm.d), 0), prm.L)
+    caches = {k: cs.Cache(k[0], k[1], L) for k, L in caches.items()}
+    plans = [cs.Plan(*prm.as_tuple(), cache=caches[(prm.P, prm.d)]) for prm in mix]
+    launches = {}
+    for jobs in ("1", "0"):
+        monkeypatch.setenv("CS_BATCH_JOBS", jobs)
+        batch = cs.Batch(plans, n_streams=2)
+        monkeypatch.delenv("CS_BATCH_JOBS")
+        launches[jobs] = batch.launches
+        for _ in range(2):
+            batch.run().sync()
+            for p, (counts, F, h) in zip(plans, ref):
+                c2, F2, h2 = p.counts()
+                assert (F2, h2) == (F, h)
+                assert np.array_equal(c2, counts)
+        batch.close()
+    assert launches["1"] < launches["0"]
+    for p in plans:
+        p.close()
+    for c in caches.values():
+        c.close()

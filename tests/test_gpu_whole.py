@@ -15,7 +15,9 @@ and is compared element by element (integers: tolerance 0):
   instance's counts, F and checksum equal to the instance alone;
 * the 256-request served stream (seed 201203772) through the request server
   (continuous batching, admission by memory): four rows of every request
-  against the oracle, and every request equal to its result alone.
+  against the oracle, and every request equal to its result alone;
+* the speed-up curve's 10-interval point (the shape of Figure 1: K = 1511#/210,
+  X = 18,000, primes up to 1e11): every row, F and the checksum.
 
 A row's checksum is the oracle's bitset checksum of that row alone at its
 position in the bitset (the checksum of a whole bitset is the sum of its rows').
@@ -190,3 +192,15 @@ def test_served_256_stream_matches_alone_and_oracle():
         assert (F2, h2) == (F1, h1), k
         assert np.array_equal(c2, c1), k
     _check_instances(g, reqs, results, [lambda i, k=k: fetched[k][i] for k in range(len(reqs))])
+
+
+def test_fig1_point_matches_oracle():
+    from paper_2012_03771_gb300.speedup_curve import m_inc_for
+    g = _golden("fig1_1511")
+    P, d, M_start, M_inc, SL, L = (int(v) for v in g["params"])
+    assert M_inc == m_inc_for(M_start, d, 10)
+    with cs.Plan(P, d, M_start, M_inc, SL, L) as p:
+        p.sieve(torch.cuda.current_stream()).sync()
+        counts, F, h = p.counts()
+        assert F == int(g["F"]) and h == int(g["hash"])
+        _check_rows(p, counts, range(10), g["m"], g["counts"], g["row_hash"], "fig1_1511")

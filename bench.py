@@ -510,9 +510,10 @@ def run_batched(args):
       plain          one instance after another, each generating its own primes;
       plain_cached   one instance after another, large primes from the shared
                      residue caches (filled once per step, as in the batch);
-      graph_launches the batch graph with one walk launch per prime chunk;
-      batch          the batch graph with the walks of all instances as jobs of
-                     a few persistent launches (the default batch).
+      batch          the batch graph (worker streams, cache fills inside it)
+                     with one walk launch per prime chunk (the default batch);
+      graph_jobs     the batch graph with the walks of all instances as jobs of
+                     a few persistent launches (CS_BATCH_JOBS=1).
     The headline ratio is batch against plain_cached: the caches on both arms."""
     import numpy as np
     import torch
@@ -575,14 +576,14 @@ def run_batched(args):
 
     arms["plain_cached"] = time_steps(plain_cached)
     ok = ok and same(cplans)
-    os.environ["CS_BATCH_JOBS"] = "0"
-    b_launch = cs.Batch(cplans, n_streams=args.batch_streams)
+    os.environ["CS_BATCH_JOBS"] = "1"
+    b_jobs = cs.Batch(cplans, n_streams=args.batch_streams)
     del os.environ["CS_BATCH_JOBS"]
-    arms["graph_launches"] = time_steps(lambda: b_launch.run(s))
-    b_launch.sync()
+    arms["graph_jobs"] = time_steps(lambda: b_jobs.run(s))
+    b_jobs.sync()
     ok = ok and same(cplans)
-    launches_per_chunk = b_launch.launches
-    b_launch.close()
+    launches_jobs = b_jobs.launches
+    b_jobs.close()
     batch = cs.Batch(cplans, n_streams=args.batch_streams)
     arms["batch"] = time_steps(lambda: batch.run(s))
     batch.sync()
@@ -597,7 +598,7 @@ def run_batched(args):
             "speedup_vs_plain": arms["plain"] / arms["batch"],
             "residue_caches": {"count": len(caches), "device_bytes": cache_bytes},
             "n_streams": batch.n_streams, "gpu_launches_per_step": batch.launches,
-            "gpu_launches_per_step_one_per_chunk": launches_per_chunk, "F_per_step": F_total,
+            "gpu_launches_per_step_jobs": launches_jobs, "F_per_step": F_total,
             "results_equal_alone": ok,
             "config": {"workload": "batched_64: P in {503,701,953,1019}, d in {210,2310}, M_inc log-U[1e3,1e6], "
                                    "SL U[5000,25000], L log-U[1e8,1e10], M_start log-U[1e6,1e8], seed 201203771",

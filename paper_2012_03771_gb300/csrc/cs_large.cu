@@ -74,8 +74,26 @@ struct Counters {
 // mask, each interleaved with its per-word prefix counts) that stay in L1.
 // The prime is read (from the chunk's array, entry idx) only when N + x can be
 // a sieving prime itself (K below 2^64).
-template <class UT>
-__device__ __forceinline__ void record_hit_z(const DevPlan &pl, uint64_t moff, uint32_t z, const UT *Pp,
+// The fields of a plan that a hit reads, held in registers by the multi-job
+// walk (its plan descriptors sit in shared memory, which the walkers' queue
+// stores would otherwise make it reload at every hit); the one-chunk walk reads
+// them from its kernel parameters.
+struct HitView {
+    const uint2 *row_tab, *col_tab;
+    uint64_t *bits;
+    uint32_t wpr, SL;
+    int small_n, compact;
+    uint64_t M_start, K64;
+    const uint32_t *cls_word, *cmask, *cprefix;
+    uint32_t n_cls, S32;
+};
+__device__ __forceinline__ HitView hit_view(const DevPlan &p) {
+    return HitView{p.row_tab, p.col_tab, p.bits, p.wpr, p.SL, p.small_n, p.compact, p.M_start, p.K64,
+                   p.cls_word, p.cmask, p.cprefix, p.n_cls, p.S32};
+}
+
+template <class UT, class PV = DevPlan>
+__device__ __forceinline__ void record_hit_z(const PV &pl, uint64_t moff, uint32_t z, const UT *Pp,
                                              uint32_t idx, Counters &c) {
     const uint32_t ms = (uint32_t)moff;                  // bit of m in its 32-m word: ms mod 32
     const uint2 rt = __ldg(&pl.row_tab[moff >> 5]);      // {coprime-m mask, rows before}
@@ -247,18 +265,20 @@ __device__ __forceinline__ uint64_t mul_add_mod(uint64_t v, uint64_t r, uint32_t
 #define CS_TG_MIN_BLOCKS_WIDE 3
 #endif
 
-// One warp's share of a walk: the batches warp_id, warp_id + n_warps, ... of
-// 32 work items of the chunk that `a` describes, prepared into the warp's
-// queue q and walked by its lanes until the share is done and the queue is
-// empty; then the warp's counters go to the plan's statistics.  item_off: the
-// class residues of class items (shared memory).
-template <class UT, class ST, class MT, int NC, bool CI>
+// One warp's share of a walk: the batches first, first + n_warps, ... of 32
+// work items of the chunk that `a` describes, prepared into the warp's queue q
+// and walked by its lanes until the share is done and the queue is empty;
+// then the warp's counters go to the plan's statistics.  item_off: the class
+// residues of class items (shared memory).
+template <class UT, class ST, class MT, int NC, bool CI, bool JOBS = false>
 __device__ __forceinline__ void walk_warp(const LargeArgs &a, TGItem<MT> *q, const uint8_t *item_off,
-                                          uint64_t warp_id, uint64_t n_warps) {
+                                          uint64_t first, uint64_t n_warps) {
     static_assert(!CI || NC == 1, "class items walk one class per item");
     constexpr int QCAP = 32 * (NC + 1);   // a refill adds at most 32 NC walkers
     const uint32_t n_cls_items = CI ? a.mc.items : 1;
     const DevPlan &pl = a.pl;
+    // the hit path's plan fields: kernel parameters, or registers for the multi-job walk
+    [[maybe_unused]] const HitView hv = JOBS ? hit_view(pl) : HitView{};
     const UT *Pp = reinterpret_cast<const UT *>(a.p);
     const UT *Rp = reinterpret_cast<const UT *>(a.r);
     const UT *Vp = reinterpret_cast<const UT *>(a.v);
@@ -278,7 +298,7 @@ __device__ __forceinline__ void walk_warp(const LargeArgs &a, TGItem<MT> *q, con
     Counters c;
     if (M == 0) return;
 
-    uint64_t batch = warp_id;          // next batch of 32 items to prepare
+    uint64_t batch = first;            // next batch of 32 items to prepare
     uint32_t qhead = 0, qcount = 0;    // warp-uniform ring state
     bool active = false;
     // walker: m offset, segment end, raw offset z = 2SL - v, and the three steps
@@ -480,7 +500,10 @@ __device__ __forceinline__ void walk_warp(const LargeArgs &a, TGItem<MT> *q, con
         constexpr int STEPS = NC == 1 && !CI ? TG_STEPS_ALL_M : TG_STEPS;
         int u = 0;
         for (; u < STEPS && active; u++) {
-            record_hit_z<UT>(pl, (uint64_t)moff, z, Pp, idx, c);
+            if constexpr (JOBS)
+                record_hit_z<UT>(hv, (uint64_t)moff, z, Pp, idx, c);
+            else
+                record_hit_z<UT>(pl, (uint64_t)moff, z, Pp, idx, c);
             const bool down = z <= wmda;
             const bool up = z >= ub;
             z += down ? da : (up ? nub : dmu);
@@ -521,13 +544,21 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
                                   ((uint64_t)gridDim.x * blockDim.x) >> 5);
 }
 
-// The walks of many chunks, of many plans, in one persistent launch: every
-// warp takes its share of job 0, then of job 1, and so on, without waiting for
-// the other warps between jobs (a launch per chunk would wait for its slowest
-// warp each time).  The jobs' descriptors are in device memory; each warp
-// copies the current one into shared memory.
+// The walks of many chunks, of many plans, in one persistent launch: the
+// batches of all jobs, in job order, are dealt round-robin to the warps (each
+// job continues where the previous one stopped, so that the many small jobs do
+// not all fall on the first warps), and every warp walks its batches of job 0,
+// then of job 1, and so on, without waiting for the other warps between jobs
+// (a launch per chunk would wait for its slowest warp each time).  The jobs'
+// descriptors are in device memory; each warp copies the current one into
+// shared memory.
+// resident CTAs per SM the multi-job walk is compiled for: its hit path keeps
+// the plan's fields in registers, which at three CTAs per SM would spill
+#ifndef CS_TG_JOBS_MIN_BLOCKS
+#define CS_TG_JOBS_MIN_BLOCKS 2
+#endif
 template <class UT, class ST, class MT, int NC, bool CI = false>
-__global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLOCKS : CS_TG_MIN_BLOCKS_WIDE)
+__global__ void __launch_bounds__(LARGE_THREADS, CS_TG_JOBS_MIN_BLOCKS)
     k_large_tg_jobs(const LargeArgs *jobs, uint32_t n_jobs) {
     constexpr int QCAP = 32 * (NC + 1);
     __shared__ TGItem<MT> queue[TG_WARPS][QCAP];
@@ -537,12 +568,18 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
     const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     static_assert(sizeof(LargeArgs) % 4 == 0, "copied as 32-bit words");
     constexpr uint32_t WORDS = sizeof(LargeArgs) / 4;
+    uint64_t dealt = 0;                 // batches of the jobs before j
     for (uint32_t j = 0; j < n_jobs; j++) {
         const uint32_t *src = reinterpret_cast<const uint32_t *>(jobs + j);
         uint32_t *dst = reinterpret_cast<uint32_t *>(&job[wib]);
         for (uint32_t k = lane; k < WORDS; k += 32) dst[k] = __ldg(src + k);
         __syncwarp();
-        walk_warp<UT, ST, MT, NC, CI>(job[wib], queue[wib], job[wib].mc.item_off, warp_id, n_warps);
+        const LargeArgs &a = job[wib];
+        const uint64_t n = min((uint64_t)*a.count, a.cap);
+        const uint64_t batches = (n * a.n_seg * (CI ? a.mc.items : 1) + 31) / 32;
+        const uint64_t first = (warp_id + n_warps - dealt % n_warps) % n_warps;
+        walk_warp<UT, ST, MT, NC, CI, true>(a, queue[wib], a.mc.item_off, first, n_warps);
+        dealt += batches;
         __syncwarp();
     }
 }

@@ -7,11 +7,14 @@
 // * Batch: a fixed set of plans, spread over worker streams with the longest
 //   first (greedy longest-processing-time assignment on each plan's cost
 //   estimate), the whole launch sequence captured once into a CUDA graph and
-//   replayed with one launch.  When every plan reads its large primes from a
-//   residue cache, the walks of all plans and all their prime chunks run as
-//   jobs of a few persistent launches (one per walk kernel, the most costly
-//   plans' jobs first) between the plans' tile sieves and their counts, so that
-//   no warp waits at the end of a chunk for the slowest one.
+//   replayed with one launch.  With CS_BATCH_JOBS=1, when every plan reads its
+//   large primes from a residue cache, the walks of all plans and all their
+//   prime chunks run instead as jobs of a few persistent launches (one per walk
+//   kernel, the most costly plans' jobs first) between the plans' tile sieves
+//   and their counts.  That is not the default: on the 64-instance mix it
+//   measured 1.19 s per run against 0.99 s with a launch per chunk, which keeps
+//   one chunk's primes and one plan's bitset in L2 at a time and reads the plan
+//   from the kernel parameters.
 // * Server: requests arrive over time; a request is admitted when a slot (a
 //   stream) is free and its device memory fits the budget, its plan is built
 //   with stream-ordered allocation and sieved on the slot's stream, so it
@@ -158,11 +161,11 @@ cs_status cs_batch_create(const cs_plan_t *plans, int n, int n_streams, cs_batch
     if (!b) return set_error(CS_ENOMEM, "host allocation failed");
     b->plans.assign(plans, plans + n);
     cs_status s = CS_OK;
-    // the walks as jobs of persistent launches when every plan is a cached
-    // three-gap plan (CS_BATCH_JOBS=0: one launch per chunk, as cs_sieve)
+    // the walks as jobs of persistent launches (CS_BATCH_JOBS=1) when every
+    // plan is a cached three-gap plan; by default one launch per chunk, as cs_sieve
     std::vector<WalkJob> jobs;
     const char *bj = getenv("CS_BATCH_JOBS");
-    bool use_jobs = !(bj && atoi(bj) == 0);
+    bool use_jobs = bj && atoi(bj) == 1;
     for (size_t o = 0; o < order.size() && use_jobs; o++) use_jobs = plan_walk_jobs(plans[order[o].second], jobs);
     if (use_jobs) {
         cudaError_t ej = walk_jobs_create(jobs, &b->wj);

@@ -240,9 +240,10 @@ def test_batch_of_cached_plans_equals_alone():
 
 
 def test_batch_walk_jobs_equal_one_launch_per_chunk(monkeypatch):
-    """Cached plans in a batch walk as jobs of a few persistent launches (one per
-    walk kernel); with CS_BATCH_JOBS=0 every chunk has its own launch.  Both give
-    every instance's alone result, in fewer launches with the jobs."""
+    """Cached plans in a batch walk, with CS_BATCH_JOBS=1, as jobs of a few
+    persistent launches (one per walk kernel); by default every chunk has its
+    own launch.  Both give every instance's alone result, in fewer launches with
+    the jobs."""
     mix = _small_mix(12, seed=12) + [workloads.SieveParams(P=503, d=2310, M_start=10**6, M_inc=3000, SL=3000,
                                                            L=3 * 10**9)]
     ref = [_alone(prm) for prm in mix]

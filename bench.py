@@ -36,7 +36,7 @@ def metric_of(params) -> str:
 
 METRIC = "enumerated factors/s at L=1e9 (bit-exact bitset + per-m counts)"
 UNIT = "factors/s"
-KC_NAMES = ["gen_small", "tile_sieve", "gen_large", "large_walk", "final"]
+KC_NAMES = ["gen_small", "tile_sieve", "gen_large", "large_walk", "final", "hit_apply"]
 # autotuner results for this GPU, one line per (P, d, SL, ceil(log2 L))
 TUNE_FILE = os.path.join(ROOT, "paper_2012_03771_gb300", "tune_gb300.txt")
 
@@ -195,7 +195,9 @@ def _shape(info, tuned):
             "m_classes_walked": f"{int(info.m_walked)} of m mod {int(info.m_mod)}",
             "chunks_class_walk": f"{int(info.split_chunks)} of {int(info.n_large_chunks)}",
             "class_items": (f"{int(info.item_chunks)} chunks, finest {int(info.item_classes)} classes of "
-                            f"m mod {int(info.item_mod)}" if info.item_chunks else "none")}
+                            f"m mod {int(info.item_mod)}" if info.item_chunks else "none"),
+            "hit_buckets": ({"bands": int(info.n_bands), "bucket_bytes": int(info.bucket_bytes),
+                             "apply_launches": int(info.apply_launches)} if info.hit_buckets else None)}
 
 
 def run_cuda(args, params):
@@ -315,8 +317,13 @@ def run_cuda(args, params):
     issue = issue_rates(torch, cs, stream)
     plan.close()                                    # room for the scattered-clear probe
     clears_peak = clear_rate(torch, cs, stream, int(info.bitset_bytes) // 4)
+    # the apply kernel clears two bands at a time at most: its peak is the
+    # clear rate over a region of two bands' words
+    band_peak = (clear_rate(torch, cs, stream, 2 * int(info.bitset_bytes) // max(int(info.n_bands), 1) // 4)
+                 if info.hit_buckets else None)
     dom = max(range(len(KC_NAMES)), key=lambda i: kern_ms[i])
-    roof = roofline(dom, kern_ms, kern_n, stats, info, params, peaks, peak_src, issue, args.config, clears_peak)
+    roof = roofline(dom, kern_ms, kern_n, stats, info, params, peaks, peak_src, issue, args.config, clears_peak,
+                    band_peak)
 
     # ---- CPU oracle on a bounded sample -------------------------------------
     cpu = None
@@ -422,14 +429,19 @@ def clear_rate(torch, cs, stream, words):
         return None
 
 
-def roofline(dom, kern_ms, kern_n, stats, info, params, peaks, peak_src, issue, config, clears_peak=None):
+def roofline(dom, kern_ms, kern_n, stats, info, params, peaks, peak_src, issue, config, clears_peak=None,
+             band_peak=None):
     """Roofline of the dominant kernel class over its average CUDA-event launch
     duration (timed on the launching stream).  The large-prime walk has two
     bounds: the integer issue rate (thread instructions per sieve, from stored
-    ncu counters, against cs_issue_rate) and the scattered bit clears (its
-    stored hits, F_large, counted live, against cs_atomic_rate over a region of
-    the bitset's size).  The bound that needs more time binds; achieved, peak
-    and frac are given in its units, the other bound beside it."""
+    ncu counters, against cs_issue_rate) and its memory side.  With direct
+    clears that is the scattered bit clears (its stored hits, F_large, counted
+    live, against cs_atomic_rate over a region of the bitset's size); with hit
+    buckets it is the 4-byte records it writes (against the measured HBM copy
+    rate), and the apply kernel that clears them gets its own entry (records
+    counted live, against cs_atomic_rate over a region of two bands).  The
+    bound that needs more time binds; achieved, peak and frac are given in its
+    units, the other bound beside it."""
     name = KC_NAMES[dom]
     n_launch = max(kern_n[dom], 1)
     per_launch_s = kern_ms[dom] / n_launch / 1e3
@@ -465,25 +477,45 @@ def roofline(dom, kern_ms, kern_n, stats, info, params, peaks, peak_src, issue, 
                    "min_ms_per_launch": inst_launch / (peak * 1e12) * 1e3, "thread_inst_per_launch": inst_launch}
         if ctr.get("dram_bytes") is not None:
             out["traffic"] = ctr["dram_bytes"] / ctr["launches"]
-    clears_b = None
-    if clears_peak:
+    clears_b = records_b = None
+    if info.hit_buckets:
+        rec_launch = stats["bucket_records"] / n_chunks       # records written by one walk launch
+        hbm = float(peaks["hbm_gbs"]) * 1e9
+        records_b = {"achieved": rec_launch * 4 / per_launch_s / 1e9, "peak": hbm / 1e9, "unit": "GB/s",
+                     "frac": rec_launch * 4 / per_launch_s / hbm, "min_ms_per_launch": rec_launch * 4 / hbm * 1e3,
+                     "records_per_launch": rec_launch}
+        ia = KC_NAMES.index("hit_apply")
+        if kern_n[ia] and band_peak:
+            apply_s = kern_ms[ia] / 1e3 / max(n_launch / n_chunks, 1)     # apply seconds per sieve
+            ach = stats["bucket_records"] / apply_s
+            out["apply"] = {"kernel": "k_apply_buckets", "achieved": ach / 1e9, "peak": band_peak / 1e9,
+                            "unit": "Gclears/s", "frac": ach / band_peak,
+                            "launches_per_sieve": int(info.apply_launches), "ms_per_sieve": apply_s * 1e3,
+                            "peak_source": "measured in this run: cs_atomic_rate over a region of two bands' "
+                                           "words (best of three launches)"}
+    elif clears_peak:
         clears_launch = stats["F_large"] / n_chunks           # stored hits: one bit clear each
         achieved = clears_launch / per_launch_s / 1e9
         clears_b = {"achieved": achieved, "peak": clears_peak / 1e9, "unit": "Gclears/s",
                     "frac": achieved / (clears_peak / 1e9), "min_ms_per_launch": clears_launch / clears_peak * 1e3,
                     "clears_per_launch": clears_launch}
-    out["bounds"] = {"issue": issue_b, "clears": clears_b}
+    out["bounds"] = {"issue": issue_b, "clears": clears_b, "records": records_b}
     out["launches_timed"] = n_launch
     walk_s = kern_ms[dom] / 1e3 / max(n_launch / n_chunks, 1)   # walk seconds per sieve
     out["per_unit_rates"] = {"visited_hits_per_s": stats["hits_all"] / walk_s, "levels_per_s": stats["levels"] / walk_s,
                              "clears_per_s": stats["F_large"] / walk_s}
     binding = None
-    if issue_b and clears_b:
-        binding = "clears" if clears_b["min_ms_per_launch"] >= issue_b["min_ms_per_launch"] else "issue"
-    elif clears_b:
-        binding = "clears"
+    mem_b = clears_b or records_b
+    if issue_b and mem_b:
+        binding = "memory" if mem_b["min_ms_per_launch"] >= issue_b["min_ms_per_launch"] else "issue"
+    elif mem_b:
+        binding = "memory"
     elif issue_b:
         binding = "issue"
+    if binding == "memory" and records_b:
+        binding = "records"
+    elif binding == "memory":
+        binding = "clears"
     if binding == "issue":
         out.update(achieved=issue_b["achieved"], frac=issue_b["frac"])
     elif binding == "clears":
@@ -491,6 +523,9 @@ def roofline(dom, kern_ms, kern_n, stats, info, params, peaks, peak_src, issue, 
                    frac=clears_b["frac"],
                    peak_source="measured in this run: cs_atomic_rate, one-bit 32-bit atomic ANDs at random "
                                "words of a region the size of the bitset (best of three launches)")
+    elif binding == "records":
+        out.update(bound="hbm", achieved=records_b["achieved"], peak=records_b["peak"], unit="GB/s",
+                   frac=records_b["frac"], peak_source=f"hbm_gbs, {peak_src}")
     if not issue_b:
         out["note"] = "ncu instruction counts not recorded for these sources and this threshold / tile height"
     return out

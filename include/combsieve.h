@@ -101,7 +101,18 @@ typedef struct {
     uint32_t class_item_hits;/* m_classes = 0: expected hits of one class of m mod Q (Q = 210
                                 or 30) per prime from which a chunk walks class items mod Q;
                                 0 = automatic (64) */
-    uint32_t reserved[2];
+    uint32_t hit_buckets;    /* three-gap walk's stored hits: 1 = cleared directly, one atomic AND
+                                each; 2 = written as records to the walk CTA's region for their
+                                band of rows (a slot taken with a shared-memory atomic, one plain
+                                store) and cleared band after band by an apply kernel, each band's
+                                words staying in L2 meanwhile (a region that is full clears
+                                directly); 0 = automatic (2 when the bitset is at least 256 MiB) */
+    uint32_t band_rows_log;  /* hit buckets: rows per band = 2^band_rows_log (at most 2^20);
+                                0 = automatic (bands of at most a fifth of L2, at most 4096
+                                bands) */
+    uint64_t bucket_records; /* hit buckets: records per (CTA, band) region, rounded up to a
+                                multiple of 4; 0 = automatic (up to 8 GiB of regions, twice the
+                                bitset at most) */
 } cs_tuning;
 
 typedef struct {
@@ -132,6 +143,10 @@ typedef struct {
     uint32_t item_mod;         /* finest Q of the chunks that walk class items (0: none) */
     uint32_t item_classes;     /* classes of m mod item_mod they walk (phi(item_mod)) */
     uint64_t item_chunks;      /* large-prime chunks that walk class items */
+    uint32_t hit_buckets;      /* 1 = the walk's stored hits go through per-band regions */
+    uint32_t n_bands;          /* bands of rows (hit buckets) */
+    uint64_t bucket_bytes;     /* device memory of the regions and their counts */
+    uint64_t apply_launches;   /* bucket applications per sieve (one per group of chunks) */
 } cs_info_t;
 
 typedef struct {
@@ -146,6 +161,8 @@ typedef struct {
     uint64_t n_large_primes;
     uint64_t survivors;        /* set bits in the bitset */
     uint64_t hash;
+    uint64_t bucket_records;   /* hit buckets: stored hits cleared through records (the rest of
+                                  F_large, if any, found their region full and cleared directly) */
 } cs_stats_t;
 
 /* Builds a sieve instance: validates the parameters, computes the row and
@@ -200,9 +217,9 @@ const void *cs_device_bitset(cs_plan_t plan);
 
 /* Kernel timings of the last cs_sieve (profile = 1 only), in milliseconds,
  * per kernel class: [0] small-prime generation, [1] tile sieve, [2] large-prime
- * generation, [3] large-prime walk, [4] counts/checksum; launches[i] = launches
- * of that class.  Waits. */
-cs_status cs_kernel_times(cs_plan_t plan, double ms[5], uint64_t launches[5]);
+ * generation, [3] large-prime walk, [4] counts/checksum, [5] application of the
+ * walk's bucketed hits; launches[i] = launches of that class.  Waits. */
+cs_status cs_kernel_times(cs_plan_t plan, double ms[6], uint64_t launches[6]);
 
 /* Frees the plan and its device memory (waits for its work first).  The memory
  * goes back to the library's pool, which keeps up to 1 GiB of it for later
@@ -225,7 +242,8 @@ const char *cs_last_error(void);
  * *out receives a complete tuning (large_mode = 2).  Validation errors as for
  * cs_plan.  Tuning fields left at 0 in any plan may also be set from the
  * environment: CS_THRESHOLD, CS_TILE_ROWS, CS_LARGE_MODE, CS_LARGE_GRID, CS_M_CLASSES,
- * CS_ITEM_HITS, CS_CLASS_MIN_HITS, CS_CLASS_ITEM_HITS, CS_CHUNK_NUMBERS. */
+ * CS_ITEM_HITS, CS_CLASS_MIN_HITS, CS_CLASS_ITEM_HITS, CS_CHUNK_NUMBERS, CS_HIT_BUCKETS,
+ * CS_BAND_ROWS_LOG, CS_BUCKET_RECORDS. */
 cs_status cs_autotune(uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc, uint32_t SL, uint64_t L,
                       const char *cache_path, cs_tuning *out);
 

@@ -81,7 +81,7 @@ uint64_t prime_count_bound(uint64_t x) {
     return (uint64_t)(1.25506 * (double)x / log((double)x)) + 1024;
 }
 
-enum KernelClass { KC_GEN_SMALL = 0, KC_TILE, KC_GEN_LARGE, KC_LARGE, KC_FINAL, KC_N };
+enum KernelClass { KC_GEN_SMALL = 0, KC_TILE, KC_GEN_LARGE, KC_LARGE, KC_FINAL, KC_APPLY, KC_N };
 
 // Device memory of plain plans: a library-owned stream-ordered pool per device
 // that keeps up to POOL_KEEP bytes of freed plan memory for the next plan
@@ -154,6 +154,8 @@ struct cs_plan_s {
     uint32_t item_mod = 0, item_classes = 0;              // finest class items walked
     uint64_t item_chunks = 0;                             // chunks that walk class items
     uint64_t large_cap = 0, small_cap = 0, est_cost = 0;
+    std::vector<uint8_t> apply_after;                     // bucketed hits: apply after this chunk's walk
+    uint64_t apply_launches = 0, bucket_bytes = 0;
     int large_grid = 0;
     uint64_t h2d = 0, dev_bytes = 0;
     // device
@@ -193,7 +195,7 @@ struct cs_plan_s {
     std::vector<size_t> cache_idx;
     // profiling
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[KC_N];
-    size_t prof_used[KC_N] = {0, 0, 0, 0, 0};
+    size_t prof_used[KC_N] = {0, 0, 0, 0, 0, 0};
 
     ~cs_plan_s() {
         // a plan that failed while being built: its allocations and upload are
@@ -313,6 +315,9 @@ void env_tuning(cs_tuning &t) {
     if (!t.class_min_hits) t.class_min_hits = (uint32_t)get("CS_CLASS_MIN_HITS");
     if (!t.class_item_hits) t.class_item_hits = (uint32_t)get("CS_CLASS_ITEM_HITS");
     if (!t.chunk_numbers) t.chunk_numbers = get("CS_CHUNK_NUMBERS");
+    if (!t.hit_buckets) t.hit_buckets = (uint32_t)get("CS_HIT_BUCKETS");
+    if (!t.band_rows_log) t.band_rows_log = (uint32_t)get("CS_BAND_ROWS_LOG");
+    if (!t.bucket_records) t.bucket_records = get("CS_BUCKET_RECORDS");
 }
 
 cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc,
@@ -617,6 +622,73 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
 
     // device memory and tables
     DevPlan &dp = pl->dp;
+
+    // the walk's stored hits through per-band regions, for bitsets of 256 MiB
+    // and more (twice L2): a scattered atomic AND per hit costs a DRAM sector
+    // read and written back (about 100 bytes) once the bitset no longer fits in
+    // L2, while a record costs 4 bytes written and read and is cleared band
+    // after band with the band's words in L2 (4.77 GB bitset: 12% less time per
+    // sieve).  Smaller bitsets stay in L2 and clear directly.
+    dp.bucket = 0;
+    {
+        const uint64_t bitset_bytes = M_c * wpr * 8;
+        const uint32_t hb = pl->tune.hit_buckets;
+        if (hb > 2) return fail(CS_EINVAL, "hit_buckets must be 0, 1 or 2");
+        if (pl->tune.band_rows_log > 20) return fail(CS_EINVAL, "band_rows_log must be at most 20");
+        bool on = hb == 2 || (hb == 0 && bitset_bytes >= (256ull << 20));
+        on = on && pl->mode == LARGE_THREE_GAP && !pl->chunks.empty() && M_c > 0 && wpr > 0;
+        uint32_t bl = pl->tune.band_rows_log;
+        if (on && !bl) {
+            // bands of at most a fifth of L2 (and no more rows than the bitset),
+            // then at most BKT_MAX_BANDS: the apply keeps about 1.3 bands in
+            // work, and larger bands let the records push them out of L2
+            // (4.77 GB bitset, GB300: 17 MB bands best, 34 MB 1.5x slower apply)
+            const uint64_t band_max = l2_bytes() / 5;
+            while ((2ull << bl) * wpr * 8 <= band_max && (2ull << bl) <= M_c) bl++;
+            while (((M_c + (1ull << bl) - 1) >> bl) > BKT_MAX_BANDS) bl++;
+        }
+        const bool fits = ((64ull * wpr) << bl) <= (1ull << 32);   // a record: (row in band) * 64 wpr + column
+        const uint64_t n_bands = (M_c + (1ull << bl) - 1) >> bl;
+        if (on && pl->tune.band_rows_log && (!fits || n_bands > BKT_MAX_BANDS))
+            return fail(CS_EINVAL, "band_rows_log gives records above 32 bits or more than 4096 bands");
+        on = on && fits && n_bands <= BKT_MAX_BANDS;
+        if (on) {
+            // a region per band for every CTA of the walk's grid (three per SM)
+            const uint64_t n_regions = (uint64_t)sm_count() * 3;
+            uint64_t cap = pl->tune.bucket_records;
+            if (!cap) {
+                const uint64_t budget =
+                    std::min<uint64_t>(8ull << 30, std::max<uint64_t>(64ull << 20, 2 * bitset_bytes));
+                cap = budget / 4 / (n_bands * n_regions);
+            }
+            // a multiple of 4, so that every region starts on a 16-byte boundary
+            cap = std::min<uint64_t>(std::max<uint64_t>((cap + 3) / 4 * 4, 4), 1ull << 24);
+            dp.bucket = 1;
+            dp.band_log = bl;
+            dp.n_bands = (uint32_t)n_bands;
+            dp.n_regions = (uint32_t)n_regions;
+            dp.region_cap = (uint32_t)cap;
+            // groups of chunks whose expected stored hits, M_c W sum 1/p over their
+            // primes (Mertens: log log hi - log log lo), fill at most 60% of the
+            // regions; a group's records are applied after its last walk
+            const size_t n_chunks = pl->chunks.size();
+            pl->apply_after.assign(n_chunks, 0);
+            const double room = 0.6 * (double)cap * (double)n_regions * (double)n_bands;
+            double acc = 0;
+            for (size_t c = 0; c < n_chunks; c++) {
+                const double lo = std::max<double>((double)pl->chunks[c].first, 3.0);
+                const double hi = std::max<double>((double)pl->chunks[c].second, lo);
+                const double e = (double)M_c * (double)W * std::log(std::log(hi) / std::log(lo));
+                if (c > 0 && acc > 0 && acc + e > room) {
+                    pl->apply_after[c - 1] = 1;
+                    acc = 0;
+                }
+                acc += e;
+            }
+            pl->apply_after[n_chunks - 1] = 1;
+            for (uint8_t f : pl->apply_after) pl->apply_launches += f;
+        }
+    }
     dp.M_start = M_start; dp.M_inc = M_inc; dp.M_c = M_c;
     dp.SL = SL; dp.S = (uint32_t)S; dp.S32 = (uint32_t)S32;
     dp.W = (uint32_t)W; dp.wpr = (uint32_t)wpr;
@@ -666,6 +738,13 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
     if ((s = pl->dalloc(&d_cnt, M_c))) return s;
     if ((s = pl->dalloc(&d_stats, ST_COUNT))) return s;
     dp.bits = d_bits; dp.counts = d_cnt; dp.stats = d_stats;
+    if (dp.bucket) {
+        const uint64_t before = pl->dev_bytes;
+        const uint64_t n_reg = (uint64_t)dp.n_bands * dp.n_regions;
+        if ((s = pl->dalloc(&dp.bkt, n_reg * dp.region_cap))) return s;
+        if ((s = pl->dalloc(&dp.bkt_cnt, n_reg + 1))) return s;   // + the apply's region counter
+        pl->bucket_bytes = pl->dev_bytes - before;
+    }
 
     // base primes (odd) <= sqrt(L) for the segmented generator
     std::vector<uint32_t> base;
@@ -790,6 +869,8 @@ cs_status plan_sieve_head(cs_plan_t pl, cudaStream_t st) {
     for (int k = 0; k < KC_N; k++) pl->prof_used[k] = 0;
     CS_CUDA(cudaMemsetAsync(dp.stats, 0, ST_COUNT * sizeof(unsigned long long), st));
     CS_CUDA(cudaMemsetAsync(pl->d_counts, 0, (1 + pl->chunks.size()) * sizeof(unsigned long long), st));
+    if (dp.bucket)
+        CS_CUDA(cudaMemsetAsync(dp.bkt_cnt, 0, ((size_t)dp.n_bands * dp.n_regions + 1) * sizeof(uint32_t), st));
     cs_status s;
     if (pl->small_hi > pl->P) {
         if ((s = prof.begin(KC_GEN_SMALL))) return s;
@@ -856,6 +937,14 @@ cs_status cs_sieve(cs_plan_t pl, void *stream) {
     cs_status s;
     if ((s = cs::plan_sieve_head(pl, st))) return s;
     Prof prof{pl, st, pl->tune.profile != 0};
+    // bucketed hits: the records of a group of chunks are cleared after its last walk
+    auto apply = [&](size_t c) -> cs_status {
+        if (!dp.bucket || !pl->apply_after[c]) return CS_OK;
+        cs_status r;
+        if ((r = prof.begin(KC_APPLY))) return r;
+        CS_CUDA(launch_apply_buckets(dp, st));
+        return prof.end();
+    };
     cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
     CS_CUDA(cudaStreamIsCapturing(st, &capst));
     if (pl->cache) {
@@ -870,6 +959,7 @@ cs_status cs_sieve(cs_plan_t pl, void *stream) {
             CS_CUDA(launch_large(dp, ch.narrow, pl->mode, ch.p, ch.r, nullptr, ch.count, ch.cap,
                                  pl->chunk_seg[c], pl->large_grid, st, pl->T, pl->L, pl->chunk_mc[c]));
             if ((s = prof.end())) return s;
+            if ((s = apply(c))) return s;
         }
     }
     for (size_t c = 0; c < pl->chunks.size() && !pl->cache; c++) {
@@ -887,6 +977,7 @@ cs_status cs_sieve(cs_plan_t pl, void *stream) {
                              pl->large_cap, pl->chunk_seg[c], pl->large_grid, st, 0, ~0ull,
                              pl->chunk_mc[c]));
         if ((s = prof.end())) return s;
+        if ((s = apply(c))) return s;
     }
     return cs::plan_sieve_tail(pl, st);
 }
@@ -929,7 +1020,7 @@ cs_status cs_info(cs_plan_t pl, cs_info_t *out) {
     for (const auto &ch : pl->chunks)
         large_launches += pl->cache ? 1 : (pl->narrow || ch.second < NARROW_LIMIT) ? 2 : 3;
     out->launches_per_sieve = (pl->small_hi > pl->P ? 1 : 0) + (pl->M_c && pl->W ? 1 : 0) +
-                              (pl->M_c ? 1 : 0) + large_launches;
+                              (pl->M_c ? 1 : 0) + large_launches + (pl->dp.bucket ? pl->apply_launches : 0);
     out->h2d_bytes = pl->h2d;
     out->device_bytes = pl->dev_bytes;
     out->est_cost = pl->est_cost;
@@ -941,6 +1032,10 @@ cs_status cs_info(cs_plan_t pl, cs_info_t *out) {
     out->item_mod = pl->item_mod;
     out->item_classes = pl->item_classes;
     out->item_chunks = pl->item_chunks;
+    out->hit_buckets = pl->dp.bucket ? 1 : 0;
+    out->n_bands = pl->dp.bucket ? pl->dp.n_bands : 0;
+    out->bucket_bytes = pl->bucket_bytes;
+    out->apply_launches = pl->dp.bucket ? pl->apply_launches : 0;
     if (pl->layout == 1) out->W = pl->Wc_max;
     return CS_OK;
 }
@@ -1011,6 +1106,7 @@ cs_status cs_stats(cs_plan_t pl, cs_stats_t *out) {
     for (auto c : lc) out->n_large_primes += c;
     out->survivors = st[ST_SURVIVORS];
     out->hash = st[ST_HASH];
+    out->bucket_records = st[ST_RECORDS];
     return CS_OK;
 }
 
@@ -1048,7 +1144,7 @@ cs_status cs_row_columns(cs_plan_t pl, uint64_t row, int64_t *x_of_col, size_t n
 
 const void *cs_device_bitset(cs_plan_t pl) { return pl ? (const void *)pl->dp.bits : nullptr; }
 
-cs_status cs_kernel_times(cs_plan_t pl, double ms[5], uint64_t launches[5]) {
+cs_status cs_kernel_times(cs_plan_t pl, double ms[6], uint64_t launches[6]) {
     if (!pl || !ms || !launches) return fail(CS_EINVAL, "NULL argument");
     if (!pl->tune.profile) return fail(CS_ESTATE, "plan was built without profile = 1");
     cs_status s = wait_plan(pl);

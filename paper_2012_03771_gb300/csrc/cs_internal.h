@@ -24,6 +24,7 @@ enum Stat {
     ST_HASH,            // bitset checksum (sum of mix64 terms, mod 2^64)
     ST_ERROR,           // bit flags, see Err
     ST_SURVIVORS,       // total survivors (sum of per-row counts)
+    ST_RECORDS,         // bucketed hit records cleared by the apply kernel
     ST_COUNT = 16
 };
 
@@ -37,6 +38,9 @@ struct SmallPrime {
 };
 
 // everything a kernel needs about one sieve instance (device pointers)
+// most bands of rows for bucketed hits: 16 KB of per-band counters in a walking CTA
+constexpr uint32_t BKT_MAX_BANDS = 4096;
+
 struct DevPlan {
     uint64_t M_start, M_inc, M_c;
     uint32_t SL, S, S32;          // S = 2 SL + 1 raw offsets, S32 = ceil(S/32) raw words
@@ -75,6 +79,16 @@ struct DevPlan {
     const uint32_t *cW;           // n_cls: columns of the class
     const uint32_t *cls_word;     // ceil(M_inc/32): class of the first row at or after m = M_start + 32 w
     uint32_t Wc_max;
+    // bucketed hits (bitsets larger than L2): a stored hit of the walk is written
+    // as a record to the walking CTA's region for its band of rows, and
+    // k_apply_buckets clears the records band after band; regions are band-major
+    int bucket;                   // 1: the three-gap walk buckets its stored hits
+    uint32_t band_log;            // rows per band = 2^band_log
+    uint32_t n_bands;             // at most BKT_MAX_BANDS (a walking CTA counts its regions in shared memory)
+    uint32_t n_regions;           // regions per band (walk CTAs; the walk grid is at most this)
+    uint32_t region_cap;          // records per region; hits beyond it are cleared directly
+    uint32_t *bkt;                // n_bands x n_regions x region_cap records: (row in band) * 64 wpr + column
+    uint32_t *bkt_cnt;            // n_bands x n_regions: records in each region, then the apply's region counter
     // outputs
     uint64_t *bits;               // M_c * wpr words
     uint32_t *counts;             // M_c
@@ -145,6 +159,9 @@ cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p
                          uint32_t n_seg, int grid, cudaStream_t stream, uint64_t p_lo = 0,
                          uint64_t p_hi = ~0ull, MClasses mc = EVERY_M);
 cudaError_t launch_final(const DevPlan &pl, cudaStream_t stream);
+// Clears the bucketed hits of the walk launches since the last application,
+// band after band, and empties the regions.
+cudaError_t launch_apply_buckets(const DevPlan &pl, cudaStream_t stream);
 
 // One chunk's three-gap walk as a job of a persistent multi-job launch (the
 // arguments launch_large takes, primes from a residue-cache chunk).
@@ -178,6 +195,7 @@ cudaError_t launch_modsolve(const uint64_t *p, const uint64_t *K, const uint64_t
                             cudaStream_t stream);
 
 int sm_count();
+uint64_t l2_bytes();   // L2 size of the current device
 
 // ---- residue cache (cs_cache.cu) ----
 // Primes and K mod p for one K = P#/d, on a fixed grid of chunks of (0, L_max]:

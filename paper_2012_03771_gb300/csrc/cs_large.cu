@@ -92,9 +92,12 @@ __device__ __forceinline__ HitView hit_view(const DevPlan &p) {
                    p.cls_word, p.cmask, p.cprefix, p.n_cls, p.S32};
 }
 
-template <class UT, class PV = DevPlan>
+// BKT: the stored hit becomes a record in this CTA's region for its band of
+// rows (slot from the CTA's per-band counter bkt_s in shared memory, one plain
+// store); a full region clears directly.
+template <class UT, class PV = DevPlan, bool BKT = false>
 __device__ __forceinline__ void record_hit_z(const PV &pl, uint64_t moff, uint32_t z, const UT *Pp,
-                                             uint32_t idx, Counters &c) {
+                                             uint32_t idx, Counters &c, uint32_t *bkt_s = nullptr) {
     const uint32_t ms = (uint32_t)moff;                  // bit of m in its 32-m word: ms mod 32
     const uint2 rt = __ldg(&pl.row_tab[moff >> 5]);      // {coprime-m mask, rows before}
     const uint2 ct = __ldg(&pl.col_tab[z >> 5]);         // {stored-x mask, columns before}
@@ -117,9 +120,21 @@ __device__ __forceinline__ void record_hit_z(const PV &pl, uint64_t moff, uint32
         store = bit_of(ccw, z) != 0;
     }
     // 32-bit view of the row's words: column col is bit (col mod 32) of word col >> 5
-    if (store)
-        atomicAnd(reinterpret_cast<unsigned int *>(pl.bits) + (uint64_t)row * (2 * pl.wpr) + (col >> 5),
-                  ~bit_at(col));
+    if (store) {
+        bool direct = true;
+        if constexpr (BKT) {
+            const uint32_t band = row >> pl.band_log;
+            const uint32_t slot = atomicAdd(bkt_s + band, 1u);
+            if (slot < pl.region_cap) {
+                pl.bkt[((uint64_t)band * pl.n_regions + blockIdx.x) * pl.region_cap + slot] =
+                    (row & ((1u << pl.band_log) - 1)) * (64 * pl.wpr) + col;
+                direct = false;
+            }
+        }
+        if (direct)
+            atomicAnd(reinterpret_cast<unsigned int *>(pl.bits) + (uint64_t)row * (2 * pl.wpr) + (col >> 5),
+                      ~bit_at(col));
+    }
     c.F += ok;
 }
 template <class UT>
@@ -270,9 +285,9 @@ __device__ __forceinline__ uint64_t mul_add_mod(uint64_t v, uint64_t r, uint32_t
 // and walked by its lanes until the share is done and the queue is empty;
 // then the warp's counters go to the plan's statistics.  item_off: the class
 // residues of class items (shared memory).
-template <class UT, class ST, class MT, int NC, bool CI, bool JOBS = false>
+template <class UT, class ST, class MT, int NC, bool CI, bool JOBS = false, bool BKT = false>
 __device__ __forceinline__ void walk_warp(const LargeArgs &a, TGItem<MT> *q, const uint8_t *item_off,
-                                          uint64_t first, uint64_t n_warps) {
+                                          uint64_t first, uint64_t n_warps, uint32_t *bkt_s = nullptr) {
     static_assert(!CI || NC == 1, "class items walk one class per item");
     constexpr int QCAP = 32 * (NC + 1);   // a refill adds at most 32 NC walkers
     const uint32_t n_cls_items = CI ? a.mc.items : 1;
@@ -503,7 +518,7 @@ __device__ __forceinline__ void walk_warp(const LargeArgs &a, TGItem<MT> *q, con
             if constexpr (JOBS)
                 record_hit_z<UT>(hv, (uint64_t)moff, z, Pp, idx, c);
             else
-                record_hit_z<UT>(pl, (uint64_t)moff, z, Pp, idx, c);
+                record_hit_z<UT, DevPlan, BKT>(pl, (uint64_t)moff, z, Pp, idx, c, bkt_s);
             const bool down = z <= wmda;
             const bool up = z >= ub;
             z += down ? da : (up ? nub : dmu);
@@ -527,31 +542,88 @@ __device__ __forceinline__ void walk_warp(const LargeArgs &a, TGItem<MT> *q, con
     }
 }
 
-template <class UT, class ST, class MT, int NC, bool CI = false>
+template <class UT, class ST, class MT, int NC, bool CI = false, bool BKT = false>
 __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLOCKS : CS_TG_MIN_BLOCKS_WIDE) k_large_tg(const LargeArgs a) {
     constexpr int QCAP = 32 * (NC + 1);
     __shared__ TGItem<MT> queue[TG_WARPS][QCAP];
     __shared__ uint8_t item_off[CI ? MAX_CLASS_ITEMS : 1];   // class items: residue of each class
+    extern __shared__ uint32_t bkt_s[];                      // BKT: records in this CTA's region per band
+    const DevPlan &pl = a.pl;
     if constexpr (CI) {
         if (threadIdx.x == 0) {
 #pragma unroll
             for (uint32_t k = 0; k < MAX_CLASS_ITEMS; k++) item_off[k] = a.mc.item_off[k];
         }
-        __syncthreads();
     }
-    walk_warp<UT, ST, MT, NC, CI>(a, queue[threadIdx.x >> 5], item_off,
-                                  (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5,
-                                  ((uint64_t)gridDim.x * blockDim.x) >> 5);
+    if constexpr (BKT)
+        for (uint32_t b = threadIdx.x; b < pl.n_bands; b += LARGE_THREADS)
+            bkt_s[b] = pl.bkt_cnt[(uint64_t)b * pl.n_regions + blockIdx.x];
+    if constexpr (CI || BKT) __syncthreads();
+    walk_warp<UT, ST, MT, NC, CI, false, BKT>(a, queue[threadIdx.x >> 5], item_off,
+                                              (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5,
+                                              ((uint64_t)gridDim.x * blockDim.x) >> 5, bkt_s);
+    if constexpr (BKT) {
+        // the region counts for the next launch (slots past the region's end were cleared directly)
+        __syncthreads();
+        for (uint32_t b = threadIdx.x; b < pl.n_bands; b += LARGE_THREADS)
+            pl.bkt_cnt[(uint64_t)b * pl.n_regions + blockIdx.x] = min(bkt_s[b], pl.region_cap);
+    }
 }
 
-// The walks of many chunks, of many plans, in one persistent launch: the
-// batches of all jobs, in job order, are dealt round-robin to the warps (each
-// job continues where the previous one stopped, so that the many small jobs do
-// not all fall on the first warps), and every warp walks its batches of job 0,
-// then of job 1, and so on, without waiting for the other warps between jobs
-// (a launch per chunk would wait for its slowest warp each time).  The jobs'
-// descriptors are in device memory; each warp copies the current one into
-// shared memory.
+// Clears the bucketed records: each CTA takes whole regions one at a time from
+// a shared counter (bkt_cnt[n_bands * n_regions]) in band-major order, so that
+// the regions in work at one time belong to one or two consecutive bands,
+// whose words stay in L2 while their clears land (a fixed stride instead lets
+// the CTAs with small regions run ahead into later bands; a warp per region
+// keeps about ten bands in work, which with bands above 4 MB no longer fit).
+// The records are read once, with loads marked evict-first so that they do
+// not push the bands' words out of L2.  Regions start on 16-byte boundaries
+// (region_cap is a multiple of 4): each thread loads two 16-byte groups of
+// records before their eight clears.
+constexpr int APPLY_THREADS = 256;
+__global__ void __launch_bounds__(APPLY_THREADS) k_apply_buckets(const DevPlan pl) {
+    uint32_t *bits = reinterpret_cast<uint32_t *>(pl.bits);
+    const uint32_t n_reg = pl.n_bands * pl.n_regions;
+    const uint64_t band_words = (uint64_t)(2 * pl.wpr) << pl.band_log;
+    __shared__ uint32_t q_s;
+    for (;;) {
+        __syncthreads();                                 // every thread has read the last q_s
+        if (threadIdx.x == 0) q_s = atomicAdd(pl.bkt_cnt + n_reg, 1u);
+        __syncthreads();
+        const uint32_t q = q_s;
+        if (q >= n_reg) break;
+        const uint32_t n = min(pl.bkt_cnt[q], pl.region_cap);
+        if (threadIdx.x == 0 && n) atomicAdd(pl.stats + ST_RECORDS, (unsigned long long)n);
+        const uint32_t *src = pl.bkt + (uint64_t)q * pl.region_cap;
+        const uint4 *src4 = reinterpret_cast<const uint4 *>(src);
+        uint32_t *dst = bits + (q / pl.n_regions) * band_words;
+        const uint32_t n4 = n / 4;
+        uint32_t i = threadIdx.x;
+        for (; i + APPLY_THREADS < n4; i += 2 * APPLY_THREADS) {
+            const uint4 a = __ldcs(src4 + i), b = __ldcs(src4 + i + APPLY_THREADS);
+            atomicAnd(dst + (a.x >> 5), ~bit_at(a.x));
+            atomicAnd(dst + (a.y >> 5), ~bit_at(a.y));
+            atomicAnd(dst + (a.z >> 5), ~bit_at(a.z));
+            atomicAnd(dst + (a.w >> 5), ~bit_at(a.w));
+            atomicAnd(dst + (b.x >> 5), ~bit_at(b.x));
+            atomicAnd(dst + (b.y >> 5), ~bit_at(b.y));
+            atomicAnd(dst + (b.z >> 5), ~bit_at(b.z));
+            atomicAnd(dst + (b.w >> 5), ~bit_at(b.w));
+        }
+        if (i < n4) {
+            const uint4 a = __ldcs(src4 + i);
+            atomicAnd(dst + (a.x >> 5), ~bit_at(a.x));
+            atomicAnd(dst + (a.y >> 5), ~bit_at(a.y));
+            atomicAnd(dst + (a.z >> 5), ~bit_at(a.z));
+            atomicAnd(dst + (a.w >> 5), ~bit_at(a.w));
+        }
+        for (uint32_t k = 4 * n4 + threadIdx.x; k < n; k += APPLY_THREADS) {
+            const uint32_t r = __ldcs(src + k);
+            atomicAnd(dst + (r >> 5), ~bit_at(r));
+        }
+    }
+}
+
 // resident CTAs per SM the multi-job walk is compiled for: its hit path keeps
 // the plan's fields in registers, which at three CTAs per SM would spill
 #ifndef CS_TG_JOBS_MIN_BLOCKS
@@ -609,15 +681,25 @@ cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p
     // walk kernel: 0 = one walker per item, 1 = two classes per item, 2 = class items
     const int kind = mc.items ? 2 : mc.n == 2 ? 1 : 0;
     LargeArgs a{pl, p, r, v, count, cap, n_seg ? n_seg : 1, p_lo, p_hi, mc};
+    // bucketed hits: three-gap walk only (the paper's walk clears directly)
+    const int bkt = (pl.bucket && mode != LARGE_PAPER) ? 1 : 0;
+    if (!bkt) a.pl.bucket = 0;
+    const size_t dyn = bkt ? (size_t)pl.n_bands * sizeof(uint32_t) : 0;
     void (*walk)(const LargeArgs) = nullptr;
     if (narrow) {
-        walk = kind == 2 ? k_large_tg<uint32_t, int32_t, uint32_t, 1, true>
-             : kind == 1 ? k_large_tg<uint32_t, int32_t, uint32_t, 2>
-                         : k_large_tg<uint32_t, int32_t, uint32_t, 1>;
+        walk = kind == 2 ? (bkt ? k_large_tg<uint32_t, int32_t, uint32_t, 1, true, true>
+                                : k_large_tg<uint32_t, int32_t, uint32_t, 1, true>)
+             : kind == 1 ? (bkt ? k_large_tg<uint32_t, int32_t, uint32_t, 2, false, true>
+                                : k_large_tg<uint32_t, int32_t, uint32_t, 2>)
+                         : (bkt ? k_large_tg<uint32_t, int32_t, uint32_t, 1, false, true>
+                                : k_large_tg<uint32_t, int32_t, uint32_t, 1>);
     } else {
-        walk = kind == 2 ? k_large_tg<uint64_t, int64_t, uint32_t, 1, true>
-             : kind == 1 ? k_large_tg<uint64_t, int64_t, uint32_t, 2>
-                         : k_large_tg<uint64_t, int64_t, uint32_t, 1>;
+        walk = kind == 2 ? (bkt ? k_large_tg<uint64_t, int64_t, uint32_t, 1, true, true>
+                                : k_large_tg<uint64_t, int64_t, uint32_t, 1, true>)
+             : kind == 1 ? (bkt ? k_large_tg<uint64_t, int64_t, uint32_t, 2, false, true>
+                                : k_large_tg<uint64_t, int64_t, uint32_t, 2>)
+                         : (bkt ? k_large_tg<uint64_t, int64_t, uint32_t, 1, false, true>
+                                : k_large_tg<uint64_t, int64_t, uint32_t, 1>);
     }
     // the three-gap walk's lanes are persistent: by default one wave of
     // resident CTAs (a partial last wave left SMs idle: 3% slower measured);
@@ -625,17 +707,22 @@ cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p
     if (grid <= 0) {
         grid = sm_count() * 8;
         if (mode != LARGE_PAPER) {
-            static std::atomic<int> resident[2][3];   // [narrow][kind], looked up once
-            std::atomic<int> &cached = resident[narrow ? 1 : 0][kind];
+            // looked up once per [narrow][kind][bucketed] (the bucket counters,
+            // at most 16 KB, do not change the occupancy bound by registers)
+            static std::atomic<int> resident[2][3][2];
+            std::atomic<int> &cached = resident[narrow ? 1 : 0][kind][bkt];
             int per_sm = cached.load(std::memory_order_relaxed);
             if (per_sm == 0) {
-                cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk, LARGE_THREADS, 0);
+                cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk, LARGE_THREADS,
+                                                                              bkt ? 4 * BKT_MAX_BANDS : 0);
                 if (e != cudaSuccess || per_sm <= 0) per_sm = -1;
                 cached.store(per_sm, std::memory_order_relaxed);
             }
             if (per_sm > 0) grid = sm_count() * per_sm;
         }
     }
+    // every walking CTA owns a region per band
+    if (bkt && (uint32_t)grid > pl.n_regions) grid = (int)pl.n_regions;
     // m - M_start < M_inc < 2^31: 32-bit m offsets in both widths
     if (mode == LARGE_PAPER) {
         if (narrow)
@@ -643,9 +730,20 @@ cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p
         else
             k_large<uint64_t, int64_t><<<grid, LARGE_THREADS, 0, stream>>>(a);
     } else {
-        walk<<<grid, LARGE_THREADS, 0, stream>>>(a);
+        walk<<<grid, LARGE_THREADS, dyn, stream>>>(a);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_apply_buckets(const DevPlan &pl, cudaStream_t stream) {
+    if (!pl.bucket || pl.n_bands == 0) return cudaSuccess;
+    // four CTAs per SM, each on one region at a time: the regions in work span
+    // about 1.3 bands (152 x 3 regions per band)
+    k_apply_buckets<<<sm_count() * 4, APPLY_THREADS, 0, stream>>>(pl);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the region counts and the apply's region counter back to 0
+    return cudaMemsetAsync(pl.bkt_cnt, 0, ((size_t)pl.n_bands * pl.n_regions + 1) * sizeof(uint32_t), stream);
 }
 
 struct WalkJobs {
@@ -671,6 +769,7 @@ cudaError_t walk_jobs_create(const std::vector<WalkJob> &jobs, WalkJobs **out) {
         const int kind = walk_kind(mc, j.pl.SL);
         g[j.narrow ? 1 : 0][kind].push_back(
             LargeArgs{j.pl, j.p, j.r, nullptr, j.count, j.cap, j.n_seg ? j.n_seg : 1, j.p_lo, j.p_hi, mc});
+        g[j.narrow ? 1 : 0][kind].back().pl.bucket = 0;      // the job walks clear directly
     }
     WalkJobs *wj = new (std::nothrow) WalkJobs();
     if (!wj) return cudaErrorMemoryAllocation;

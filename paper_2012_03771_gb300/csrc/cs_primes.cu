@@ -111,7 +111,7 @@ template <int KIND>
 __device__ __forceinline__ void emit(const GenArgs &a, uint64_t p, bool valid, unsigned lane) {
     // residue work for this lane's prime
     uint32_t e0 = 0, e1 = 0, e2 = 0, e3 = 0;
-    uint64_t w0 = 0, w1 = 0, w2 = 0;
+    uint64_t w0 = 0, w1 = 0;
     if (valid) {
         if (KIND == KIND_SMALL) {
             uint32_t p32 = (uint32_t)p;
@@ -482,6 +482,17 @@ int sm_count() {
         if (n <= 0) n = 1;
     }
     return n;
+}
+
+uint64_t l2_bytes() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrL2CacheSize, dev);
+        if (n <= 0) n = 1 << 20;
+    }
+    return (uint64_t)n;
 }
 
 cudaError_t launch_gen_small(const DevPlan &pl, uint64_t lo, uint64_t hi, const uint32_t *base,

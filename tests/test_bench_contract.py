@@ -40,7 +40,8 @@ def test_reference_arm_prints_one_contract_line():
 
 
 def _info(**kw):
-    base = dict(threshold=120003, tile_rows=16, n_large_chunks=17, bitset_bytes=37487120, M_c=22858)
+    base = dict(threshold=120003, tile_rows=16, n_large_chunks=17, bitset_bytes=37487120, M_c=22858,
+                hit_buckets=0, n_bands=0, apply_launches=0, bucket_bytes=0)
     base.update(kw)
     return SimpleNamespace(**base)
 
@@ -82,6 +83,20 @@ def test_roofline_uses_counters_only_for_the_same_sources_and_setup(bench, monke
     monkeypatch.setitem(bench.WALK_COUNTERS, "search_953", dict(ctr, csrc_sha="0" * 16))
     r = bench.roofline(walk, kern_ms, kern_n, stats, _info(), *args)
     assert r["achieved"] is None
+    # hit buckets: the walk's memory side is the records it writes (4 bytes each,
+    # against the HBM copy rate), and the apply kernel gets its own entry
+    monkeypatch.setitem(bench.WALK_COUNTERS, "search_953", ctr)
+    apply = bench.KC_NAMES.index("hit_apply")
+    kb_ms, kb_n = list(kern_ms), list(kern_n)
+    kb_ms[apply], kb_n[apply] = 10 * 1.5, 10 * 2
+    sb = dict(stats, bucket_records=1.7e8)
+    r = bench.roofline(walk, kb_ms, kb_n, sb, _info(hit_buckets=1, n_bands=3, apply_launches=2), *args,
+                       clears_peak=2e10, band_peak=1.5e11)
+    assert r["bounds"]["clears"] is None and r["bounds"]["records"]["unit"] == "GB/s"
+    assert r["bound"] == "alu" and r["unit"] == "Tinst/s"           # 0.68 GB of records per sieve: issue binds
+    want_a = 1.7e8 / 1.5e-3
+    assert abs(r["apply"]["achieved"] - want_a / 1e9) < 1e-6 * want_a / 1e9
+    assert abs(r["apply"]["frac"] - want_a / 1.5e11) < 1e-12 and r["apply"]["unit"] == "Gclears/s"
     # no measured peaks: no fraction (never a derived stand-in)
     monkeypatch.setitem(bench.WALK_COUNTERS, "search_953", ctr)
     r = bench.roofline(walk, kern_ms, kern_n, stats, _info(), None, peaks, "measured", {"error": "x"}, "search_953")

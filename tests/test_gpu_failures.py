@@ -42,10 +42,12 @@ def _same(a, b):
 def test_every_allocation_of_a_plan_build_can_fail_cleanly(monkeypatch):
     """Each device allocation of a plan build, failed in turn, gives CS_ENOMEM
     with its message and no plan; afterwards the same plan builds and sieves
-    to the same result, for a plan of 32-bit and one of 64-bit primes."""
+    to the same result, for a plan of 32-bit primes, one of 64-bit primes and
+    one whose walk buckets its hits (more allocations)."""
     for prm, tuning in ((workloads.PLAIN_503, {}),
                         (workloads.SieveParams(P=503, d=2310, M_start=10**6, M_inc=3000, SL=3000, L=3 * 10**9),
-                         {"item_hits": 32})):
+                         {"item_hits": 32}),
+                        (workloads.PLAIN_503, {"hit_buckets": 2})):
         ref = _alone(prm, **tuning)
         tune = cs.make_tuning(**tuning) if tuning else None
         k = 0

@@ -189,6 +189,69 @@ def test_class_items_with_segments_bit_exact(d):
         assert np.array_equal(mixed["bits"], got["bits"]) and mixed["F"] == got["F"]
 
 
+@pytest.mark.parametrize("band_rows_log, bucket_records", [(1, 0), (3, 16), (2, 1), (0, 0)])
+def test_bucketed_hits_bit_exact(band_rows_log, bucket_records):
+    """The walk's stored hits written as records to the walking CTA's region for
+    their band of rows and cleared band after band give the oracle's bitset:
+    with many small bands, with regions so small that most hits clear directly
+    (1 or 16 records per region), with automatic bands, in the
+    literal and the compact layout, for 32- and 64-bit primes and on the tiny
+    brute-force cases."""
+    kw = dict(hit_buckets=2, band_rows_log=band_rows_log, bucket_records=bucket_records)
+    for prm in (workloads.PLAIN_503.with_(L=3 * 10**6),
+                workloads.SieveParams(P=37, d=30, M_start=10**6, M_inc=300, SL=400, L=10**5)):
+        args = prm.as_tuple()
+        got = _run(args, threshold=max(2 * prm.SL, 1), **kw)
+        info = got["info"]
+        assert info.hit_buckets == 1 and info.n_bands >= 1 and info.apply_launches >= 1
+        if band_rows_log:
+            assert info.n_bands == -(-len(got["rows"]) // (1 << band_rows_log))
+        assert info.apply_launches <= info.n_large_chunks
+        # every stored hit is a record or (its region full) a direct clear
+        assert 0 < got["stats"]["bucket_records"] <= got["stats"]["F_large"]
+        if bucket_records == 1:
+            assert got["stats"]["bucket_records"] < got["stats"]["F_large"]
+        _check_full(args, got)
+        comp = _bits_only(args, layout=1, **kw)
+        lit = _bits_only(args, layout=1, hit_buckets=1)
+        assert comp["info"].hit_buckets == 1 and lit["info"].hit_buckets == 0
+        assert np.array_equal(comp["bits"], lit["bits"]) and comp["F"] == lit["F"]
+    # 64-bit primes (L above 2^30): the whole bitset against direct clears,
+    # sampled rows against the oracle
+    prm = workloads.SieveParams(P=503, d=2310, M_start=10**6, M_inc=3000, SL=3000, L=3 * 10**9)
+    got = _run(prm.as_tuple(), **kw)
+    ref = _run(prm.as_tuple(), hit_buckets=1)
+    assert got["info"].narrow == 0 and got["info"].hit_buckets == 1 and ref["info"].hit_buckets == 0
+    assert ref["stats"]["bucket_records"] == 0
+    assert np.array_equal(got["bits"], ref["bits"])
+    assert (got["F"], got["hash"]) == (ref["F"], ref["hash"])
+    sample = [0, len(got["rows"]) // 2, len(got["rows"]) - 1]
+    bits, _, _ = O.sieve(prm.P, prm.d, prm.SL, prm.L, [int(got["rows"][i]) for i in sample])
+    for k, i in enumerate(sample):
+        assert np.array_equal(got["bits"][i], bits[k])
+    n = 0
+    for prm in workloads.tiny_cases(150, seed=13):
+        args = prm.as_tuple()
+        if O.validate(*args):
+            continue
+        got = _run(args, large_mode=2, threshold=max(2 * prm.SL, 1), **kw)
+        _check_full(args, got)
+        n += 1
+    assert n > 60
+
+
+def test_bucketed_hits_of_the_search_equal_direct_clears():
+    """search_953 with its hits bucketed (forced; its 37.5 MB bitset clears
+    directly by default) gives the same checksum, F and per-row counts."""
+    prm = workloads.SEARCH_953
+    a = _run(prm.as_tuple(), hit_buckets=2)
+    b = _run(prm.as_tuple())
+    assert a["info"].hit_buckets == 1 and b["info"].hit_buckets == 0
+    assert 0 < a["stats"]["bucket_records"] <= a["stats"]["F_large"]
+    assert (a["F"], a["hash"]) == (b["F"], b["hash"])
+    assert np.array_equal(a["counts"], b["counts"])
+
+
 def test_k1_survivors_are_primes():
     """K = d = 1 and L >= sqrt(N + SL): survivors are the primes (Section 1 gaps)."""
     SL = 199_999

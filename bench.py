@@ -383,15 +383,24 @@ def csrc_sha() -> str:
 
 
 # ncu counters of the large-prime walk, summed over the walk's launches of one
-# sieve of each workload, taken with
+# sieve (the first, the bench's warm-up sieve) of each workload, taken with
+#   ncu --metrics smsp__thread_inst_executed.sum,gpu__time_duration.sum --clock-control none
+#       -k regex:k_large_tg -c 756 --csv python bench.py --steps 1 --warmup 1 --no-cpu
 #   ncu --metrics gpu__time_duration.sum,smsp__thread_inst_executed.sum,dram__bytes_read.sum,
-#       dram__bytes_write.sum --clock-control none -k regex:k_large_tg -s <walk launches of the
-#       warm-up sieve> -c <walk launches of one sieve> --csv python bench.py --config <workload>
-#       --steps 1 --warmup 1 --no-cpu
+#       dram__bytes_write.sum --clock-control none -k regex:k_large_tg -c 17 --csv
+#       python bench.py --config search_953 --steps 1 --warmup 1 --no-cpu
 # The work is deterministic (same inputs, same code), so these are per-sieve
 # constants for the walk sources whose digest is recorded (csrc_sha) and the
 # same threshold, tile height and chunking; otherwise they are not used.
-WALK_COUNTERS = {}
+WALK_COUNTERS = {
+    # one GB300, sources of the walk with hit buckets (large_1019 buckets its hits,
+    # search_953 clears directly); large_1019's DRAM bytes were not captured at
+    # full size (several passes on a 13 GB working set)
+    "large_1019": {"csrc_sha": "4dbc7f665b0758df", "threshold": 100002, "tile_rows": 8, "launches": 756,
+                   "thread_inst": 13183978472484.0, "dram_bytes": None},
+    "search_953": {"csrc_sha": "4dbc7f665b0758df", "threshold": 120003, "tile_rows": 16, "launches": 17,
+                   "thread_inst": 87976364443.0, "dram_bytes": 1243115008.0 + 946688.0},
+}
 
 
 def issue_rates(torch, cs, stream):

@@ -692,7 +692,7 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
     dp.M_start = M_start; dp.M_inc = M_inc; dp.M_c = M_c;
     dp.SL = SL; dp.S = (uint32_t)S; dp.S32 = (uint32_t)S32;
     dp.W = (uint32_t)W; dp.wpr = (uint32_t)wpr;
-    dp.P = P; dp.L = L; dp.T = T;
+    dp.P = P; dp.L = L; dp.T = T; dp.d = d;
     dp.small_n = small_n; dp.K64 = K64;
     cs_status s;
     // the read-only tables go up together (one allocation, one copy)

@@ -46,6 +46,7 @@ struct DevPlan {
     uint32_t SL, S, S32;          // S = 2 SL + 1 raw offsets, S32 = ceil(S/32) raw words
     uint32_t W, wpr;              // stored columns, uint64 words per row
     uint64_t P, L, T;             // primorial bound, sieve limit, small/large threshold
+    uint64_t d;                   // K = P# / d
     int small_n;                  // N + x may equal a sieving prime or a prime of d
     uint64_t K64;                 // K when it fits in 64 bits (small_n only)
     // K's prime factors packed into words: products below 2^31 / 2^64

@@ -95,22 +95,27 @@ __device__ __forceinline__ HitView hit_view(const DevPlan &p) {
 // BKT: the stored hit becomes a record in this CTA's region for its band of
 // rows (slot from the CTA's per-band counter bkt_s in shared memory, one plain
 // store); a full region clears directly.
-template <class UT, class PV = DevPlan, bool BKT = false>
-__device__ __forceinline__ void record_hit_z(const PV &pl, uint64_t moff, uint32_t z, const UT *Pp,
-                                             uint32_t idx, Counters &c, uint32_t *bkt_s = nullptr) {
+// rt = row_tab[moff >> 5] {coprime-m mask, rows before}, ct = col_tab[z >> 5]
+// {stored-x mask, columns before}: loaded by the caller, the walk one step
+// ahead so that the loads are in flight while the previous hit is recorded.
+// ROWS: m is known to be a row, and its row index is row_in (rt unused; the
+// class-item walk with Q = d, literal layout).
+template <class UT, class PV = DevPlan, bool BKT = false, bool ROWS = false>
+__device__ __forceinline__ void record_hit_rc(const PV &pl, uint64_t moff, uint32_t z, uint2 rt, uint2 ct,
+                                              const UT *Pp, uint32_t idx, Counters &c, uint32_t *bkt_s = nullptr,
+                                              uint32_t row_in = 0) {
     const uint32_t ms = (uint32_t)moff;                  // bit of m in its 32-m word: ms mod 32
-    const uint2 rt = __ldg(&pl.row_tab[moff >> 5]);      // {coprime-m mask, rows before}
-    const uint2 ct = __ldg(&pl.col_tab[z >> 5]);         // {stored-x mask, columns before}
-    bool ok = (bit_of(rt.x, ms) & bit_of(ct.x, z)) != 0; // m coprime to d, x coprime to K
+    // m coprime to d, x coprime to K
+    bool ok = ROWS ? bit_of(ct.x, z) != 0 : (bit_of(rt.x, ms) & bit_of(ct.x, z)) != 0;
     if (pl.small_n) {
         unsigned __int128 n = (unsigned __int128)(pl.M_start + moff) * pl.K64 + z - pl.SL;
         ok = ok && n != (unsigned __int128)Pp[idx];      // N + x is p itself
     }
-    const uint32_t row_below = __popc(bits_below(rt.x, ms));
-    const uint32_t row = rt.y + row_below;
+    const uint32_t row_below = ROWS ? 0u : __popc(bits_below(rt.x, ms));
+    const uint32_t row = ROWS ? row_in : rt.y + row_below;
     uint32_t col = ct.y + __popc(bits_below(ct.x, z));
     bool store = ok;                                     // F counts every stored x coprime to K
-    if (pl.compact && ok) {
+    if (!ROWS && pl.compact && ok) {
         // the row's class keeps only x with gcd(N + x, d) = 1; class of the
         // first row of this 32-m word, plus the rows before m in the word
         uint32_t cls = __ldg(&pl.cls_word[moff >> 5]) + row_below;
@@ -136,6 +141,12 @@ __device__ __forceinline__ void record_hit_z(const PV &pl, uint64_t moff, uint32
                       ~bit_at(col));
     }
     c.F += ok;
+}
+template <class UT, class PV = DevPlan, bool BKT = false>
+__device__ __forceinline__ void record_hit_z(const PV &pl, uint64_t moff, uint32_t z, const UT *Pp,
+                                             uint32_t idx, Counters &c, uint32_t *bkt_s = nullptr) {
+    record_hit_rc<UT, PV, BKT>(pl, moff, z, __ldg(&pl.row_tab[moff >> 5]), __ldg(&pl.col_tab[z >> 5]), Pp, idx, c,
+                               bkt_s);
 }
 template <class UT>
 __device__ __forceinline__ void record_hit(const DevPlan &pl, uint64_t moff, UT v, const UT *Pp, uint32_t idx,
@@ -285,7 +296,10 @@ __device__ __forceinline__ uint64_t mul_add_mod(uint64_t v, uint64_t r, uint32_t
 // and walked by its lanes until the share is done and the queue is empty;
 // then the warp's counters go to the plan's statistics.  item_off: the class
 // residues of class items (shared memory).
-template <class UT, class ST, class MT, int NC, bool CI, bool JOBS = false, bool BKT = false>
+// CI: 0 = m-class walkers, 1 = class items, 2 = class items mod Q = d in the
+// literal layout, whose rows follow from the walker's steps: every walked m is
+// a row, and a step of k Q in m passes k phi(Q) rows.
+template <class UT, class ST, class MT, int NC, int CI, bool JOBS = false, bool BKT = false>
 __device__ __forceinline__ void walk_warp(const LargeArgs &a, TGItem<MT> *q, const uint8_t *item_off,
                                           uint64_t first, uint64_t n_warps, uint32_t *bkt_s = nullptr) {
     static_assert(!CI || NC == 1, "class items walk one class per item");
@@ -322,6 +336,12 @@ __device__ __forceinline__ void walk_warp(const LargeArgs &a, TGItem<MT> *q, con
     // z += d_a - u_b
     MT moff = 0, end = 0, ma = 0, mb = 0, mab = 0;
     uint32_t z = 0, idx = 0, da = 0, ub = 0, wmda = 0, nub = 0, dmu = 0;
+    // the current hit's row and column table words (loaded one step ahead)
+    const uint2 *row_tab = JOBS ? hv.row_tab : pl.row_tab;
+    const uint2 *col_tab = JOBS ? hv.col_tab : pl.col_tab;
+    uint2 rt = make_uint2(0, 0), ct = make_uint2(0, 0);
+    constexpr bool ROWS = CI == 2;
+    uint32_t row = 0, ra = 0, rb = 0, rab = 0;   // ROWS: row of the current hit, rows per step
 
     while (true) {
         // refill: prepare 32 items when the queue can take their walkers
@@ -499,6 +519,15 @@ __device__ __forceinline__ void walk_warp(const LargeArgs &a, TGItem<MT> *q, con
                 wmda = (uint32_t)w - da;
                 nub = 0u - ub;
                 dmu = da - ub;                       // both wrap; z ends in [0, 2SL]
+                rt = __ldg(&row_tab[moff >> 5]);
+                ct = __ldg(&col_tab[z >> 5]);
+                if constexpr (ROWS) {
+                    // steps are multiples of Q (a clamped one ends the walker)
+                    row = rt.y + __popc(bits_below(rt.x, (uint32_t)moff));
+                    ra = (uint32_t)ma / Q * n_cls_items;
+                    rb = (uint32_t)mb / Q * n_cls_items;
+                    rab = ra + rb;
+                }
                 active = true;
             }
             qhead = (qhead + take) % QCAP;
@@ -515,16 +544,27 @@ __device__ __forceinline__ void walk_warp(const LargeArgs &a, TGItem<MT> *q, con
         constexpr int STEPS = NC == 1 && !CI ? TG_STEPS_ALL_M : TG_STEPS;
         int u = 0;
         for (; u < STEPS && active; u++) {
-            if constexpr (JOBS)
-                record_hit_z<UT>(hv, (uint64_t)moff, z, Pp, idx, c);
-            else
-                record_hit_z<UT, DevPlan, BKT>(pl, (uint64_t)moff, z, Pp, idx, c, bkt_s);
             const bool down = z <= wmda;
             const bool up = z >= ub;
-            z += down ? da : (up ? nub : dmu);
+            const uint32_t zn = z + (down ? da : (up ? nub : dmu));
             const MT step = down ? ma : (up ? mb : mab);
             active = step < end - moff;
-            moff += step;
+            const MT mn = moff + step;
+            // the next hit's table words, in flight while this one is recorded
+            uint2 rtn = rt, ctn = ct;
+            if (active) {
+                if constexpr (!ROWS) rtn = __ldg(&row_tab[mn >> 5]);
+                ctn = __ldg(&col_tab[zn >> 5]);
+            }
+            if constexpr (JOBS)
+                record_hit_rc<UT>(hv, (uint64_t)moff, z, rt, ct, Pp, idx, c);
+            else
+                record_hit_rc<UT, DevPlan, BKT, ROWS>(pl, (uint64_t)moff, z, rt, ct, Pp, idx, c, bkt_s, row);
+            if constexpr (ROWS) row += down ? ra : (up ? rb : rab);
+            rt = rtn;
+            ct = ctn;
+            z = zn;
+            moff = mn;
         }
         c.hits += u;                                 // one hit per step taken
     }
@@ -542,7 +582,7 @@ __device__ __forceinline__ void walk_warp(const LargeArgs &a, TGItem<MT> *q, con
     }
 }
 
-template <class UT, class ST, class MT, int NC, bool CI = false, bool BKT = false>
+template <class UT, class ST, class MT, int NC, int CI = 0, bool BKT = false>
 __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLOCKS : CS_TG_MIN_BLOCKS_WIDE) k_large_tg(const LargeArgs a) {
     constexpr int QCAP = 32 * (NC + 1);
     __shared__ TGItem<MT> queue[TG_WARPS][QCAP];
@@ -629,7 +669,7 @@ __global__ void __launch_bounds__(APPLY_THREADS) k_apply_buckets(const DevPlan p
 #ifndef CS_TG_JOBS_MIN_BLOCKS
 #define CS_TG_JOBS_MIN_BLOCKS 2
 #endif
-template <class UT, class ST, class MT, int NC, bool CI = false>
+template <class UT, class ST, class MT, int NC, int CI = 0>
 __global__ void __launch_bounds__(LARGE_THREADS, CS_TG_JOBS_MIN_BLOCKS)
     k_large_tg_jobs(const LargeArgs *jobs, uint32_t n_jobs) {
     constexpr int QCAP = 32 * (NC + 1);
@@ -678,8 +718,11 @@ cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p
                          int grid, cudaStream_t stream, uint64_t p_lo, uint64_t p_hi, MClasses mc) {
     const bool items_ok = mc.items == mc.n && mc.n <= MAX_CLASS_ITEMS && mc.Q <= 256;
     if (mc.Q == 0 || mc.n < 1 || mc.n > mc.Q || (mc.items ? !items_ok : mc.n > 2) || pl.SL == 0) mc = EVERY_M;
-    // walk kernel: 0 = one walker per item, 1 = two classes per item, 2 = class items
-    const int kind = mc.items ? 2 : mc.n == 2 ? 1 : 0;
+    // walk kernel: 0 = one walker per item, 1 = two classes per item, 2 = class
+    // items, 3 = class items mod Q = d with rows from the steps (32-bit primes,
+    // literal layout)
+    int kind = mc.items ? 2 : mc.n == 2 ? 1 : 0;
+    if (kind == 2 && narrow && mode != LARGE_PAPER && !pl.compact && mc.Q == pl.d) kind = 3;
     LargeArgs a{pl, p, r, v, count, cap, n_seg ? n_seg : 1, p_lo, p_hi, mc};
     // bucketed hits: three-gap walk only (the paper's walk clears directly)
     const int bkt = (pl.bucket && mode != LARGE_PAPER) ? 1 : 0;
@@ -687,18 +730,20 @@ cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p
     const size_t dyn = bkt ? (size_t)pl.n_bands * sizeof(uint32_t) : 0;
     void (*walk)(const LargeArgs) = nullptr;
     if (narrow) {
-        walk = kind == 2 ? (bkt ? k_large_tg<uint32_t, int32_t, uint32_t, 1, true, true>
-                                : k_large_tg<uint32_t, int32_t, uint32_t, 1, true>)
-             : kind == 1 ? (bkt ? k_large_tg<uint32_t, int32_t, uint32_t, 2, false, true>
+        walk = kind == 3 ? (bkt ? k_large_tg<uint32_t, int32_t, uint32_t, 1, 2, true>
+                                : k_large_tg<uint32_t, int32_t, uint32_t, 1, 2>)
+             : kind == 2 ? (bkt ? k_large_tg<uint32_t, int32_t, uint32_t, 1, 1, true>
+                                : k_large_tg<uint32_t, int32_t, uint32_t, 1, 1>)
+             : kind == 1 ? (bkt ? k_large_tg<uint32_t, int32_t, uint32_t, 2, 0, true>
                                 : k_large_tg<uint32_t, int32_t, uint32_t, 2>)
-                         : (bkt ? k_large_tg<uint32_t, int32_t, uint32_t, 1, false, true>
+                         : (bkt ? k_large_tg<uint32_t, int32_t, uint32_t, 1, 0, true>
                                 : k_large_tg<uint32_t, int32_t, uint32_t, 1>);
     } else {
-        walk = kind == 2 ? (bkt ? k_large_tg<uint64_t, int64_t, uint32_t, 1, true, true>
-                                : k_large_tg<uint64_t, int64_t, uint32_t, 1, true>)
-             : kind == 1 ? (bkt ? k_large_tg<uint64_t, int64_t, uint32_t, 2, false, true>
+        walk = kind == 2 ? (bkt ? k_large_tg<uint64_t, int64_t, uint32_t, 1, 1, true>
+                                : k_large_tg<uint64_t, int64_t, uint32_t, 1, 1>)
+             : kind == 1 ? (bkt ? k_large_tg<uint64_t, int64_t, uint32_t, 2, 0, true>
                                 : k_large_tg<uint64_t, int64_t, uint32_t, 2>)
-                         : (bkt ? k_large_tg<uint64_t, int64_t, uint32_t, 1, false, true>
+                         : (bkt ? k_large_tg<uint64_t, int64_t, uint32_t, 1, 0, true>
                                 : k_large_tg<uint64_t, int64_t, uint32_t, 1>);
     }
     // the three-gap walk's lanes are persistent: by default one wave of
@@ -709,7 +754,7 @@ cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p
         if (mode != LARGE_PAPER) {
             // looked up once per [narrow][kind][bucketed] (the bucket counters,
             // at most 16 KB, do not change the occupancy bound by registers)
-            static std::atomic<int> resident[2][3][2];
+            static std::atomic<int> resident[2][4][2];
             std::atomic<int> &cached = resident[narrow ? 1 : 0][kind][bkt];
             int per_sm = cached.load(std::memory_order_relaxed);
             if (per_sm == 0) {
@@ -795,11 +840,11 @@ cudaError_t walk_jobs_launch(const WalkJobs *wj, cudaStream_t stream) {
             if (!wj->n_jobs[nw][k]) continue;
             void (*kern)(const LargeArgs *, uint32_t);
             if (nw) {
-                kern = k == 2 ? k_large_tg_jobs<uint32_t, int32_t, uint32_t, 1, true>
+                kern = k == 2 ? k_large_tg_jobs<uint32_t, int32_t, uint32_t, 1, 1>
                      : k == 1 ? k_large_tg_jobs<uint32_t, int32_t, uint32_t, 2>
                               : k_large_tg_jobs<uint32_t, int32_t, uint32_t, 1>;
             } else {
-                kern = k == 2 ? k_large_tg_jobs<uint64_t, int64_t, uint32_t, 1, true>
+                kern = k == 2 ? k_large_tg_jobs<uint64_t, int64_t, uint32_t, 1, 1>
                      : k == 1 ? k_large_tg_jobs<uint64_t, int64_t, uint32_t, 2>
                               : k_large_tg_jobs<uint64_t, int64_t, uint32_t, 1>;
             }

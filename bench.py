@@ -36,7 +36,7 @@ def metric_of(params) -> str:
 
 METRIC = "enumerated factors/s at L=1e9 (bit-exact bitset + per-m counts)"
 UNIT = "factors/s"
-KC_NAMES = ["gen_small", "tile_sieve", "gen_large", "large_walk", "final", "hit_apply"]
+KC_NAMES = ["gen_small", "tile_sieve", "gen_large", "large_walk", "final", "hit_apply", "walk_prep"]
 # autotuner results for this GPU, one line per (P, d, SL, ceil(log2 L))
 TUNE_FILE = os.path.join(ROOT, "paper_2012_03771_gb300", "tune_gb300.txt")
 
@@ -197,7 +197,8 @@ def _shape(info, tuned):
             "class_items": (f"{int(info.item_chunks)} chunks, finest {int(info.item_classes)} classes of "
                             f"m mod {int(info.item_mod)}" if info.item_chunks else "none"),
             "hit_buckets": ({"bands": int(info.n_bands), "bucket_bytes": int(info.bucket_bytes),
-                             "apply_launches": int(info.apply_launches)} if info.hit_buckets else None)}
+                             "apply_launches": int(info.apply_launches)} if info.hit_buckets else None),
+            "prepared_walker_chunks": int(info.prep_chunks)}
 
 
 def run_cuda(args, params):
@@ -509,6 +510,13 @@ def roofline(dom, kern_ms, kern_n, stats, info, params, peaks, peak_src, issue, 
                     "frac": achieved / (clears_peak / 1e9), "min_ms_per_launch": clears_launch / clears_peak * 1e3,
                     "clears_per_launch": clears_launch}
     out["bounds"] = {"issue": issue_b, "clears": clears_b, "records": records_b}
+    # the walker preparation of the one-walker chunks (its own kernel, k_tg_prep)
+    ip = KC_NAMES.index("walk_prep")
+    if kern_n[ip] and issue_b and ctr.get("prep_thread_inst") and ctr.get("prep_launches") == int(info.prep_chunks):
+        prep_s = kern_ms[ip] / 1e3 / max(n_launch / n_chunks, 1)       # prep seconds per sieve
+        ach = ctr["prep_thread_inst"] / prep_s / 1e12
+        out["prep"] = {"kernel": "k_tg_prep", "achieved": ach, "peak": peak, "unit": "Tinst/s",
+                       "frac": ach / peak, "ms_per_sieve": prep_s * 1e3, "launches_per_sieve": int(info.prep_chunks)}
     out["launches_timed"] = n_launch
     walk_s = kern_ms[dom] / 1e3 / max(n_launch / n_chunks, 1)   # walk seconds per sieve
     out["per_unit_rates"] = {"visited_hits_per_s": stats["hits_all"] / walk_s, "levels_per_s": stats["levels"] / walk_s,

@@ -113,6 +113,11 @@ typedef struct {
     uint64_t bucket_records; /* hit buckets: records per (CTA, band) region, rounded up to a
                                 multiple of 4; 0 = automatic (up to 8 GiB of regions, twice the
                                 bitset at most) */
+    uint32_t walk_prep;      /* one-walker chunks of the three-gap walk (odd m or every m, one
+                                segment per prime, in a plan without a residue cache): 2 = each
+                                prime's first hit and steps computed by a preparation kernel
+                                into a 24-byte walker descriptor that the walk reads; 1 = the
+                                walk prepares its items itself; 0 = automatic (2) */
 } cs_tuning;
 
 typedef struct {
@@ -147,6 +152,7 @@ typedef struct {
     uint32_t n_bands;          /* bands of rows (hit buckets) */
     uint64_t bucket_bytes;     /* device memory of the regions and their counts */
     uint64_t apply_launches;   /* bucket applications per sieve (one per group of chunks) */
+    uint64_t prep_chunks;      /* large-prime chunks whose walkers a preparation kernel computes */
 } cs_info_t;
 
 typedef struct {
@@ -218,8 +224,9 @@ const void *cs_device_bitset(cs_plan_t plan);
 /* Kernel timings of the last cs_sieve (profile = 1 only), in milliseconds,
  * per kernel class: [0] small-prime generation, [1] tile sieve, [2] large-prime
  * generation, [3] large-prime walk, [4] counts/checksum, [5] application of the
- * walk's bucketed hits; launches[i] = launches of that class.  Waits. */
-cs_status cs_kernel_times(cs_plan_t plan, double ms[6], uint64_t launches[6]);
+ * walk's bucketed hits, [6] walker preparation of the one-walker chunks;
+ * launches[i] = launches of that class.  Waits. */
+cs_status cs_kernel_times(cs_plan_t plan, double ms[7], uint64_t launches[7]);
 
 /* Frees the plan and its device memory (waits for its work first).  The memory
  * goes back to the library's pool, which keeps up to 1 GiB of it for later

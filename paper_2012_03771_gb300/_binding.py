@@ -53,7 +53,8 @@ class cs_tuning(ctypes.Structure):
                 ("profile", ctypes.c_uint32), ("layout", ctypes.c_uint32), ("m_classes", ctypes.c_uint32),
                 ("item_hits", ctypes.c_uint32), ("class_min_hits", ctypes.c_uint32),
                 ("class_item_hits", ctypes.c_uint32), ("hit_buckets", ctypes.c_uint32),
-                ("band_rows_log", ctypes.c_uint32), ("bucket_records", ctypes.c_uint64)]
+                ("band_rows_log", ctypes.c_uint32), ("bucket_records", ctypes.c_uint64),
+                ("walk_prep", ctypes.c_uint32)]
 
 
 class cs_info_t(ctypes.Structure):
@@ -67,7 +68,8 @@ class cs_info_t(ctypes.Structure):
                 ("m_mod", ctypes.c_uint32), ("m_walked", ctypes.c_uint32), ("split_chunks", ctypes.c_uint64),
                 ("item_mod", ctypes.c_uint32), ("item_classes", ctypes.c_uint32),
                 ("item_chunks", ctypes.c_uint64), ("hit_buckets", ctypes.c_uint32), ("n_bands", ctypes.c_uint32),
-                ("bucket_bytes", ctypes.c_uint64), ("apply_launches", ctypes.c_uint64)]
+                ("bucket_bytes", ctypes.c_uint64), ("apply_launches", ctypes.c_uint64),
+                ("prep_chunks", ctypes.c_uint64)]
 
 
 class cs_stats_t(ctypes.Structure):
@@ -165,8 +167,9 @@ def _stream_handle(stream) -> ctypes.c_void_p:
 def make_tuning(threshold=0, tile_rows=0, large_mode=0, no_wheel=False, large_grid=0,
                 chunk_numbers=0, profile=False, layout=0, m_classes=0, item_hits=0,
                 class_min_hits=0, class_item_hits=0, hit_buckets=0, band_rows_log=0,
-                bucket_records=0) -> cs_tuning:
+                bucket_records=0, walk_prep=0) -> cs_tuning:
     t = cs_tuning()
+    t.walk_prep = walk_prep
     t.hit_buckets, t.band_rows_log, t.bucket_records = hit_buckets, band_rows_log, bucket_records
     t.layout = layout
     t.m_classes, t.item_hits, t.class_min_hits = m_classes, item_hits, class_min_hits
@@ -251,8 +254,8 @@ def cs_device_bitset(plan) -> int:
 
 
 def cs_kernel_times(plan):
-    ms = (ctypes.c_double * 6)()
-    n = (ctypes.c_uint64 * 6)()
+    ms = (ctypes.c_double * 7)()
+    n = (ctypes.c_uint64 * 7)()
     _check(load().cs_kernel_times(plan, ms, n))
     return list(ms), list(n)
 

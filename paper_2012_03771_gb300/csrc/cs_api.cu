@@ -81,7 +81,7 @@ uint64_t prime_count_bound(uint64_t x) {
     return (uint64_t)(1.25506 * (double)x / log((double)x)) + 1024;
 }
 
-enum KernelClass { KC_GEN_SMALL = 0, KC_TILE, KC_GEN_LARGE, KC_LARGE, KC_FINAL, KC_APPLY, KC_N };
+enum KernelClass { KC_GEN_SMALL = 0, KC_TILE, KC_GEN_LARGE, KC_LARGE, KC_FINAL, KC_APPLY, KC_PREP, KC_N };
 
 // Device memory of plain plans: a library-owned stream-ordered pool per device
 // that keeps up to POOL_KEEP bytes of freed plan memory for the next plan
@@ -166,6 +166,8 @@ struct cs_plan_s {
     uint32_t n_base = 0;
     SmallPrime *d_small = nullptr;
     void *d_lp = nullptr, *d_lr = nullptr, *d_lv = nullptr;
+    uint4 *d_desc0 = nullptr;             // walkers prepared by k_tg_prep (one-walker chunks)
+    uint2 *d_desc1 = nullptr;
     unsigned long long *d_counts = nullptr;   // [0] small count, [1..] per-chunk counts
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
@@ -195,7 +197,7 @@ struct cs_plan_s {
     std::vector<size_t> cache_idx;
     // profiling
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[KC_N];
-    size_t prof_used[KC_N] = {0, 0, 0, 0, 0, 0};
+    size_t prof_used[KC_N] = {};
 
     ~cs_plan_s() {
         // a plan that failed while being built: its allocations and upload are
@@ -318,6 +320,7 @@ void env_tuning(cs_tuning &t) {
     if (!t.hit_buckets) t.hit_buckets = (uint32_t)get("CS_HIT_BUCKETS");
     if (!t.band_rows_log) t.band_rows_log = (uint32_t)get("CS_BAND_ROWS_LOG");
     if (!t.bucket_records) t.bucket_records = get("CS_BUCKET_RECORDS");
+    if (!t.walk_prep) t.walk_prep = (uint32_t)get("CS_WALK_PREP");
 }
 
 cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, uint64_t M_inc,
@@ -634,6 +637,7 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
         const uint64_t bitset_bytes = M_c * wpr * 8;
         const uint32_t hb = pl->tune.hit_buckets;
         if (hb > 2) return fail(CS_EINVAL, "hit_buckets must be 0, 1 or 2");
+        if (pl->tune.walk_prep > 2) return fail(CS_EINVAL, "walk_prep must be 0, 1 or 2");
         if (pl->tune.band_rows_log > 20) return fail(CS_EINVAL, "band_rows_log must be at most 20");
         bool on = hb == 2 || (hb == 0 && bitset_bytes >= (256ull << 20));
         on = on && pl->mode == LARGE_THREE_GAP && !pl->chunks.empty() && M_c > 0 && wpr > 0;
@@ -768,6 +772,13 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
         if ((s = pl->dalloc(&b, pl->large_cap * el))) return s;
         if ((s = pl->dalloc(&c, pl->large_cap * el))) return s;
         pl->d_lp = a; pl->d_lr = b; pl->d_lv = c;
+        bool any_prep = false;
+        for (size_t k = 0; k < pl->chunks.size(); k++)
+            any_prep = any_prep || prep_eligible(pl->dp, pl->mode, pl->chunk_seg[k], pl->chunk_mc[k]);
+        if (any_prep && pl->tune.walk_prep != 1) {
+            if ((s = pl->dalloc(&pl->d_desc0, pl->large_cap))) return s;
+            if ((s = pl->dalloc(&pl->d_desc1, pl->large_cap))) return s;
+        }
     }
     CS_CUDA(cudaEventCreateWithFlags(&pl->done, cudaEventDisableTiming));
     CS_CUDA(cudaStreamSynchronize(pl->upload_stream()));
@@ -972,10 +983,17 @@ cs_status cs_sieve(cs_plan_t pl, void *stream) {
                                  pl->d_base, pl->n_base, pl->d_lp, pl->d_lr, pl->d_lv,
                                  pl->large_cap, cnt, st));
         if ((s = prof.end())) return s;
+        const bool pre = pl->d_desc0 && prep_eligible(dp, pl->mode, pl->chunk_seg[c], pl->chunk_mc[c]);
+        if (pre) {
+            if ((s = prof.begin(KC_PREP))) return s;
+            CS_CUDA(launch_tg_prep(dp, narrow, pl->d_lp, pl->d_lr, pl->d_lv, cnt, pl->large_cap, 0, ~0ull,
+                                   pl->chunk_mc[c], pl->d_desc0, pl->d_desc1, st));
+            if ((s = prof.end())) return s;
+        }
         if ((s = prof.begin(KC_LARGE))) return s;
         CS_CUDA(launch_large(dp, narrow, pl->mode, pl->d_lp, pl->d_lr, pl->d_lv, cnt,
                              pl->large_cap, pl->chunk_seg[c], pl->large_grid, st, 0, ~0ull,
-                             pl->chunk_mc[c]));
+                             pl->chunk_mc[c], pre ? pl->d_desc0 : nullptr, pre ? pl->d_desc1 : nullptr));
         if ((s = prof.end())) return s;
         if ((s = apply(c))) return s;
     }
@@ -1016,9 +1034,13 @@ cs_status cs_info(cs_plan_t pl, cs_info_t *out) {
     out->n_large_chunks = pl->chunks.size();
     // per large-prime chunk: the walk, and without a cache the generator (and,
     // for 64-bit primes, the residue kernel)
+    // (and the walker preparation of the one-walker chunks)
     uint64_t large_launches = 0;
-    for (const auto &ch : pl->chunks)
+    for (size_t c = 0; c < pl->chunks.size(); c++) {
+        const auto &ch = pl->chunks[c];
         large_launches += pl->cache ? 1 : (pl->narrow || ch.second < NARROW_LIMIT) ? 2 : 3;
+        large_launches += pl->d_desc0 && prep_eligible(pl->dp, pl->mode, pl->chunk_seg[c], pl->chunk_mc[c]);
+    }
     out->launches_per_sieve = (pl->small_hi > pl->P ? 1 : 0) + (pl->M_c && pl->W ? 1 : 0) +
                               (pl->M_c ? 1 : 0) + large_launches + (pl->dp.bucket ? pl->apply_launches : 0);
     out->h2d_bytes = pl->h2d;
@@ -1036,6 +1058,9 @@ cs_status cs_info(cs_plan_t pl, cs_info_t *out) {
     out->n_bands = pl->dp.bucket ? pl->dp.n_bands : 0;
     out->bucket_bytes = pl->bucket_bytes;
     out->apply_launches = pl->dp.bucket ? pl->apply_launches : 0;
+    out->prep_chunks = 0;
+    for (size_t c = 0; c < pl->chunks.size() && pl->d_desc0; c++)
+        out->prep_chunks += prep_eligible(pl->dp, pl->mode, pl->chunk_seg[c], pl->chunk_mc[c]);
     if (pl->layout == 1) out->W = pl->Wc_max;
     return CS_OK;
 }
@@ -1144,7 +1169,7 @@ cs_status cs_row_columns(cs_plan_t pl, uint64_t row, int64_t *x_of_col, size_t n
 
 const void *cs_device_bitset(cs_plan_t pl) { return pl ? (const void *)pl->dp.bits : nullptr; }
 
-cs_status cs_kernel_times(cs_plan_t pl, double ms[6], uint64_t launches[6]) {
+cs_status cs_kernel_times(cs_plan_t pl, double ms[7], uint64_t launches[7]) {
     if (!pl || !ms || !launches) return fail(CS_EINVAL, "NULL argument");
     if (!pl->tune.profile) return fail(CS_ESTATE, "plan was built without profile = 1");
     cs_status s = wait_plan(pl);

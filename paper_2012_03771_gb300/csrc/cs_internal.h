@@ -155,10 +155,20 @@ constexpr MClasses EVERY_M = MClasses{1, 1, {0, 0}, 0, {}};
 // v may be NULL: then v0 = (r M_start + SL) mod p is computed per prime, and
 // only primes with p_lo < p <= p_hi are walked (a residue-cache chunk holds
 // primes outside the plan's range).
+// desc0/desc1: walkers prepared by launch_tg_prep for this chunk (used when
+// prep_eligible; NULL: the walk prepares its items itself).
 cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p, const void *r,
                          const void *v, const unsigned long long *count, uint64_t cap,
                          uint32_t n_seg, int grid, cudaStream_t stream, uint64_t p_lo = 0,
-                         uint64_t p_hi = ~0ull, MClasses mc = EVERY_M);
+                         uint64_t p_hi = ~0ull, MClasses mc = EVERY_M, const uint4 *desc0 = nullptr,
+                         const uint2 *desc1 = nullptr);
+// Walker preparation for one-walker chunks of the three-gap walk (odd m or
+// every m, one segment per prime, SL > 0): per prime of the chunk, the first
+// hit and the two steps, into desc0/desc1 (cap entries each).
+bool prep_eligible(const DevPlan &pl, int mode, uint32_t n_seg, MClasses mc);
+cudaError_t launch_tg_prep(const DevPlan &pl, bool narrow, const void *p, const void *r, const void *v,
+                           const unsigned long long *count, uint64_t cap, uint64_t p_lo, uint64_t p_hi,
+                           MClasses mc, uint4 *desc0, uint2 *desc1, cudaStream_t stream);
 cudaError_t launch_final(const DevPlan &pl, cudaStream_t stream);
 // Clears the bucketed hits of the walk launches since the last application,
 // band after band, and empties the regions.

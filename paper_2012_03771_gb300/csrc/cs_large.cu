@@ -39,7 +39,12 @@ struct LargeArgs {
     uint32_t n_seg;      // m-segments per prime (work items = primes x n_seg)
     uint64_t p_lo, p_hi; // walk only p_lo < p <= p_hi (v == NULL: shared cache chunk)
     MClasses mc;         // three-gap walk: m-classes walked (Q = 1: every m)
+    // one-walker chunks: walkers prepared by k_tg_prep, per prime i
+    // {first m - M_start (or NO_WALKER), v there, d_a, u_b} and {steps of m a, b}
+    const uint4 *desc0;
+    const uint2 *desc1;
 };
+constexpr uint32_t NO_WALKER = 0xffffffffu;
 
 // v0 = (r * M_start + SL) mod p, for primes from a shared residue cache
 __device__ __forceinline__ uint32_t start_v(uint32_t r, uint64_t M_start, uint32_t SL, uint32_t p) {
@@ -299,10 +304,12 @@ __device__ __forceinline__ uint64_t mul_add_mod(uint64_t v, uint64_t r, uint32_t
 // CI: 0 = m-class walkers, 1 = class items, 2 = class items mod Q = d in the
 // literal layout, whose rows follow from the walker's steps: every walked m is
 // a row, and a step of k Q in m passes k phi(Q) rows.
-template <class UT, class ST, class MT, int NC, int CI, bool JOBS = false, bool BKT = false>
+// PRE: the walkers come prepared by k_tg_prep (one-walker items, one segment).
+template <class UT, class ST, class MT, int NC, int CI, bool JOBS = false, bool BKT = false, bool PRE = false>
 __device__ __forceinline__ void walk_warp(const LargeArgs &a, TGItem<MT> *q, const uint8_t *item_off,
                                           uint64_t first, uint64_t n_warps, uint32_t *bkt_s = nullptr) {
     static_assert(!CI || NC == 1, "class items walk one class per item");
+    static_assert(!PRE || (NC == 1 && !CI && !JOBS), "prepared walkers: one-walker items");
     constexpr int QCAP = 32 * (NC + 1);   // a refill adds at most 32 NC walkers
     const uint32_t n_cls_items = CI ? a.mc.items : 1;
     const DevPlan &pl = a.pl;
@@ -354,7 +361,19 @@ __device__ __forceinline__ void walk_warp(const LargeArgs &a, TGItem<MT> *q, con
             TGItem<MT> e;
 #pragma unroll
             for (int k = 0; k < NC; k++) push[k] = false;
-            if (item < n_items) {
+            if (PRE && item < n_items) {
+                const uint4 d = a.desc0[item];
+                const uint2 st = a.desc1[item];
+                push[0] = d.x != NO_WALKER;
+                first_m[0] = (MT)d.x;
+                first_v[0] = (UT)d.y;
+                e.end = (MT)M;
+                e.idx = (uint32_t)item;
+                e.da = d.z;
+                e.ub = d.w;
+                e.ma = (MT)st.x;
+                e.mb = (MT)st.y;
+            } else if (!PRE && item < n_items) {
                 uint64_t i = item, m_lo = 0, m_hi = M;
                 uint32_t off0 = a.mc.off[0];               // NC = 1: the class walked
                 if constexpr (CI) {
@@ -582,7 +601,7 @@ __device__ __forceinline__ void walk_warp(const LargeArgs &a, TGItem<MT> *q, con
     }
 }
 
-template <class UT, class ST, class MT, int NC, int CI = 0, bool BKT = false>
+template <class UT, class ST, class MT, int NC, int CI = 0, bool BKT = false, bool PRE = false>
 __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLOCKS : CS_TG_MIN_BLOCKS_WIDE) k_large_tg(const LargeArgs a) {
     constexpr int QCAP = 32 * (NC + 1);
     __shared__ TGItem<MT> queue[TG_WARPS][QCAP];
@@ -599,7 +618,7 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
         for (uint32_t b = threadIdx.x; b < pl.n_bands; b += LARGE_THREADS)
             bkt_s[b] = pl.bkt_cnt[(uint64_t)b * pl.n_regions + blockIdx.x];
     if constexpr (CI || BKT) __syncthreads();
-    walk_warp<UT, ST, MT, NC, CI, false, BKT>(a, queue[threadIdx.x >> 5], item_off,
+    walk_warp<UT, ST, MT, NC, CI, false, BKT, PRE>(a, queue[threadIdx.x >> 5], item_off,
                                               (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5,
                                               ((uint64_t)gridDim.x * blockDim.x) >> 5, bkt_s);
     if constexpr (BKT) {
@@ -607,6 +626,93 @@ __global__ void __launch_bounds__(LARGE_THREADS, sizeof(UT) == 4 ? CS_TG_MIN_BLO
         __syncthreads();
         for (uint32_t b = threadIdx.x; b < pl.n_bands; b += LARGE_THREADS)
             pl.bkt_cnt[(uint64_t)b * pl.n_regions + blockIdx.x] = min(bkt_s[b], pl.region_cap);
+    }
+}
+
+// Walker preparation for the one-walker chunks (odd m, or every m; one
+// segment per prime): per prime, the class's first v, the two steps from one
+// Euclid run and the first hit, exactly as the walk prepares an item, written
+// as a descriptor that the walk reads instead.  The Euclid runs are serial
+// chains of float-estimate divisions (one per step, about a dozen steps per
+// prime); the walk kernel, with its queue and hit path, holds 80 registers and
+// keeps 24 warps per SM, too few to hide them, while this kernel keeps one
+// prime per thread and many more warps.  Solver statistics and errors are
+// counted here.
+constexpr int PREP_THREADS = 256;
+template <class UT, class ST>
+__global__ void __launch_bounds__(PREP_THREADS) k_tg_prep(const LargeArgs a, uint4 *desc0, uint2 *desc1) {
+    const DevPlan &pl = a.pl;
+    const UT *Pp = reinterpret_cast<const UT *>(a.p);
+    const UT *Rp = reinterpret_cast<const UT *>(a.r);
+    const UT *Vp = reinterpret_cast<const UT *>(a.v);
+    const uint64_t n = min((uint64_t)*a.count, a.cap);
+    const UT w = (UT)(2 * pl.SL);
+    const uint64_t M = pl.M_inc;
+    const uint32_t Q = a.mc.Q, off0 = a.mc.off[0];
+    const uint32_t max_iter = 4 * 8 * sizeof(UT) + 8;
+    unsigned long long solves = 0, levels = 0, err = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * PREP_THREADS;
+    for (uint64_t i = blockIdx.x * (uint64_t)PREP_THREADS + threadIdx.x; i < n; i += stride) {
+        const UT pp = Pp[i], r = Rp[i];
+        bool ok = (uint64_t)pp > a.p_lo && (uint64_t)pp <= a.p_hi;
+        const UT vv = ok ? (Vp ? Vp[i] : start_v(r, pl.M_start, pl.SL, pp)) : (UT)0;
+        uint32_t it = 0;
+        UT ma_ = 0, da_ = 0, mb_ = 0, ub_ = 0;
+        uint64_t first = 0;
+        UT vk = vv;
+        uint32_t dd = 0;
+        if (ok) {
+            // the class's first m is m = off0 (mod Q), Q <= 2: v advances by r per m
+            dd = off0;
+            vk = add_times(vv, r, dd, pp);
+            const UT rq = add_times(r, r, Q - 1, pp);
+            if constexpr (sizeof(UT) == 8) {
+                if (w >= 1024) {
+                    uint64_t a64, b64;
+                    uint32_t da32, ub32;
+                    ok = tg_steps_w(pp, rq, (uint32_t)w, a64, da32, b64, ub32, it, max_iter);
+                    ma_ = a64; mb_ = b64; da_ = da32; ub_ = ub32;
+                } else {
+                    ok = tg_steps<UT>(pp, rq, w, ma_, da_, mb_, ub_, it, max_iter);
+                }
+            } else {
+                ok = tg_steps<UT>(pp, rq, w, ma_, da_, mb_, ub_, it, max_iter);
+            }
+            if (!ok) err |= ERR_SOLVER_LIMIT;
+            solves += 2 + (vk > w);
+            if (ok && vk > w) {
+                if constexpr (sizeof(UT) == 4) {
+                    uint32_t y;
+                    first = (uint64_t)first_hit32(pp, rcp_rn((float)pp), w, ma_, da_, mb_, ub_, vk, y) * Q;
+                    vk = y;
+                } else {
+                    const bool narrow_ab = w >= 1024 && ((uint64_t)ma_ | (uint64_t)mb_) < (1ull << 31);
+                    if (narrow_ab) {
+                        uint32_t y;
+                        first = first_hit_w(pp, rcp_rn(u64_to_f((uint64_t)pp)), (uint32_t)w, (uint32_t)ma_,
+                                            (uint32_t)da_, (uint32_t)mb_, (uint32_t)ub_, vk, y) * Q;
+                        vk = (UT)y;
+                    } else {
+                        uint64_t y;
+                        first = first_hit64(pp, w, ma_, da_, mb_, ub_, vk, y) * Q;
+                        vk = (UT)y;
+                    }
+                }
+            }
+        }
+        levels += it;
+        const uint64_t mf = dd + first;
+        const uint64_t sa = (uint64_t)ma_ * Q, sb = (uint64_t)mb_ * Q;
+        desc0[i] = make_uint4(ok && mf < M ? (uint32_t)mf : NO_WALKER, (uint32_t)vk, (uint32_t)da_, (uint32_t)ub_);
+        desc1[i] = make_uint2((uint32_t)(sa < M ? sa : M), (uint32_t)(sb < M ? sb : M));
+    }
+    solves = warp_sum(solves);
+    levels = warp_sum(levels);
+    for (int o = 16; o; o >>= 1) err |= __shfl_xor_sync(0xffffffffu, err, o);
+    if ((threadIdx.x & 31) == 0) {
+        if (solves) atomicAdd(pl.stats + ST_SOLVES, solves);
+        if (levels) atomicAdd(pl.stats + ST_LEVELS, levels);
+        if (err) atomicOr(pl.stats + ST_ERROR, err);
     }
 }
 
@@ -713,9 +819,35 @@ __global__ void k_modsolve(const uint64_t *p, const uint64_t *K, const uint64_t 
 
 }  // namespace
 
+bool prep_eligible(const DevPlan &pl, int mode, uint32_t n_seg, MClasses mc) {
+    return mode != LARGE_PAPER && pl.SL > 0 && (n_seg <= 1) && !mc.items && mc.n == 1 && mc.Q <= 2 &&
+           mc.off[0] < mc.Q;
+}
+
+cudaError_t launch_tg_prep(const DevPlan &pl, bool narrow, const void *p, const void *r, const void *v,
+                           const unsigned long long *count, uint64_t cap, uint64_t p_lo, uint64_t p_hi,
+                           MClasses mc, uint4 *desc0, uint2 *desc1, cudaStream_t stream) {
+    LargeArgs a{pl, p, r, v, count, cap, 1, p_lo, p_hi, mc, nullptr, nullptr};
+    void (*kern)(const LargeArgs, uint4 *, uint2 *) =
+        narrow ? k_tg_prep<uint32_t, int32_t> : k_tg_prep<uint64_t, int64_t>;
+    // one wave of resident CTAs, looked up once per width
+    static std::atomic<int> resident[2];
+    std::atomic<int> &cached = resident[narrow ? 1 : 0];
+    int per_sm = cached.load(std::memory_order_relaxed);
+    if (per_sm == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PREP_THREADS, 0) != cudaSuccess ||
+            per_sm <= 0)
+            per_sm = 1;
+        cached.store(per_sm, std::memory_order_relaxed);
+    }
+    kern<<<sm_count() * per_sm, PREP_THREADS, 0, stream>>>(a, desc0, desc1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p, const void *r,
                          const void *v, const unsigned long long *count, uint64_t cap, uint32_t n_seg,
-                         int grid, cudaStream_t stream, uint64_t p_lo, uint64_t p_hi, MClasses mc) {
+                         int grid, cudaStream_t stream, uint64_t p_lo, uint64_t p_hi, MClasses mc,
+                         const uint4 *desc0, const uint2 *desc1) {
     const bool items_ok = mc.items == mc.n && mc.n <= MAX_CLASS_ITEMS && mc.Q <= 256;
     if (mc.Q == 0 || mc.n < 1 || mc.n > mc.Q || (mc.items ? !items_ok : mc.n > 2) || pl.SL == 0) mc = EVERY_M;
     // walk kernel: 0 = one walker per item, 1 = two classes per item, 2 = class
@@ -723,14 +855,20 @@ cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p
     // literal layout)
     int kind = mc.items ? 2 : mc.n == 2 ? 1 : 0;
     if (kind == 2 && narrow && mode != LARGE_PAPER && !pl.compact && mc.Q == pl.d) kind = 3;
-    LargeArgs a{pl, p, r, v, count, cap, n_seg ? n_seg : 1, p_lo, p_hi, mc};
+    // 4 = one walker per item, prepared by k_tg_prep
+    const bool pre = desc0 && desc1 && kind == 0 && prep_eligible(pl, mode, n_seg, mc);
+    if (pre) kind = 4;
+    LargeArgs a{pl, p, r, v, count, cap, n_seg ? n_seg : 1, p_lo, p_hi, mc, pre ? desc0 : nullptr,
+                pre ? desc1 : nullptr};
     // bucketed hits: three-gap walk only (the paper's walk clears directly)
     const int bkt = (pl.bucket && mode != LARGE_PAPER) ? 1 : 0;
     if (!bkt) a.pl.bucket = 0;
     const size_t dyn = bkt ? (size_t)pl.n_bands * sizeof(uint32_t) : 0;
     void (*walk)(const LargeArgs) = nullptr;
     if (narrow) {
-        walk = kind == 3 ? (bkt ? k_large_tg<uint32_t, int32_t, uint32_t, 1, 2, true>
+        walk = kind == 4 ? (bkt ? k_large_tg<uint32_t, int32_t, uint32_t, 1, 0, true, true>
+                                : k_large_tg<uint32_t, int32_t, uint32_t, 1, 0, false, true>)
+             : kind == 3 ? (bkt ? k_large_tg<uint32_t, int32_t, uint32_t, 1, 2, true>
                                 : k_large_tg<uint32_t, int32_t, uint32_t, 1, 2>)
              : kind == 2 ? (bkt ? k_large_tg<uint32_t, int32_t, uint32_t, 1, 1, true>
                                 : k_large_tg<uint32_t, int32_t, uint32_t, 1, 1>)
@@ -739,7 +877,9 @@ cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p
                          : (bkt ? k_large_tg<uint32_t, int32_t, uint32_t, 1, 0, true>
                                 : k_large_tg<uint32_t, int32_t, uint32_t, 1>);
     } else {
-        walk = kind == 2 ? (bkt ? k_large_tg<uint64_t, int64_t, uint32_t, 1, 1, true>
+        walk = kind == 4 ? (bkt ? k_large_tg<uint64_t, int64_t, uint32_t, 1, 0, true, true>
+                                : k_large_tg<uint64_t, int64_t, uint32_t, 1, 0, false, true>)
+             : kind == 2 ? (bkt ? k_large_tg<uint64_t, int64_t, uint32_t, 1, 1, true>
                                 : k_large_tg<uint64_t, int64_t, uint32_t, 1, 1>)
              : kind == 1 ? (bkt ? k_large_tg<uint64_t, int64_t, uint32_t, 2, 0, true>
                                 : k_large_tg<uint64_t, int64_t, uint32_t, 2>)
@@ -754,7 +894,7 @@ cudaError_t launch_large(const DevPlan &pl, bool narrow, int mode, const void *p
         if (mode != LARGE_PAPER) {
             // looked up once per [narrow][kind][bucketed] (the bucket counters,
             // at most 16 KB, do not change the occupancy bound by registers)
-            static std::atomic<int> resident[2][4][2];
+            static std::atomic<int> resident[2][5][2];
             std::atomic<int> &cached = resident[narrow ? 1 : 0][kind][bkt];
             int per_sm = cached.load(std::memory_order_relaxed);
             if (per_sm == 0) {

@@ -41,7 +41,7 @@ def test_reference_arm_prints_one_contract_line():
 
 def _info(**kw):
     base = dict(threshold=120003, tile_rows=16, n_large_chunks=17, bitset_bytes=37487120, M_c=22858,
-                hit_buckets=0, n_bands=0, apply_launches=0, bucket_bytes=0)
+                hit_buckets=0, n_bands=0, apply_launches=0, bucket_bytes=0, prep_chunks=0)
     base.update(kw)
     return SimpleNamespace(**base)
 

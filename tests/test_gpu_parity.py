@@ -240,6 +240,53 @@ def test_bucketed_hits_bit_exact(band_rows_log, bucket_records):
     assert n > 60
 
 
+def test_prepared_walkers_bit_exact():
+    """One-walker chunks whose walkers a preparation kernel computes (first hit
+    and steps per prime, then only walked) give the same bitset, F, counts and
+    solver statistics as the walk preparing its items itself: 32-bit primes,
+    64-bit primes (L above 2^30, with hit buckets too), odd d (every m walked)
+    and the tiny brute-force cases against the oracle."""
+    cases = [workloads.PLAIN_503.with_(L=3 * 10**6),
+             workloads.SieveParams(P=503, d=2310, M_start=10**6, M_inc=3000, SL=3000, L=3 * 10**9),
+             workloads.SieveParams(P=97, d=15, M_start=10**5 + 7, M_inc=700, SL=900, L=2 * 10**6)]
+    for prm in cases:
+        args = prm.as_tuple()
+        for extra in ({}, {"hit_buckets": 2}):
+            got = _run(args, walk_prep=2, **extra)
+            ref = _run(args, walk_prep=1, **extra)
+            assert got["info"].prep_chunks > 0 and ref["info"].prep_chunks == 0, prm
+            assert np.array_equal(got["bits"], ref["bits"]), prm
+            assert (got["F"], got["hash"]) == (ref["F"], ref["hash"])
+            assert np.array_equal(got["counts"], ref["counts"])
+            for k in ("solves", "levels", "hits_all", "F_large"):
+                assert got["stats"][k] == ref["stats"][k], (prm, k)
+    _check_full(cases[0].as_tuple(), _run(cases[0].as_tuple(), walk_prep=2))
+    n = 0
+    for prm in workloads.tiny_cases(150, seed=17):
+        args = prm.as_tuple()
+        if O.validate(*args):
+            continue
+        got = _run(args, large_mode=2, threshold=max(2 * prm.SL, 1), walk_prep=2)
+        _check_full(args, got)
+        n += got["info"].prep_chunks > 0
+    assert n > 10
+
+
+def test_profiled_launches_equal_the_stated_count():
+    """The kernels a sieve launches (counted by the plan's own CUDA-event
+    brackets, one kernel each for primes below 2^30; a 64-bit chunk's
+    generation bracket also holds its residue kernel) are the
+    launches_per_sieve the plan states, which bench.py reports as
+    gpu_launches."""
+    for prm, extra in ((workloads.SEARCH_953, {}), (workloads.PLAIN_503.with_(L=3 * 10**6), {}),
+                       (workloads.PLAIN_503.with_(L=3 * 10**6), {"hit_buckets": 2}),
+                       (workloads.PLAIN_503.with_(L=3 * 10**6), {"walk_prep": 1})):
+        with cs.Plan(*prm.as_tuple(), profile=True, **extra) as plan:
+            plan.sieve(torch.cuda.current_stream()).sync()
+            ms, n = plan.kernel_times()
+            assert sum(n) == int(plan.info.launches_per_sieve), (prm, extra, n)
+
+
 def test_bucketed_hits_of_the_search_equal_direct_clears():
     """search_953 with its hits bucketed (forced; its 37.5 MB bitset clears
     directly by default) gives the same checksum, F and per-row counts."""

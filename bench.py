@@ -386,21 +386,26 @@ def csrc_sha() -> str:
 # ncu counters of the large-prime walk, summed over the walk's launches of one
 # sieve (the first, the bench's warm-up sieve) of each workload, taken with
 #   ncu --metrics smsp__thread_inst_executed.sum,gpu__time_duration.sum --clock-control none
-#       -k regex:k_large_tg -c 756 --csv python bench.py --steps 1 --warmup 1 --no-cpu
+#       -k regex:"k_large_tg|k_tg_prep" -c 1424 --csv python bench.py --steps 1 --warmup 1 --no-cpu
 #   ncu --metrics gpu__time_duration.sum,smsp__thread_inst_executed.sum,dram__bytes_read.sum,
-#       dram__bytes_write.sum --clock-control none -k regex:k_large_tg -c 17 --csv
+#       dram__bytes_write.sum --clock-control none -k regex:"k_large_tg|k_tg_prep" -c 24 --csv
 #       python bench.py --config search_953 --steps 1 --warmup 1 --no-cpu
+# (756 and 17 walk launches, 668 and 7 preparation launches per sieve)
 # The work is deterministic (same inputs, same code), so these are per-sieve
 # constants for the walk sources whose digest is recorded (csrc_sha) and the
 # same threshold, tile height and chunking; otherwise they are not used.
 WALK_COUNTERS = {
-    # one GB300, sources of the walk with hit buckets (large_1019 buckets its hits,
-    # search_953 clears directly); large_1019's DRAM bytes were not captured at
-    # full size (several passes on a 13 GB working set)
-    "large_1019": {"csrc_sha": "4dbc7f665b0758df", "threshold": 100002, "tile_rows": 8, "launches": 756,
-                   "thread_inst": 13183978472484.0, "dram_bytes": None},
-    "search_953": {"csrc_sha": "4dbc7f665b0758df", "threshold": 120003, "tile_rows": 16, "launches": 17,
-                   "thread_inst": 87976364443.0, "dram_bytes": 1243115008.0 + 946688.0},
+    # one GB300, walk sources with hit buckets, class-item rows from the steps and
+    # prepared walkers for the one-walker chunks (large_1019 buckets its hits,
+    # search_953 clears directly); prep_*: the walker-preparation kernel of the
+    # same run; large_1019's DRAM bytes were not captured at full size (several
+    # passes on a 13 GB working set)
+    "large_1019": {"csrc_sha": "41c598252c393e29", "threshold": 100002, "tile_rows": 8, "launches": 756,
+                   "thread_inst": 9116869325695.0, "dram_bytes": None,
+                   "prep_launches": 668, "prep_thread_inst": 3682295560799.0},
+    "search_953": {"csrc_sha": "41c598252c393e29", "threshold": 120003, "tile_rows": 16, "launches": 17,
+                   "thread_inst": 62759972625.0, "dram_bytes": 1798116864.0,
+                   "prep_launches": 7, "prep_thread_inst": 26092470260.0},
 }
 
 

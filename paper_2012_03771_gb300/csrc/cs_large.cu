@@ -24,6 +24,7 @@
 
 #include "cs_arith.cuh"
 #include "cs_internal.h"
+#include "cs_walker.cuh"
 
 namespace cs {
 
@@ -44,7 +45,6 @@ struct LargeArgs {
     const uint4 *desc0;
     const uint2 *desc1;
 };
-constexpr uint32_t NO_WALKER = 0xffffffffu;
 
 // v0 = (r * M_start + SL) mod p, for primes from a shared residue cache
 __device__ __forceinline__ uint32_t start_v(uint32_t r, uint64_t M_start, uint32_t SL, uint32_t p) {
@@ -266,15 +266,6 @@ constexpr int TG_STEPS = CS_TG_STEPS;               // class walks (long walkers
 constexpr int TG_STEPS_ALL_M = CS_TG_STEPS_ALL_M;   // one-walker items (the light chunks)
 constexpr int TG_WARPS = LARGE_THREADS / 32;
 
-// v + k r mod p for a small k (v, r < p, 2p fits in UT)
-template <class UT>
-__device__ __forceinline__ UT add_times(UT v, UT r, uint32_t k, UT p) {
-    for (; k; k--) {
-        v += r;
-        if (v >= p) v -= p;
-    }
-    return v;
-}
 // the same for k < 2^31 in one reduction (fr = rcp_rn(p) for 32-bit p)
 __device__ __forceinline__ uint32_t mul_add_mod(uint32_t v, uint32_t r, uint32_t k, uint32_t p, float fr) {
     int64_t rem;
@@ -654,57 +645,14 @@ __global__ void __launch_bounds__(PREP_THREADS) k_tg_prep(const LargeArgs a, uin
     const uint64_t stride = (uint64_t)gridDim.x * PREP_THREADS;
     for (uint64_t i = blockIdx.x * (uint64_t)PREP_THREADS + threadIdx.x; i < n; i += stride) {
         const UT pp = Pp[i], r = Rp[i];
-        bool ok = (uint64_t)pp > a.p_lo && (uint64_t)pp <= a.p_hi;
-        const UT vv = ok ? (Vp ? Vp[i] : start_v(r, pl.M_start, pl.SL, pp)) : (UT)0;
-        uint32_t it = 0;
-        UT ma_ = 0, da_ = 0, mb_ = 0, ub_ = 0;
-        uint64_t first = 0;
-        UT vk = vv;
-        uint32_t dd = 0;
-        if (ok) {
-            // the class's first m is m = off0 (mod Q), Q <= 2: v advances by r per m
-            dd = off0;
-            vk = add_times(vv, r, dd, pp);
-            const UT rq = add_times(r, r, Q - 1, pp);
-            if constexpr (sizeof(UT) == 8) {
-                if (w >= 1024) {
-                    uint64_t a64, b64;
-                    uint32_t da32, ub32;
-                    ok = tg_steps_w(pp, rq, (uint32_t)w, a64, da32, b64, ub32, it, max_iter);
-                    ma_ = a64; mb_ = b64; da_ = da32; ub_ = ub32;
-                } else {
-                    ok = tg_steps<UT>(pp, rq, w, ma_, da_, mb_, ub_, it, max_iter);
-                }
-            } else {
-                ok = tg_steps<UT>(pp, rq, w, ma_, da_, mb_, ub_, it, max_iter);
-            }
-            if (!ok) err |= ERR_SOLVER_LIMIT;
-            solves += 2 + (vk > w);
-            if (ok && vk > w) {
-                if constexpr (sizeof(UT) == 4) {
-                    uint32_t y;
-                    first = (uint64_t)first_hit32(pp, rcp_rn((float)pp), w, ma_, da_, mb_, ub_, vk, y) * Q;
-                    vk = y;
-                } else {
-                    const bool narrow_ab = w >= 1024 && ((uint64_t)ma_ | (uint64_t)mb_) < (1ull << 31);
-                    if (narrow_ab) {
-                        uint32_t y;
-                        first = first_hit_w(pp, rcp_rn(u64_to_f((uint64_t)pp)), (uint32_t)w, (uint32_t)ma_,
-                                            (uint32_t)da_, (uint32_t)mb_, (uint32_t)ub_, vk, y) * Q;
-                        vk = (UT)y;
-                    } else {
-                        uint64_t y;
-                        first = first_hit64(pp, w, ma_, da_, mb_, ub_, vk, y) * Q;
-                        vk = (UT)y;
-                    }
-                }
-            }
+        uint4 d0 = make_uint4(NO_WALKER, 0, 0, 0);
+        uint2 d1 = make_uint2(0, 0);
+        if ((uint64_t)pp > a.p_lo && (uint64_t)pp <= a.p_hi) {
+            const UT vv = Vp ? Vp[i] : start_v(r, pl.M_start, pl.SL, pp);
+            prep_walker<UT>(pp, r, vv, w, M, Q, off0, max_iter, solves, levels, err, d0, d1);
         }
-        levels += it;
-        const uint64_t mf = dd + first;
-        const uint64_t sa = (uint64_t)ma_ * Q, sb = (uint64_t)mb_ * Q;
-        desc0[i] = make_uint4(ok && mf < M ? (uint32_t)mf : NO_WALKER, (uint32_t)vk, (uint32_t)da_, (uint32_t)ub_);
-        desc1[i] = make_uint2((uint32_t)(sa < M ? sa : M), (uint32_t)(sb < M ? sb : M));
+        desc0[i] = d0;
+        desc1[i] = d1;
     }
     solves = warp_sum(solves);
     levels = warp_sum(levels);

@@ -253,12 +253,18 @@ struct TGItem {
     MT ma, mb;                     // steps of m (clamped to M_inc)
 };
 
-// three-gap steps per lane between queue checks
+// three-gap steps per lane between queue checks, class walkers (class items
+// and the two walkers mod 6): their m-segments hold nearly the same number of
+// hits (about the walked hits per item, 128), so the lanes of a warp finish
+// their walkers at nearly the same time and waiting for them costs little,
+// while each queue check costs its ballots and branches.  large_1019 walk: 720
+// ms at 8 steps, 689 at 16, 656 at 48, 625 at 128, 617-618 at 256 and more;
+// search_953 (fewer hits per item): 4.14, 4.08, 4.13, 4.10, 4.20-4.48 ms.
 #ifndef CS_TG_STEPS
-#define CS_TG_STEPS 8
+#define CS_TG_STEPS 128
 #endif
 // one-walker items (odd m or every m; the light chunks, a few hits per walker):
-// four steps measured best of 2, 3, 4, 8
+// four steps measured best of 2, 3, 4, 6, 8
 #ifndef CS_TG_STEPS_ALL_M
 #define CS_TG_STEPS_ALL_M 4
 #endif

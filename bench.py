@@ -402,12 +402,12 @@ WALK_COUNTERS = {
     # search_953 clears directly); prep_*: the walker-preparation kernel of the
     # same run; large_1019's DRAM bytes were not captured at full size (several
     # passes on a 13 GB working set)
-    "large_1019": {"csrc_sha": "41c598252c393e29", "threshold": 100002, "tile_rows": 8, "launches": 756,
-                   "thread_inst": 9116869325695.0, "dram_bytes": None,
-                   "prep_launches": 668, "prep_thread_inst": 3682295560799.0},
-    "search_953": {"csrc_sha": "41c598252c393e29", "threshold": 120003, "tile_rows": 16, "launches": 17,
-                   "thread_inst": 62759972625.0, "dram_bytes": 1798116864.0,
-                   "prep_launches": 7, "prep_thread_inst": 26092470260.0},
+    "large_1019": {"csrc_sha": "5137cbf2aa2f3f3b", "threshold": 100002, "tile_rows": 8, "launches": 756,
+                   "thread_inst": 8482410453711.0, "dram_bytes": None,
+                   "prep_launches": 668, "prep_thread_inst": 3688559220935.0},
+    "search_953": {"csrc_sha": "5137cbf2aa2f3f3b", "threshold": 120003, "tile_rows": 16, "launches": 17,
+                   "thread_inst": 59499039090.0, "dram_bytes": 1797687296.0,
+                   "prep_launches": 7, "prep_thread_inst": 25639266335.0},
 }
 
 

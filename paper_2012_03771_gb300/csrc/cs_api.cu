@@ -626,70 +626,27 @@ cs_status build_plan(cs_plan_s *pl, uint32_t P, uint64_t d, uint64_t M_start, ui
     // device memory and tables
     DevPlan &dp = pl->dp;
 
-    // the walk's stored hits through per-band regions, for bitsets of 256 MiB
-    // and more (twice L2): a scattered atomic AND per hit costs a DRAM sector
-    // read and written back (about 100 bytes) once the bitset no longer fits in
-    // L2, while a record costs 4 bytes written and read and is cleared band
-    // after band with the band's words in L2 (4.77 GB bitset: 12% less time per
-    // sieve).  Smaller bitsets stay in L2 and clear directly.
+    // the walk's stored hits through per-band regions (cs_buckets.h): by
+    // default for bitsets of 256 MiB and more, whose scattered clears would go
+    // to DRAM (4.77 GB bitset: 12% less time per sieve)
     dp.bucket = 0;
     {
-        const uint64_t bitset_bytes = M_c * wpr * 8;
-        const uint32_t hb = pl->tune.hit_buckets;
-        if (hb > 2) return fail(CS_EINVAL, "hit_buckets must be 0, 1 or 2");
+        if (pl->tune.hit_buckets > 2) return fail(CS_EINVAL, "hit_buckets must be 0, 1 or 2");
         if (pl->tune.walk_prep > 2) return fail(CS_EINVAL, "walk_prep must be 0, 1 or 2");
         if (pl->tune.band_rows_log > 20) return fail(CS_EINVAL, "band_rows_log must be at most 20");
-        bool on = hb == 2 || (hb == 0 && bitset_bytes >= (256ull << 20));
-        on = on && pl->mode == LARGE_THREE_GAP && !pl->chunks.empty() && M_c > 0 && wpr > 0;
-        uint32_t bl = pl->tune.band_rows_log;
-        if (on && !bl) {
-            // bands of at most a fifth of L2 (and no more rows than the bitset),
-            // then at most BKT_MAX_BANDS: the apply keeps about 1.3 bands in
-            // work, and larger bands let the records push them out of L2
-            // (4.77 GB bitset, GB300: 17 MB bands best, 34 MB 1.5x slower apply)
-            const uint64_t band_max = l2_bytes() / 5;
-            while ((2ull << bl) * wpr * 8 <= band_max && (2ull << bl) <= M_c) bl++;
-            while (((M_c + (1ull << bl) - 1) >> bl) > BKT_MAX_BANDS) bl++;
-        }
-        const bool fits = ((64ull * wpr) << bl) <= (1ull << 32);   // a record: (row in band) * 64 wpr + column
-        const uint64_t n_bands = (M_c + (1ull << bl) - 1) >> bl;
-        if (on && pl->tune.band_rows_log && (!fits || n_bands > BKT_MAX_BANDS))
+        // a region per band for every CTA of the walk's grid (three per SM)
+        const BucketLayout b = bucket_layout(pl->tune.hit_buckets, pl->tune.band_rows_log,
+                                             pl->tune.bucket_records, pl->mode == LARGE_THREE_GAP,
+                                             !pl->chunks.empty(), M_c, wpr, l2_bytes(), (uint64_t)sm_count() * 3);
+        if (b.bad_band_log)
             return fail(CS_EINVAL, "band_rows_log gives records above 32 bits or more than 4096 bands");
-        on = on && fits && n_bands <= BKT_MAX_BANDS;
-        if (on) {
-            // a region per band for every CTA of the walk's grid (three per SM)
-            const uint64_t n_regions = (uint64_t)sm_count() * 3;
-            uint64_t cap = pl->tune.bucket_records;
-            if (!cap) {
-                const uint64_t budget =
-                    std::min<uint64_t>(8ull << 30, std::max<uint64_t>(64ull << 20, 2 * bitset_bytes));
-                cap = budget / 4 / (n_bands * n_regions);
-            }
-            // a multiple of 4, so that every region starts on a 16-byte boundary
-            cap = std::min<uint64_t>(std::max<uint64_t>((cap + 3) / 4 * 4, 4), 1ull << 24);
+        if (b.on) {
             dp.bucket = 1;
-            dp.band_log = bl;
-            dp.n_bands = (uint32_t)n_bands;
-            dp.n_regions = (uint32_t)n_regions;
-            dp.region_cap = (uint32_t)cap;
-            // groups of chunks whose expected stored hits, M_c W sum 1/p over their
-            // primes (Mertens: log log hi - log log lo), fill at most 60% of the
-            // regions; a group's records are applied after its last walk
-            const size_t n_chunks = pl->chunks.size();
-            pl->apply_after.assign(n_chunks, 0);
-            const double room = 0.6 * (double)cap * (double)n_regions * (double)n_bands;
-            double acc = 0;
-            for (size_t c = 0; c < n_chunks; c++) {
-                const double lo = std::max<double>((double)pl->chunks[c].first, 3.0);
-                const double hi = std::max<double>((double)pl->chunks[c].second, lo);
-                const double e = (double)M_c * (double)W * std::log(std::log(hi) / std::log(lo));
-                if (c > 0 && acc > 0 && acc + e > room) {
-                    pl->apply_after[c - 1] = 1;
-                    acc = 0;
-                }
-                acc += e;
-            }
-            pl->apply_after[n_chunks - 1] = 1;
+            dp.band_log = b.band_log;
+            dp.n_bands = (uint32_t)b.n_bands;
+            dp.n_regions = (uint32_t)b.n_regions;
+            dp.region_cap = (uint32_t)b.cap;
+            pl->apply_after = apply_groups(pl->chunks, M_c, W, b);
             for (uint8_t f : pl->apply_after) pl->apply_launches += f;
         }
     }

@@ -8,6 +8,7 @@
 #include <mutex>
 
 #include "../../include/combsieve.h"
+#include "cs_buckets.h"
 #include "cs_errors.h"
 
 namespace cs {
@@ -38,9 +39,6 @@ struct SmallPrime {
 };
 
 // everything a kernel needs about one sieve instance (device pointers)
-// most bands of rows for bucketed hits: 16 KB of per-band counters in a walking CTA
-constexpr uint32_t BKT_MAX_BANDS = 4096;
-
 struct DevPlan {
     uint64_t M_start, M_inc, M_c;
     uint32_t SL, S, S32;          // S = 2 SL + 1 raw offsets, S32 = ceil(S/32) raw words

@@ -402,12 +402,12 @@ WALK_COUNTERS = {
     # search_953 clears directly); prep_*: the walker-preparation kernel of the
     # same run; large_1019's DRAM bytes were not captured at full size (several
     # passes on a 13 GB working set)
-    "large_1019": {"csrc_sha": "5137cbf2aa2f3f3b", "threshold": 100002, "tile_rows": 8, "launches": 756,
-                   "thread_inst": 8482410453711.0, "dram_bytes": None,
-                   "prep_launches": 668, "prep_thread_inst": 3688559220935.0},
-    "search_953": {"csrc_sha": "5137cbf2aa2f3f3b", "threshold": 120003, "tile_rows": 16, "launches": 17,
-                   "thread_inst": 59499039090.0, "dram_bytes": 1797687296.0,
-                   "prep_launches": 7, "prep_thread_inst": 25639266335.0},
+    "large_1019": {"csrc_sha": "c62acc85a540bf78", "threshold": 100002, "tile_rows": 8, "launches": 756,
+                   "thread_inst": 8482416284364.0, "dram_bytes": None,
+                   "prep_launches": 668, "prep_thread_inst": 3688559218341.0},
+    "search_953": {"csrc_sha": "c62acc85a540bf78", "threshold": 120003, "tile_rows": 16, "launches": 17,
+                   "thread_inst": 59499229837.0, "dram_bytes": 1798157568.0,
+                   "prep_launches": 7, "prep_thread_inst": 25639266207.0},
 }
 
 

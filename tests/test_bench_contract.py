@@ -97,6 +97,18 @@ def test_roofline_uses_counters_only_for_the_same_sources_and_setup(bench, monke
     want_a = 1.7e8 / 1.5e-3
     assert abs(r["apply"]["achieved"] - want_a / 1e9) < 1e-6 * want_a / 1e9
     assert abs(r["apply"]["frac"] - want_a / 1.5e11) < 1e-12 and r["apply"]["unit"] == "Gclears/s"
+    # the walker preparation's own entry: its stored instructions per sieve over
+    # its timed share, when the stored launch count matches the plan's
+    prep = bench.KC_NAMES.index("walk_prep")
+    kp_ms, kp_n = list(kern_ms), list(kern_n)
+    kp_ms[prep], kp_n[prep] = 10 * 1.7, 10 * 7
+    monkeypatch.setitem(bench.WALK_COUNTERS, "search_953", dict(ctr, prep_launches=7, prep_thread_inst=2.56e10))
+    r = bench.roofline(walk, kp_ms, kp_n, stats, _info(prep_chunks=7), *args, clears_peak=2e11)
+    want_p = 2.56e10 / 1.7e-3 / 1e12
+    assert abs(r["prep"]["achieved"] - want_p) < 1e-9 * want_p and abs(r["prep"]["frac"] - want_p / 38.25) < 1e-12
+    r = bench.roofline(walk, kp_ms, kp_n, stats, _info(prep_chunks=6), *args, clears_peak=2e11)
+    assert "prep" not in r                                          # other chunking: no entry
+    monkeypatch.setitem(bench.WALK_COUNTERS, "search_953", ctr)
     # no measured peaks: no fraction (never a derived stand-in)
     monkeypatch.setitem(bench.WALK_COUNTERS, "search_953", ctr)
     r = bench.roofline(walk, kern_ms, kern_n, stats, _info(), None, peaks, "measured", {"error": "x"}, "search_953")
